@@ -1,0 +1,292 @@
+"""FP64 CPU oracle of one IT-MPC control iteration (ctypes wrapper around itmpc_oracle.c).
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite, the package's
+smoke check and the benchmark's CPU-baseline leg may import this package.
+It shares no code with the CUDA library and never calls it; inputs come from
+the seeded generators in ``paper_1707_02342_gb300.inputs``.
+
+Every computation lives in ``itmpc_oracle.c`` (plain C, double precision,
+the paper's order of operations); this file only marshals numpy arrays.
+Functions whose result has no independent pin say so in their docstring and
+in the design notes ("parity unpinned"); at present every exported function
+is pinned by a CPU test under ``tests/``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "itmpc_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+
+OK, ERR_ARG, ERR_NONFINITE = 0, -1, -3
+
+
+def build(force: bool = False) -> str:
+    """Compile itmpc_oracle.c into a shared library (gcc, IEEE double, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("K", C.c_int32), ("T", C.c_int32), ("H", C.c_int32), ("activation", C.c_int32),
+        ("dt", C.c_double), ("lam", C.c_double), ("gamma", C.c_double), ("alpha_explore", C.c_double),
+        ("sigma", C.c_double * 2), ("u_min", C.c_double * 2), ("u_max", C.c_double * 2),
+        ("cost_w", C.c_double * 4),
+        ("v_des", C.c_double), ("crash_cost", C.c_double), ("crash_decay", C.c_double),
+        ("track_thresh", C.c_double), ("slip_thresh", C.c_double), ("map_cap", C.c_double),
+        ("seed", C.c_uint64), ("instance", C.c_uint32), ("n_threads", C.c_int32),
+        ("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_void_p),
+        ("W3", C.c_void_p), ("b3", C.c_void_p),
+        ("map", C.c_void_p), ("map_w", C.c_int32), ("map_h", C.c_int32),
+        ("res", C.c_double), ("origin_x", C.c_double), ("origin_y", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.POINTER(_Problem)
+        d, u32p, i64p = C.c_void_p, C.c_void_p, C.c_void_p
+        sig = {
+            "oracle_philox4x32_10": (None, [d, d, d]),
+            "oracle_philox_batch": (None, [C.c_int64, d, d, d]),
+            "oracle_box_muller": (None, [C.c_uint32, C.c_uint32, d]),
+            "oracle_noise": (None, [P, C.c_uint64, C.c_int64, C.c_int32, d]),
+            "oracle_noise_all": (None, [P, C.c_uint64, d]),
+            "oracle_mlp": (None, [P, d, d]),
+            "oracle_dynamics_step": (None, [P, d, d, d]),
+            "oracle_plant_step": (None, [P, d, d, d]),
+            "oracle_costmap": (C.c_double, [P, C.c_double, C.c_double]),
+            "oracle_state_cost": (C.c_double, [P, d, C.c_int32, d, d]),
+            "oracle_rollout_sample": (C.c_double, [P, d, d, C.c_uint64, C.c_int64, d, d, d]),
+            "oracle_weights": (C.c_int, [C.c_int64, d, C.c_double, d, d, d]),
+            "oracle_update": (None, [P, C.c_uint64, d, d, d]),
+            "oracle_rollout_many": (C.c_int, [P, d, d, C.c_uint64, C.c_int64, i64p, d, d, d]),
+            "oracle_iterate": (C.c_int, [P, d, d, C.c_uint64, d, d, d]),
+            "oracle_max_threads": (C.c_int, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(_lib, name)
+            f.restype = res
+            f.argtypes = args
+        del u32p
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+@dataclass
+class Problem:
+    """All inputs of one control iteration except x0, U and the iteration index.
+
+    ``layers`` is a list of three (W, b) pairs with W of shape (fan_out, fan_in);
+    ``costmap`` is a 2-D float32 array (row i, column j) placed by res/origin.
+    """
+    K: int
+    T: int
+    layers: list
+    costmap: np.ndarray
+    res: float
+    origin_x: float
+    origin_y: float
+    dt: float = 0.02
+    lam: float = 1.0
+    gamma: float = 0.0
+    alpha_explore: float = 0.0
+    sigma: tuple = (0.3, 0.35)
+    u_min: tuple = (-1.0, -1.0)
+    u_max: tuple = (1.0, 1.0)
+    cost_w: tuple = (1.0, 1.0, 1.0, 0.0)
+    v_des: float = 6.0
+    crash_cost: float = 1e4
+    crash_decay: float = 0.9
+    track_thresh: float = 0.99
+    slip_thresh: float = 0.75
+    map_cap: float = 2.5
+    seed: int = 0x170702342
+    instance: int = 0
+    activation: int = 0
+    n_threads: int = 1
+    _keep: list = field(default_factory=list, repr=False)
+
+    def struct(self) -> _Problem:
+        (W1, b1), (W2, b2), (W3, b3) = self.layers
+        H = W1.shape[0]
+        assert W1.shape == (H, 6) and W2.shape == (H, H) and W3.shape == (4, H)
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (W1, b1, W2, b2, W3, b3)]
+        m = np.ascontiguousarray(self.costmap, dtype=np.float32)
+        self._keep = arrs + [m]
+        s = _Problem()
+        s.K, s.T, s.H, s.activation = self.K, self.T, H, self.activation
+        s.dt, s.lam, s.gamma, s.alpha_explore = self.dt, self.lam, self.gamma, self.alpha_explore
+        s.sigma[:] = list(self.sigma)
+        s.u_min[:] = list(self.u_min)
+        s.u_max[:] = list(self.u_max)
+        s.cost_w[:] = list(self.cost_w)
+        s.v_des, s.crash_cost, s.crash_decay = self.v_des, self.crash_cost, self.crash_decay
+        s.track_thresh, s.slip_thresh, s.map_cap = self.track_thresh, self.slip_thresh, self.map_cap
+        s.seed, s.instance, s.n_threads = self.seed & (2**64 - 1), self.instance, self.n_threads
+        s.W1, s.b1, s.W2, s.b2, s.W3, s.b3 = (_ptr(a) for a in arrs)
+        s.map, s.map_h, s.map_w = _ptr(m), m.shape[0], m.shape[1]
+        s.res, s.origin_x, s.origin_y = self.res, self.origin_x, self.origin_y
+        return s
+
+    def replace(self, **kw) -> "Problem":
+        d = {k: getattr(self, k) for k in self.__dataclass_fields__ if k != "_keep"}
+        d.update(kw)
+        return Problem(**d)
+
+
+def _f64(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def philox(ctr: np.ndarray, key) -> np.ndarray:
+    """Philox-4x32-10 blocks for an (n, 4) uint32 counter array under a 2-word key."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32).reshape(2)
+    out = np.empty_like(ctr)
+    lib().oracle_philox_batch(ctr.shape[0], _ptr(ctr), _ptr(k), _ptr(out))
+    return out
+
+
+def box_muller(a0: int, a1: int) -> np.ndarray:
+    z = np.empty(2)
+    lib().oracle_box_muller(a0, a1, _ptr(z))
+    return z
+
+
+def noise(P: Problem, it: int) -> np.ndarray:
+    """All of an iteration's noise, (K, T, 2) float64."""
+    s = P.struct()
+    eps = np.empty((P.K, P.T, 2))
+    lib().oracle_noise_all(C.byref(s), it, _ptr(eps))
+    return eps
+
+
+def noise_at(P: Problem, it: int, k: int, t: int) -> np.ndarray:
+    s = P.struct()
+    e = np.empty(2)
+    lib().oracle_noise(C.byref(s), it, k, t, _ptr(e))
+    return e
+
+
+def mlp(P: Problem, z) -> np.ndarray:
+    s = P.struct()
+    z = _f64(z, (6,))
+    d = np.empty(4)
+    lib().oracle_mlp(C.byref(s), _ptr(z), _ptr(d))
+    return d
+
+
+def dynamics_step(P: Problem, x, gv) -> np.ndarray:
+    s = P.struct()
+    x, gv = _f64(x, (7,)), _f64(gv, (2,))
+    xn = np.empty(7)
+    lib().oracle_dynamics_step(C.byref(s), _ptr(x), _ptr(gv), _ptr(xn))
+    return xn
+
+
+def plant_step(P: Problem, x, u) -> np.ndarray:
+    s = P.struct()
+    x, u = _f64(x, (7,)), _f64(u, (2,))
+    xn = np.empty(7)
+    lib().oracle_plant_step(C.byref(s), _ptr(x), _ptr(u), _ptr(xn))
+    return xn
+
+
+def costmap(P: Problem, px: float, py: float) -> float:
+    s = P.struct()
+    return lib().oracle_costmap(C.byref(s), float(px), float(py))
+
+
+def state_cost(P: Problem, x, t: int):
+    """(c, components(4), threshold margin) of one state at loop index t."""
+    s = P.struct()
+    x = _f64(x, (7,))
+    comp = np.empty(4)
+    m = np.empty(1)
+    c = lib().oracle_state_cost(C.byref(s), _ptr(x), t, _ptr(comp), _ptr(m))
+    return c, comp, float(m[0])
+
+
+def rollout_sample(P: Problem, x0, U, it: int, k: int):
+    """(S_k, trajectory (T+1, 7), components (5,), margin) of one sample."""
+    s = P.struct()
+    x0, U = _f64(x0, (7,)), _f64(U, (P.T, 2))
+    traj = np.empty((P.T + 1, 7))
+    comp = np.empty(5)
+    m = np.empty(1)
+    S = lib().oracle_rollout_sample(C.byref(s), _ptr(x0), _ptr(U), it, k, _ptr(traj), _ptr(comp), _ptr(m))
+    return S, traj, comp, float(m[0])
+
+
+def weights(S, lam: float):
+    """(status, w, rho, eta~) of Alg. 2."""
+    S = _f64(S)
+    w = np.empty_like(S)
+    rho = np.empty(1)
+    eta = np.empty(1)
+    rc = lib().oracle_weights(S.shape[0], _ptr(S), float(lam), _ptr(w), _ptr(rho), _ptr(eta))
+    return rc, w, float(rho[0]), float(eta[0])
+
+
+def update(P: Problem, it: int, w, U) -> np.ndarray:
+    s = P.struct()
+    w, U = _f64(w, (P.K,)), _f64(U, (P.T, 2))
+    out = np.empty((P.T, 2))
+    lib().oracle_update(C.byref(s), it, _ptr(w), _ptr(U), _ptr(out))
+    return out
+
+
+def rollout_many(P: Problem, x0, U, it: int, ks=None, with_components: bool = False):
+    """Costs (and threshold margins, optionally components) of the samples ``ks`` (default all)."""
+    s = P.struct()
+    x0, U = _f64(x0, (7,)), _f64(U, (P.T, 2))
+    ks = np.arange(P.K, dtype=np.int64) if ks is None else np.ascontiguousarray(ks, dtype=np.int64)
+    S = np.empty(ks.shape[0])
+    m = np.empty(ks.shape[0])
+    comps = np.empty((ks.shape[0], 5)) if with_components else None
+    rc = lib().oracle_rollout_many(C.byref(s), _ptr(x0), _ptr(U), it, ks.shape[0], _ptr(ks), _ptr(S), _ptr(m),
+                                   _ptr(comps) if comps is not None else None)
+    if rc:
+        raise ValueError(f"oracle_rollout_many: status {rc}")
+    return (S, m, comps) if with_components else (S, m)
+
+
+def iterate(P: Problem, x0, U, it: int):
+    """(status, U' (T, 2), w (K,), S (K,)) of one control iteration."""
+    s = P.struct()
+    x0, U = _f64(x0, (7,)), _f64(U, (P.T, 2))
+    Uo = np.empty((P.T, 2))
+    w = np.empty(P.K)
+    S = np.empty(P.K)
+    rc = lib().oracle_iterate(C.byref(s), _ptr(x0), _ptr(U), it, _ptr(Uo), _ptr(w), _ptr(S))
+    return rc, Uo, w, S
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())

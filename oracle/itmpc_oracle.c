@@ -1,0 +1,373 @@
+/*
+ * itmpc_oracle.c -- plain FP64 CPU oracle of one IT-MPC control iteration.
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  This file exists only to check the
+ * CUDA library against the paper.  The test suite, the package's smoke check
+ * and the benchmark's CPU-baseline leg are the only things that may load it.
+ * It shares no source, header, table or helper with the CUDA library, and it
+ * never calls it.
+ *
+ * Paper: G. Williams, P. Drews, B. Goldfain, J. M. Rehg, E. A. Theodorou,
+ * "Information Theoretic Model Predictive Control: Theory and Applications to
+ * Autonomous Driving", arXiv 1707.02342.
+ *
+ * Everything below is double precision and follows the paper's order of
+ * operations without blocking, fusion or reordering:
+ *   - Alg. 1 (Sampling Based MPC): draw noise, roll every sample out for T
+ *     steps through F(x, g(v)), add the running cost after each step;
+ *   - Alg. 2 (Information Theoretic Weight Computation): rho = min_k S_k,
+ *     eta~ = sum_k exp(-(S_k - rho)/lambda), w_k = exp(-(S_k - rho)/lambda)/eta~;
+ *   - the control law of Sec. III-D (IT-Controls), u_t = sum_k w_k v_{k,t};
+ *   - dynamics of Sec. V-B (kinematics k(x) plus a network f(x_d, v));
+ *   - the state cost of Sec. V-C (track, speed and stabilizing terms).
+ * Where the paper is silent or garbled, the reading taken is stated at the
+ * function that implements it.
+ *
+ * Noise: the paper does not say how its Gaussian samples are produced.  Both
+ * this oracle and the CUDA path implement Philox-4x32-10 from its published
+ * definition (J. K. Salmon, M. A. Moraes, R. O. Dror, D. E. Shaw, "Parallel
+ * Random Numbers: As Easy as 1, 2, 3", SC'11) and the Box-Muller transform
+ * (G. E. P. Box, M. E. Muller, Ann. Math. Stat. 29, 1958) independently, so
+ * any iteration's noise can be regenerated here exactly.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_ERR_ARG (-1)
+#define ORACLE_ERR_NONFINITE (-3)
+
+/* Problem description.  The network weights follow the layout (fan_out x
+ * fan_in), row-major: W1 is H x 6, W2 is H x H, W3 is 4 x H. */
+typedef struct {
+  int32_t K, T, H, activation; /* activation: 0 = tanh, 1 = identity */
+  double dt, lambda, gamma, alpha_explore;
+  double sigma[2], u_min[2], u_max[2];
+  double cost_w[4]; /* multipliers of: track, speed, stabilizing, crash impulses */
+  double v_des, crash_cost, crash_decay, track_thresh, slip_thresh, map_cap;
+  uint64_t seed;
+  uint32_t instance;
+  int32_t n_threads;
+  const double *W1, *b1, *W2, *b2, *W3, *b3;
+  const float *map;
+  int32_t map_w, map_h;
+  double res, origin_x, origin_y;
+} oracle_problem;
+
+/* ------------------------------------------------------------------------- */
+/* Philox-4x32-10 (Salmon et al., SC'11, Sec. 5): ten rounds of two 32x32->64
+ * multiplications with the round constants 0xD2511F53 and 0xCD9E8D57; the
+ * key is bumped by the Weyl constants 0x9E3779B9 and 0xBB67AE85 between
+ * rounds.                                                                    */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void oracle_philox_batch(int64_t n, const uint32_t *ctr, const uint32_t key[2], uint32_t *out) {
+  for (int64_t i = 0; i < n; ++i) oracle_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
+/* Uniform in (0, 1]: the top 24 bits of a word, plus one, times 2^-24.  Every
+ * such value is exact in binary32 and binary64, so both sides see the same u. */
+static double u01(uint32_t a) { return ((double)(a >> 8) + 1.0) * (1.0 / 16777216.0); }
+
+/* Box-Muller: two standard normals from two uniforms. */
+void oracle_box_muller(uint32_t a0, uint32_t a1, double z[2]) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double u0 = u01(a0), u1 = u01(a1);
+  double r = sqrt(-2.0 * log(u0));
+  z[0] = r * cos(two_pi * u1);
+  z[1] = r * sin(two_pi * u1);
+}
+
+/* eps^k_t ~ N(0, Sigma), Sigma = diag(sigma_1^2, sigma_2^2) (Sec. II; Alg. 1
+ * "Sample E^k").  One Philox block per (k, t):
+ *   counter = (k, t, iter_lo, (iter_hi & 0xFFFF) | instance << 16),
+ *   key     = (seed_lo, seed_hi);
+ * words 0 and 1 feed Box-Muller; words 2 and 3 are unused.                   */
+void oracle_noise(const oracle_problem *P, uint64_t iter, int64_t k, int32_t t, double eps[2]) {
+  uint32_t ctr[4] = {(uint32_t)k, (uint32_t)t, (uint32_t)iter,
+                     (uint32_t)((iter >> 32) & 0xFFFFu) | (P->instance << 16)};
+  uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};
+  uint32_t w[4];
+  double z[2];
+  oracle_philox4x32_10(ctr, key, w);
+  oracle_box_muller(w[0], w[1], z);
+  eps[0] = P->sigma[0] * z[0];
+  eps[1] = P->sigma[1] * z[1];
+}
+
+void oracle_noise_all(const oracle_problem *P, uint64_t iter, double *eps /* K x T x 2 */) {
+  for (int64_t k = 0; k < P->K; ++k)
+    for (int32_t t = 0; t < P->T; ++t) oracle_noise(P, iter, k, t, eps + 2 * ((size_t)k * P->T + t));
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. V-B, "Neural Network Model": two fully connected hidden layers with
+ * hyperbolic-tangent non-linearities and a linear output layer.  Input
+ * z = (roll, v_x, v_y, theta_dot, steer, throttle); output = f(x_d, v), the
+ * time derivative of x_d = (roll, v_x, v_y, theta_dot).                       */
+static double act(const oracle_problem *P, double a) { return P->activation == 1 ? a : tanh(a); }
+
+#define ORACLE_MAX_H 1024
+
+void oracle_mlp(const oracle_problem *P, const double z[6], double d[4]) {
+  const int H = P->H;
+  double h1[ORACLE_MAX_H], h2[ORACLE_MAX_H];
+  for (int j = 0; j < H; ++j) {
+    double a = P->b1[j];
+    for (int i = 0; i < 6; ++i) a += P->W1[j * 6 + i] * z[i];
+    h1[j] = act(P, a);
+  }
+  for (int j = 0; j < H; ++j) {
+    double a = P->b2[j];
+    for (int i = 0; i < H; ++i) a += P->W2[(size_t)j * H + i] * h1[i];
+    h2[j] = act(P, a);
+  }
+  for (int o = 0; o < 4; ++o) {
+    double a = P->b3[o];
+    for (int i = 0; i < H; ++i) a += P->W3[(size_t)o * H + i] * h2[i];
+    d[o] = a;
+  }
+}
+
+/* g(v): clamp each control into [u_min, u_max] (Sec. III-E, "Handling Control
+ * Constraints").  The paper gives no limits; callers pass them. */
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* One explicit-Euler step of the full equations of motion (Sec. V-B):
+ *   x_k(t+1) = x_k(t) + k(x(t)) dt,  k(x) = (cos th v_x - sin th v_y,
+ *                                            sin th v_x + cos th v_y, th_dot)
+ *   x_d(t+1) = x_d(t) + f(x_d(t), v(t)) dt
+ * Both halves use the old state x(t).  gv is the already clamped control. */
+void oracle_dynamics_step(const oracle_problem *P, const double x[7], const double gv[2], double xn[7]) {
+  double th = x[2], vx = x[4], vy = x[5], thd = x[6];
+  double z[6] = {x[3], x[4], x[5], x[6], gv[0], gv[1]};
+  double f[4];
+  oracle_mlp(P, z, f);
+  xn[0] = x[0] + (cos(th) * vx - sin(th) * vy) * P->dt;
+  xn[1] = x[1] + (sin(th) * vx + cos(th) * vy) * P->dt;
+  xn[2] = x[2] + thd * P->dt;
+  for (int i = 0; i < 4; ++i) xn[3 + i] = x[3 + i] + f[i] * P->dt;
+}
+
+/* Noise-free plant step F(x, g(u)) used by a closed loop (Alg. 1,
+ * "SendToActuators"). */
+void oracle_plant_step(const oracle_problem *P, const double x[7], const double u[2], double xn[7]) {
+  double gv[2] = {clampd(u[0], P->u_min[0], P->u_max[0]), clampd(u[1], P->u_min[1], P->u_max[1])};
+  oracle_dynamics_step(P, x, gv, xn);
+}
+
+/* h(p_x, p_y): the costmap lookup of Sec. V-C ("Track Cost").  The paper uses
+ * the hardware-interpolated texture fetch; this is bilinear interpolation
+ * with texel (i, j) centred at (origin_x + (j + 1/2) res, origin_y + (i + 1/2) res)
+ * and clamp-to-edge addressing, in double precision. */
+static long clamp_index(double i, long n) { return i < 0.0 ? 0 : (i > (double)(n - 1) ? n - 1 : (long)i); }
+
+double oracle_costmap(const oracle_problem *P, double px, double py) {
+  double fx = (px - P->origin_x) / P->res - 0.5;
+  double fy = (py - P->origin_y) / P->res - 0.5;
+  if (isnan(fx) || isnan(fy)) return NAN;
+  double jf = floor(fx), if_ = floor(fy);
+  double a = fx - jf, b = fy - if_;
+  long W = P->map_w, Hh = P->map_h;
+  long j0 = clamp_index(jf, W), j1 = clamp_index(jf + 1.0, W);
+  long i0 = clamp_index(if_, Hh), i1 = clamp_index(if_ + 1.0, Hh);
+  double m00 = P->map[i0 * W + j0], m01 = P->map[i0 * W + j1];
+  double m10 = P->map[i1 * W + j0], m11 = P->map[i1 * W + j1];
+  return (1.0 - a) * (1.0 - b) * m00 + a * (1.0 - b) * m01 + (1.0 - a) * b * m10 + a * b * m11;
+}
+
+/* State cost c(x_t) at loop index t = 1..T (Sec. V-C):
+ *   alpha_1 Track + alpha_2 Speed + alpha_3 Stabilizing, with
+ *   Track       = h + decay^t * crash * I{h > track_thresh}, h capped at map_cap,
+ *   Speed       = (v_x - v_des)^2,
+ *   Stabilizing = zeta^2 + crash * I{|zeta| > slip_thresh},
+ *   zeta        = -arctan(v_y / |v_x|), read as -atan2(v_y, |v_x|) so that it
+ *                 is defined at v_x = 0.
+ * The paper prints alpha_1..3 without values.  cost_w[0..2] are those
+ * multipliers and cost_w[3] multiplies both impulse terms, so
+ *   c = w0 h + w1 Speed + w2 zeta^2 + w3 crash (decay^t I{h>.} + I{|zeta|>.}).
+ * comp (optional) receives the four unweighted terms; margin (optional)
+ * receives the distance of h and |zeta| to their thresholds.               */
+double oracle_state_cost(const oracle_problem *P, const double x[7], int32_t t, double comp[4], double *margin) {
+  double h = oracle_costmap(P, x[0], x[1]);
+  if (h > P->map_cap) h = P->map_cap;
+  double vx = x[4], vy = x[5];
+  double zeta = -atan2(vy, fabs(vx));
+  double speed = (vx - P->v_des) * (vx - P->v_des);
+  double imp = 0.0;
+  if (h > P->track_thresh) imp += pow(P->crash_decay, (double)t) * P->crash_cost;
+  if (fabs(zeta) > P->slip_thresh) imp += P->crash_cost;
+  if (comp) {
+    comp[0] = h;
+    comp[1] = speed;
+    comp[2] = zeta * zeta;
+    comp[3] = imp;
+  }
+  if (margin) {
+    double m1 = fabs(h - P->track_thresh), m2 = fabs(fabs(zeta) - P->slip_thresh);
+    *margin = m1 < m2 ? m1 : m2;
+  }
+  return P->cost_w[0] * h + P->cost_w[1] * speed + P->cost_w[2] * zeta * zeta + P->cost_w[3] * imp;
+}
+
+/* Alg. 1, inner loop, for one sample k:
+ *   x <- x0
+ *   for t = 1..T:
+ *     v_{t-1} = u_{t-1} + eps_{t-1}  if k < (1 - alpha) K, else eps_{t-1}
+ *     x <- F(x, g(v_{t-1}))
+ *     S += c(x) + gamma u_{t-1}^T Sigma^{-1} v_{t-1}
+ *   S += phi(x)
+ * Readings: the control-cost line of Alg. 1 prints v_t inside a loop whose
+ * other lines use t-1; v_{t-1} is taken.  The term is skipped when gamma is 0
+ * (so that Sigma = 0 stays defined).  phi is not given by the paper and is 0.
+ * traj (optional) receives x_0..x_T, (T+1) x 7; comp (optional) receives the
+ * five unweighted sums (track, speed, stabilizing, impulses, control term
+ * without gamma); margin (optional) the smallest threshold distance along
+ * the rollout.  Returns S_k.                                                */
+double oracle_rollout_sample(const oracle_problem *P, const double x0[7], const double *U, uint64_t iter,
+                             int64_t k, double *traj, double comp[5], double *margin) {
+  double x[7], xn[7];
+  memcpy(x, x0, sizeof(x));
+  if (traj) memcpy(traj, x0, sizeof(x));
+  int importance = (double)k < (1.0 - P->alpha_explore) * (double)P->K;
+  double S = 0.0, mmin = INFINITY;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int32_t t = 1; t <= P->T; ++t) {
+    double eps[2], v[2], gv[2];
+    oracle_noise(P, iter, k, t - 1, eps);
+    for (int i = 0; i < 2; ++i) {
+      v[i] = importance ? U[2 * (t - 1) + i] + eps[i] : eps[i];
+      gv[i] = clampd(v[i], P->u_min[i], P->u_max[i]);
+    }
+    oracle_dynamics_step(P, x, gv, xn);
+    memcpy(x, xn, sizeof(x));
+    if (traj) memcpy(traj + 7 * (size_t)t, x, sizeof(x));
+    double c4[4], m;
+    double c = oracle_state_cost(P, x, t, c4, &m);
+    if (m < mmin) mmin = m;
+    for (int i = 0; i < 4; ++i) acc[i] += c4[i];
+    double ctrl = 0.0;
+    if (P->gamma != 0.0) {
+      ctrl = U[2 * (t - 1)] * v[0] / (P->sigma[0] * P->sigma[0]) +
+             U[2 * (t - 1) + 1] * v[1] / (P->sigma[1] * P->sigma[1]);
+      acc[4] += ctrl;
+    }
+    S += c + P->gamma * ctrl;
+  }
+  if (comp) memcpy(comp, acc, sizeof(acc));
+  if (margin) *margin = mmin;
+  return S;
+}
+
+/* Alg. 2.  Non-finite costs get weight 0 (they stand for rollouts that left
+ * the representable range); if no cost is finite the iteration is rejected.
+ * The paper's line w_k <- exp(.)/eta uses eta~, the sum it has just formed. */
+int oracle_weights(int64_t K, const double *S, double lambda, double *w, double *rho_out, double *eta_out) {
+  if (K <= 0 || !(lambda > 0.0)) return ORACLE_ERR_ARG;
+  double rho = INFINITY;
+  for (int64_t k = 0; k < K; ++k)
+    if (isfinite(S[k]) && S[k] < rho) rho = S[k];
+  if (!isfinite(rho)) return ORACLE_ERR_NONFINITE;
+  double eta = 0.0;
+  for (int64_t k = 0; k < K; ++k) eta += isfinite(S[k]) ? exp(-(S[k] - rho) / lambda) : 0.0;
+  for (int64_t k = 0; k < K; ++k) w[k] = isfinite(S[k]) ? exp(-(S[k] - rho) / lambda) / eta : 0.0;
+  if (rho_out) *rho_out = rho;
+  if (eta_out) *eta_out = eta;
+  return ORACLE_OK;
+}
+
+/* Control update.  Sec. III-D (IT-Controls) sets u_t = sum_k w_k v_{k,t}, the
+ * weighted mean of the sampled (unclamped) controls.  With alpha = 0 this is
+ * Alg. 1's U + sum_k w_k eps_k (the weights sum to one); with exploration
+ * samples (v = eps) the two forms differ and the equation's form is taken.
+ * Savitzky-Golay smoothing is not applied here.                              */
+void oracle_update(const oracle_problem *P, uint64_t iter, const double *w, const double *U, double *U_out) {
+  for (int32_t t = 0; t < P->T; ++t) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t k = 0; k < P->K; ++k) {
+      if (w[k] == 0.0) continue;
+      double eps[2];
+      oracle_noise(P, iter, k, t, eps);
+      int importance = (double)k < (1.0 - P->alpha_explore) * (double)P->K;
+      double v0 = importance ? U[2 * t] + eps[0] : eps[0];
+      double v1 = importance ? U[2 * t + 1] + eps[1] : eps[1];
+      s0 += w[k] * v0;
+      s1 += w[k] * v1;
+    }
+    U_out[2 * t] = s0;
+    U_out[2 * t + 1] = s1;
+  }
+}
+
+static int check_problem(const oracle_problem *P) {
+  if (!P || P->K <= 0 || P->T <= 0 || P->H <= 0 || P->H > ORACLE_MAX_H) return ORACLE_ERR_ARG;
+  if (!P->W1 || !P->b1 || !P->W2 || !P->b2 || !P->W3 || !P->b3) return ORACLE_ERR_ARG;
+  if (!P->map || P->map_w <= 0 || P->map_h <= 0 || !(P->res > 0.0)) return ORACLE_ERR_ARG;
+  if (!(P->lambda > 0.0)) return ORACLE_ERR_ARG;
+  return ORACLE_OK;
+}
+
+/* Costs of a list of samples (for sampled parity at large K and for timing).
+ * Samples are independent (Alg. 1's loop over k), so they may run on several
+ * threads; each sample's arithmetic is unchanged.                           */
+int oracle_rollout_many(const oracle_problem *P, const double x0[7], const double *U, uint64_t iter, int64_t n,
+                        const int64_t *ks, double *S, double *margins, double *comps /* n x 5 or NULL */) {
+  int rc = check_problem(P);
+  if (rc) return rc;
+  int nt = P->n_threads > 0 ? P->n_threads : 1;
+  (void)nt;
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i)
+    S[i] = oracle_rollout_sample(P, x0, U, iter, ks[i], NULL, comps ? comps + 5 * i : NULL,
+                                 margins ? margins + i : NULL);
+  return ORACLE_OK;
+}
+
+/* One control iteration: the body of Alg. 1's outer loop up to the update.
+ * Outputs U_out (T x 2), weights w (K) and costs S (K).                     */
+int oracle_iterate(const oracle_problem *P, const double x0[7], const double *U, uint64_t iter, double *U_out,
+                   double *w, double *S) {
+  int rc = check_problem(P);
+  if (rc) return rc;
+  int nt = P->n_threads > 0 ? P->n_threads : 1;
+  (void)nt;
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
+  for (int64_t k = 0; k < P->K; ++k) S[k] = oracle_rollout_sample(P, x0, U, iter, k, NULL, NULL, NULL);
+  rc = oracle_weights(P->K, S, P->lambda, w, NULL, NULL);
+  if (rc) return rc;
+  oracle_update(P, iter, w, U, U_out);
+  return ORACLE_OK;
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
