@@ -1,0 +1,354 @@
+"""Benchmark of one IT-MPC control iteration on GB300.
+
+Workload (the working-size configuration): K = 2048 samples, T = 100 steps,
+6->32->32->4 tanh dynamics network (Xavier, seed 42), 1024 x 1024 FP32
+costmap at 0.1 m of a seeded closed spline track, speed target 6 m/s, 1e4
+impulses, lambda = 1, sigma = (0.3, 0.35).  All inputs are synthetic.
+
+A step is one full iteration (noise, rollouts, costs, weights, update) through
+``itmpc_iterate``; the iteration index advances every step and U' is fed back
+as the next nominal sequence.  L2 is flushed (256 MiB write) before every timed
+step; only the iteration itself is inside each step's CUDA-event pair.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
+paper ships no implementation to run).  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MPPI rollout-steps/s & control updates/s; BF16/batched vs FP32 at stated error"
+UNIT = "rollout-steps/s"
+K_WORK, T_WORK, H_WORK = 2048, 100, 32
+FLOP_PER_SAMPLE_STEP = 2 * (6 * H_WORK + H_WORK * H_WORK + H_WORK * 4)  # network MACs x 2 = 2688
+PROFILE = os.path.join(ROOT, "profiles", "iterate_fp32_K2048_T100.md")
+KERNEL_SOURCES = ["paper_1707_02342_gb300/csrc/iterate_fp32.cu", "paper_1707_02342_gb300/csrc/itmpc_device.cuh"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m_src = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_src or not m_b or m_src.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+def workload():
+    from paper_1707_02342_gb300 import inputs
+
+    tmap = inputs.track_costmap(inputs.spline_centerline(1), 1024, 0.1, 2.5)
+    layers = inputs.mlp_xavier((6, H_WORK, H_WORK, 4), seed=42)
+    x0 = inputs.start_state(tmap.centerline)
+    x0[4] = 4.0
+    U = inputs.nominal_controls(T_WORK, seed=9, scale=0.2)
+    params = dict(dt=0.02, lam=1.0, gamma=0.0, alpha_explore=0.0, sigma=(0.3, 0.35), u_min=(-1.0, -1.0),
+                  u_max=(1.0, 1.0), cost_w=(1.0, 1.0, 1.0, 1.0), v_des=6.0, crash_cost=1e4, crash_decay=0.9,
+                  track_thresh=0.99, slip_thresh=0.75, map_cap=2.5, seed=0x170702342)
+    return tmap, layers, x0, U, params
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.05)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(seconds: float = 10.0, min_iters: int = 2):
+    """The FP64 oracle on the host cores: full iterations of the workload for about ``seconds``."""
+    import numpy as np
+
+    import oracle
+
+    tmap, layers, x0, U, params = workload()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    P = oracle.Problem(K=K_WORK, T=T_WORK, layers=layers, costmap=tmap.data, res=tmap.res, origin_x=tmap.origin_x,
+                       origin_y=tmap.origin_y, lam=params["lam"], sigma=params["sigma"], cost_w=params["cost_w"],
+                       n_threads=cores)
+    U64 = U.astype(np.float64)
+    n, t0 = 0, time.perf_counter()
+    while n < min_iters or time.perf_counter() - t0 < seconds:
+        rc, U64, _, _ = oracle.iterate(P, x0, U64, n)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": K_WORK * T_WORK * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} full iterations of K={K_WORK}, T={T_WORK} (FP64 C oracle, OpenMP over samples) "
+                      f"in {dt:.1f} s"}, dt / n
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    d = json.load(open(path)) if os.path.exists(path) else {}
+    return d
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    per = None
+    import numpy as np
+
+    import oracle
+
+    tmap, layers, x0, U, params = workload()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    P = oracle.Problem(K=K_WORK, T=T_WORK, layers=layers, costmap=tmap.data, res=tmap.res, origin_x=tmap.origin_x,
+                       origin_y=tmap.origin_y, lam=params["lam"], sigma=params["sigma"], cost_w=params["cost_w"],
+                       n_threads=cores)
+    U64 = U.astype(np.float64)
+    for i in range(args.warmup):
+        _, U64, _, _ = oracle.iterate(P, x0, U64, i)
+    # bounded: at most ~60 s of timed oracle work whatever --steps says
+    t0 = time.perf_counter()
+    n = 0
+    for i in range(steps):
+        _, U64, _, _ = oracle.iterate(P, x0, U64, args.warmup + i)
+        n += 1
+        if time.perf_counter() - t0 > 60.0:
+            break
+    dt = time.perf_counter() - t0
+    per = dt / n
+    value = K_WORK * T_WORK / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"it-mpc iteration K={K_WORK} T={T_WORK} H={H_WORK} spline-1024 map",
+                       "K": K_WORK, "T": T_WORK, "hidden": H_WORK, "map": "1024x1024@0.1m"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} full iterations (FP64 C oracle, OpenMP over samples)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "control_updates_per_s": 1.0 / per}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1707_02342_gb300 import build as nbuild
+    from paper_1707_02342_gb300 import itmpc
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        nbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    tmap, layers, x0, U, params = workload()
+    stream = torch.cuda.current_stream()
+    ctl = itmpc.Controller(K_WORK, T_WORK, hidden=H_WORK, instance=rank, **params)
+    ctl.set_dynamics([(torch.tensor(W, device="cuda"), torch.tensor(b, device="cuda")) for W, b in layers])
+    ctl.set_costmap(torch.tensor(tmap.data, device="cuda"), tmap.res, tmap.origin_x, tmap.origin_y)
+    x0_d = torch.tensor(x0, device="cuda")
+    U0_d = torch.tensor(U, device="cuda")
+    U_d = U0_d.clone()
+    w_d = torch.empty(K_WORK, device="cuda")
+    S_d = torch.empty(K_WORK, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    launches_per_step = 1 if K_WORK <= 16384 else 2
+
+    def step(i):
+        ctl.iterate(x0_d, U_d, i, U_d, w_d, S_d)
+
+    for i in range(args.warmup):
+        flush.zero_()
+        step(i)
+    torch.cuda.synchronize()
+    assert ctl.read_status() == itmpc.OK
+    U_d.copy_(U0_d)
+
+    n = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    sampler = ClockSampler(local_rank)
+    with sampler:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for i in range(n):
+            flush.zero_()
+            starts[i].record(stream)
+            step(args.warmup + i)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t_wall = time.perf_counter() - t_wall
+    assert ctl.read_status() == itmpc.OK
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    mean_ms = float(step_ms.mean())
+    if world > 1:
+        t = torch.tensor([mean_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        mean_ms = float(t.item())
+
+    # end to end through the host-pointer entry point: h2d of x0 + U, d2h of U'
+    x0_h = torch.tensor(x0).pin_memory().numpy()
+    U_h = torch.tensor(U).pin_memory().numpy()
+    Uo_h = torch.empty((T_WORK, 2), dtype=torch.float32).pin_memory().numpy()
+    e2e_n = min(n, 500)
+    e2e_s = []
+    for i in range(e2e_n):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ctl.iterate_host(x0_h, U_h, args.warmup + i, Uo_h)
+        e2e_s.append(time.perf_counter() - t0)
+        assert st == itmpc.OK
+        U_h[:] = Uo_h
+    e2e_mean = float(np.mean(e2e_s))
+    if world > 1:
+        t = torch.tensor([e2e_mean], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_mean = float(t.item())
+
+    if rank != 0:
+        return
+    pk = peaks()
+    props = torch.cuda.get_device_properties(local_rank)
+    n_sm = props.multi_processor_count
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = FLOP_PER_SAMPLE_STEP * K_WORK * T_WORK / (float(step_ms.mean()) * 1e-3) / 1e12
+    traffic = profiled_traffic()
+    clocks = sampler.summary()
+    value = world * K_WORK * T_WORK / (mean_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"it-mpc iteration K={K_WORK} T={T_WORK} H={H_WORK} spline-1024 map",
+                   "K": K_WORK, "T": T_WORK, "hidden": H_WORK, "map": "1024x1024@0.1m", "crash_cost": 1e4,
+                   "l2": "flushed before every timed step (256 MiB write, outside the step's events)",
+                   "instances": "one independent instance per GPU (Philox instance = rank)"},
+        "control_updates_per_s": world / (mean_ms * 1e-3),
+        "ms_per_step_median": float(np.median(step_ms)),
+        "wall_s_timed_region_incl_flush": t_wall,
+        "e2e": {"value": world * K_WORK * T_WORK / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": 4 * (7 + 2 * T_WORK),
+                "d2h_bytes_per_step": 4 * 2 * T_WORK, "steps": e2e_n,
+                "entry_point": "itmpc_iterate_host (pinned host buffers; includes copies and stream sync)"},
+        "gpu_launches": n * launches_per_step,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "iterate_fp32_kernel<32,4,4>",
+                     "peak_derivation": f"{n_sm} SMs x 128 FP32 lanes x 2 FLOP x {sm_max:.0f} MHz (max SM clock)",
+                     "algorithmic_flop_per_launch": FLOP_PER_SAMPLE_STEP * K_WORK * T_WORK},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cb, _ = cpu_oracle_rate(seconds=args.cpu_seconds)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    ctl.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * itmpc.h -- C ABI of the GB300 IT-MPC control-iteration library (libitmpc.so).
+ *
+ * One control iteration of information-theoretic MPC (Williams, Drews,
+ * Goldfain, Rehg, Theodorou, "Information Theoretic Model Predictive Control:
+ * Theory and Applications to Autonomous Driving", arXiv 1707.02342):
+ *   1. draw K noise sequences eps^k ~ N(0, Sigma) of length T  (Alg. 1),
+ *   2. roll every perturbed sequence out through x <- F(x, g(v)) with the
+ *      network-plus-kinematics vehicle model of Sec. V-B,
+ *   3. add the state cost of Sec. V-C after every step (Alg. 1),
+ *   4. weight the samples by exp(-(S_k - rho)/lambda)/eta~ (Alg. 2) and
+ *      replace the nominal sequence by the weighted mean of the sampled
+ *      controls (Sec. III-D, "IT-Controls").
+ * Every step runs in hand-written CUDA kernels for sm_103a.  There is no CPU
+ * fallback: without a usable GPU the calls return ITMPC_ERR_CUDA.
+ *
+ * Conventions shared by all entry points:
+ *   - Arrays are row-major FP32 unless stated.  State order is
+ *     (p_x, p_y, theta, roll, v_x, v_y, theta_dot), control order
+ *     (steer, throttle) (Sec. V-B).
+ *   - "device pointer" arguments must point to memory of the device that was
+ *     current when the context was created; calls taking them are
+ *     asynchronous and ordered on the context's stream.
+ *   - No entry point keeps a caller pointer after it returns: set_* calls copy.
+ *   - Errors never cross the ABI as exceptions: every call returns an
+ *     itmpc_status, and itmpc_last_error() gives a message for the last
+ *     failing call on a context.  Argument errors are detected before any GPU
+ *     work is queued and leave the context unchanged.
+ *   - Noise is Philox-4x32-10 (Salmon et al., SC'11) with one block per
+ *     (k, t): counter = (k, t, iter_lo, (iter_hi & 0xFFFF) | instance << 16),
+ *     key = (seed_lo, seed_hi); words 0 and 1 give u_i = ((w_i >> 8) + 1) 2^-24
+ *     and Box-Muller gives (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1);
+ *     eps = (sigma_0 z0, sigma_1 z1).  The paper does not specify its
+ *     generator; this layout lets any iteration be regenerated exactly.
+ */
+#ifndef ITMPC_H
+#define ITMPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ITMPC_OK = 0,
+  ITMPC_ERR_ARG = -1,       /* invalid argument (shape, pointer, range) */
+  ITMPC_ERR_CUDA = -2,      /* CUDA runtime error, including "no device" */
+  ITMPC_ERR_NONFINITE = -3, /* every rollout cost was non-finite: U left unchanged */
+  ITMPC_ERR_TIMEOUT = -4,   /* a bounded device-side wait ran out */
+  ITMPC_ERR_STATE = -5,     /* call out of order (e.g. iterate before set_dynamics) */
+  ITMPC_ERR_OOM = -6        /* device allocation failed */
+} itmpc_status;
+
+typedef enum { ITMPC_FP32 = 0, ITMPC_BF16 = 1, ITMPC_FP8 = 2 } itmpc_precision;
+typedef enum { ITMPC_ACT_TANH = 0, ITMPC_ACT_IDENTITY = 1 } itmpc_activation;
+
+#define ITMPC_MAX_K (1 << 24)
+#define ITMPC_MAX_T 512
+#define ITMPC_STATS_LEN 8
+
+/* Iteration parameters (Alg. 1 inputs; Sec. III-E; Sec. V-C).
+ *   K, T            samples and horizon; T <= T_max (fixed at create; 0 means T)
+ *   hidden          H of the 6 -> H -> H -> 4 dynamics network (32, 64 or 128)
+ *   dt              Euler step of Sec. V-B
+ *   lambda          inverse temperature of Alg. 2 (> 0)
+ *   gamma           control-cost parameter of Sec. III-E; the term
+ *                   gamma u_{t-1}' Sigma^-1 v_{t-1} is added to S when gamma != 0
+ *   alpha_explore   fraction of samples drawn around zero (Alg. 1's alpha):
+ *                   sample k uses v = u + eps iff k < (1 - alpha) K
+ *   sigma           standard deviations, Sigma = diag(sigma^2)
+ *   u_min, u_max    bounds of the clamp g (Sec. III-E, "Handling Control Constraints")
+ *   cost_w          multipliers of (track, speed, stabilizing, impulse) terms
+ *   v_des           speed target; crash_cost the impulse size (1e4 in Sec. V-C);
+ *   crash_decay     the 0.9 of the time-decayed track impulse (power t = 1..T);
+ *   track_thresh    0.99; slip_thresh 0.75; map_cap 2.5 (Sec. V-C)
+ *   seed, instance  Philox key and instance tag
+ *   precision       ITMPC_FP32 for itmpc_iterate
+ *   activation      ITMPC_ACT_TANH (the paper's network) or ITMPC_ACT_IDENTITY
+ *                   (an affine network, used by closed-form checks)
+ *   stream          cudaStream_t all calls are ordered on (NULL: legacy default) */
+typedef struct {
+  int32_t K, T, T_max, hidden;
+  float dt, lambda, gamma, alpha_explore;
+  float sigma[2];
+  float u_min[2], u_max[2];
+  float cost_w[4];
+  float v_des, crash_cost, crash_decay, track_thresh, slip_thresh, map_cap;
+  uint64_t seed;
+  uint32_t instance;
+  int32_t precision;
+  int32_t activation;
+  int32_t reserved;
+  void *stream;
+} itmpc_config;
+
+typedef struct itmpc_ctx itmpc_ctx;
+
+/* Create a context for cfg on the current device.  Allocates all device
+ * buffers the iteration needs for K samples and horizon T_max (no allocation
+ * happens in itmpc_iterate).  *out receives the context, or NULL on error.
+ * Errors: ITMPC_ERR_ARG (bad cfg), ITMPC_ERR_CUDA / ITMPC_ERR_OOM. */
+itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out);
+
+/* Replace the iteration parameters.  K may not exceed the K given at create,
+ * T may not exceed T_max and hidden may not change.  Host-only; takes effect
+ * for calls queued afterwards. */
+itmpc_status itmpc_set_config(itmpc_ctx *ctx, const itmpc_config *cfg);
+
+/* Set the stream later calls are queued on (a cudaStream_t, NULL = default). */
+itmpc_status itmpc_set_stream(itmpc_ctx *ctx, void *stream);
+
+/* Dynamics network f of Sec. V-B ("Neural Network Model"): two hidden layers
+ * with tanh and a linear output, f(z) = W3 tanh(W2 tanh(W1 z + b1) + b2) + b3,
+ * z = (roll, v_x, v_y, theta_dot, steer, throttle), f = d x_d / dt.
+ *   n_layers must be 3; widths = {6, H, H, 4} with H == cfg.hidden;
+ *   W[l] is (widths[l+1] x widths[l]) row-major, b[l] has widths[l+1] entries;
+ *   on_device != 0: the pointers are device pointers, else host pointers.
+ * The weights are copied into the context (synchronously for host input). */
+itmpc_status itmpc_set_dynamics(itmpc_ctx *ctx, int32_t n_layers, const int32_t *widths, const float *const *W,
+                                const float *const *b, int32_t on_device);
+
+/* Track costmap h of Sec. V-C: height x width FP32 texels, row-major (row i,
+ * column j), texel (i, j) centred at (origin_x + (j + 0.5) res,
+ * origin_y + (i + 0.5) res).  Lookups are bilinear with clamp-to-edge
+ * addressing, computed in FP32 in software (the paper's hardware texture
+ * filter has 8-bit weights).  The map is copied into the context; a new size
+ * reallocates it.  on_device selects device or host input. */
+itmpc_status itmpc_set_costmap(itmpc_ctx *ctx, const float *map, int32_t width, int32_t height, float res,
+                               float origin_x, float origin_y, int32_t on_device);
+
+/* One control iteration (Alg. 1 body up to the update; Alg. 2).
+ *   x0      device, 7 floats: start state
+ *   U       device, T x 2: nominal controls u_0..u_{T-1}
+ *   iter    Philox counter words 2-3 (use the closed-loop step index)
+ *   U_out   device, T x 2: sum_k w_k v_{k,t} (= U + sum_k w_k eps_k when alpha = 0);
+ *           may alias U
+ *   weights device, K, or NULL: w_k of Alg. 2
+ *   costs   device, K, or NULL: S_k, including the gamma term
+ * Asynchronous.  A device-side condition (every S_k non-finite) copies U to
+ * U_out, zeroes the weights and records ITMPC_ERR_NONFINITE, which
+ * itmpc_read_status() returns. */
+itmpc_status itmpc_iterate(itmpc_ctx *ctx, const float *x0, const float *U, uint64_t iter, float *U_out,
+                           float *weights, float *costs);
+
+/* itmpc_iterate on HOST buffers: copies x0 and U to the device, runs the
+ * iteration, copies U_out (and weights/costs when non-NULL) back and waits.
+ * Returns the device-side status as well (e.g. ITMPC_ERR_NONFINITE). */
+itmpc_status itmpc_iterate_host(itmpc_ctx *ctx, const float *x0, const float *U, uint64_t iter, float *U_out,
+                                float *weights, float *costs);
+
+/* Wait for the context's stream and return the device-side status of the
+ * last iteration (ITMPC_OK or ITMPC_ERR_NONFINITE), then clear it. */
+itmpc_status itmpc_read_status(itmpc_ctx *ctx);
+
+/* Copy the last iteration's diagnostics to host (waits for the stream):
+ * out[0] rho = min_k S_k, out[1] eta~ = sum_k exp(-(S_k - rho)/lambda),
+ * out[2] effective sample size 1 / sum_k w_k^2, out[3] free energy estimate
+ * -lambda log((1/K) sum_k exp(-S_k/lambda)) (Sec. II, "Free-Energy"),
+ * out[4] number of finite costs, out[5..7] reserved. */
+itmpc_status itmpc_get_stats(itmpc_ctx *ctx, float out[ITMPC_STATS_LEN]);
+
+/* Diagnostics for stage-wise checks.
+ * itmpc_noise: eps of iteration iter for every (k, t), device K x T x 2.
+ * itmpc_rollout_states: the full rollout of samples 0..n-1 (device,
+ *   n x (T+1) x 7, states x_0..x_T) plus all costs (device, K); n <= K. */
+itmpc_status itmpc_noise(itmpc_ctx *ctx, uint64_t iter, float *eps);
+itmpc_status itmpc_rollout_states(itmpc_ctx *ctx, const float *x0, const float *U, uint64_t iter, int32_t n,
+                                  float *states, float *costs);
+
+/* Raw Philox-4x32-10 blocks: out[i] = Philox(ctr[i], key) for i < n.
+ * ctr, out: device, n x 4 uint32; key: host, 2 words.  stream: cudaStream_t. */
+itmpc_status itmpc_philox4x32_10(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int64_t n,
+                                 void *stream);
+
+/* The rollout's FP32 tanh applied elementwise (device x, y of n floats), for
+ * accuracy checks of the kernel's activation against a reference tanh. */
+itmpc_status itmpc_tanh_f32(const float *x, float *y, int64_t n, void *stream);
+
+/* Merge per-shard partial sums of one iteration whose K samples were split
+ * into n_shards disjoint sets (e.g. one per GPU).  Host memory only; no GPU
+ * needed.  Shard s contributes the record partials[s * (8 + 2T) ...]:
+ *   [0] rho_s = min S over the shard, [1] eta_s = sum exp(-(S - rho_s)/lambda),
+ *   [2] the same sum over importance samples only, [3] sum of squared terms,
+ *   [4] finite count, [5..7] unused, [8 + 2t + i] sum e * eps_{t,i}.
+ * U_out (T x 2, may alias U) = U * eta_imp/eta + E/eta after rescaling every
+ * shard by exp(-(rho_s - rho)/lambda), rho = min rho_s (log-sum-exp merge).
+ * Returns ITMPC_ERR_NONFINITE (U copied) when no shard has a finite cost. */
+itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *partials, const float *U,
+                                  float lambda, float *U_out);
+
+/* Message for the last failing call on ctx (never NULL). */
+const char *itmpc_last_error(const itmpc_ctx *ctx);
+
+/* Name of a status code. */
+const char *itmpc_status_string(int32_t status);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int32_t itmpc_version(void);
+
+/* Release every resource of the context (waits for its stream). NULL is a no-op. */
+void itmpc_destroy(itmpc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ITMPC_H */

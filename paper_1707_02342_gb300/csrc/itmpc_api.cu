@@ -1,0 +1,451 @@
+// itmpc_api.cu -- the C ABI of include/itmpc.h: argument checks, context-owned
+// device memory, launches.  All arithmetic of the iteration is in the kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "itmpc.h"
+#include "itmpc_internal.h"
+
+using namespace itmpc;
+
+struct itmpc_ctx {
+  itmpc_config cfg{};
+  int K_cap = 0, T_max = 0, H = 0, device = -1;
+  cudaStream_t stream = nullptr;
+  float *net = nullptr;
+  bool have_net = false;
+  float *map = nullptr;
+  int map_w = 0, map_h = 0;
+  float res = 1.f, origin_x = 0.f, origin_y = 0.f;
+  bool have_map = false;
+  float *partials = nullptr, *scale = nullptr, *costs = nullptr, *stats = nullptr;
+  unsigned int *counter = nullptr;
+  int *status = nullptr;
+  // device staging for the host-pointer entry point
+  float *x0_d = nullptr, *U_d = nullptr, *Uout_d = nullptr, *w_d = nullptr;
+  int max_ctas = 0;
+  size_t smem_optin = 0;
+  std::string err;
+};
+
+namespace {
+
+const char *kNoCtx = "no context";
+
+itmpc_status fail(itmpc_ctx *c, itmpc_status st, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return st;
+}
+
+itmpc_status cuda_fail(itmpc_ctx *c, cudaError_t e, const char *what) {
+  cudaGetLastError();  // clear a sticky-free error so later calls are not affected
+  return fail(c, e == cudaErrorMemoryAllocation ? ITMPC_ERR_OOM : ITMPC_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(c, call, what)                         \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+bool finite(float v) { return isfinite(v) != 0; }
+
+// Host-side validation of a configuration (no CUDA calls).
+itmpc_status check_config(const itmpc_config *cfg, char *msg, size_t n) {
+  if (!cfg) { snprintf(msg, n, "cfg is NULL"); return ITMPC_ERR_ARG; }
+  const int T_max = cfg->T_max > 0 ? cfg->T_max : cfg->T;
+  if (cfg->K < 1 || cfg->K > ITMPC_MAX_K) { snprintf(msg, n, "K=%d outside [1, %d]", cfg->K, ITMPC_MAX_K); return ITMPC_ERR_ARG; }
+  if (cfg->T < 1 || T_max > ITMPC_MAX_T || cfg->T > T_max) {
+    snprintf(msg, n, "T=%d / T_max=%d outside 1 <= T <= T_max <= %d", cfg->T, cfg->T_max, ITMPC_MAX_T);
+    return ITMPC_ERR_ARG;
+  }
+  if (cfg->hidden != 32 && cfg->hidden != 64 && cfg->hidden != 128) {
+    snprintf(msg, n, "hidden=%d not one of 32, 64, 128", cfg->hidden);
+    return ITMPC_ERR_ARG;
+  }
+  if (!(cfg->lambda > 0.f) || !finite(cfg->lambda)) { snprintf(msg, n, "lambda must be finite and > 0"); return ITMPC_ERR_ARG; }
+  if (!finite(cfg->dt) || !finite(cfg->gamma)) { snprintf(msg, n, "dt and gamma must be finite"); return ITMPC_ERR_ARG; }
+  if (!(cfg->alpha_explore >= 0.f && cfg->alpha_explore <= 1.f)) { snprintf(msg, n, "alpha_explore outside [0, 1]"); return ITMPC_ERR_ARG; }
+  for (int i = 0; i < 2; ++i) {
+    if (!(cfg->sigma[i] >= 0.f) || !finite(cfg->sigma[i])) { snprintf(msg, n, "sigma[%d] must be finite and >= 0", i); return ITMPC_ERR_ARG; }
+    if (!(cfg->u_min[i] <= cfg->u_max[i])) { snprintf(msg, n, "u_min[%d] > u_max[%d]", i, i); return ITMPC_ERR_ARG; }
+  }
+  if (cfg->gamma != 0.f && (cfg->sigma[0] == 0.f || cfg->sigma[1] == 0.f)) {
+    snprintf(msg, n, "gamma != 0 needs sigma > 0 (Sigma^-1 in the control cost)");
+    return ITMPC_ERR_ARG;
+  }
+  for (int i = 0; i < 4; ++i)
+    if (!finite(cfg->cost_w[i])) { snprintf(msg, n, "cost_w[%d] not finite", i); return ITMPC_ERR_ARG; }
+  if (!(cfg->crash_decay > 0.f) || !finite(cfg->crash_decay)) { snprintf(msg, n, "crash_decay must be > 0"); return ITMPC_ERR_ARG; }
+  if (cfg->precision != ITMPC_FP32) { snprintf(msg, n, "precision %d not supported by this entry point", cfg->precision); return ITMPC_ERR_ARG; }
+  if (cfg->activation != ITMPC_ACT_TANH && cfg->activation != ITMPC_ACT_IDENTITY) { snprintf(msg, n, "bad activation"); return ITMPC_ERR_ARG; }
+  return ITMPC_OK;
+}
+
+IterParams make_params(const itmpc_ctx *c) {
+  const itmpc_config &g = c->cfg;
+  IterParams p{};
+  p.K = g.K;
+  p.T = g.T;
+  p.H = c->H;
+  p.activation = g.activation;
+  // Alg. 1: sample k is centred on U iff k < (1 - alpha) K, i.e. k < ceil((1 - alpha) K)
+  double nimp = ceil((1.0 - (double)g.alpha_explore) * (double)g.K);
+  p.n_imp = (int)(nimp < 0 ? 0 : (nimp > g.K ? g.K : nimp));
+  p.key0 = (uint32_t)g.seed;
+  p.key1 = (uint32_t)(g.seed >> 32);
+  p.sigma0 = g.sigma[0];
+  p.sigma1 = g.sigma[1];
+  p.dt = g.dt;
+  p.umin0 = g.u_min[0]; p.umin1 = g.u_min[1];
+  p.umax0 = g.u_max[0]; p.umax1 = g.u_max[1];
+  p.w_track = g.cost_w[0]; p.w_speed = g.cost_w[1]; p.w_stab = g.cost_w[2]; p.w_crash = g.cost_w[3];
+  p.v_des = g.v_des;
+  p.crash_cost = g.crash_cost;
+  p.log2_decay = (float)log2((double)g.crash_decay);
+  p.track_thresh = g.track_thresh;
+  p.slip_thresh = g.slip_thresh;
+  p.map_cap = g.map_cap;
+  p.gamma = g.gamma;
+  p.inv_sig2_0 = g.sigma[0] > 0 ? (float)(1.0 / ((double)g.sigma[0] * g.sigma[0])) : 0.f;
+  p.inv_sig2_1 = g.sigma[1] > 0 ? (float)(1.0 / ((double)g.sigma[1] * g.sigma[1])) : 0.f;
+  p.lambda = g.lambda;
+  p.inv_lambda = (float)(1.0 / (double)g.lambda);
+  p.map = c->map;
+  p.map_w = c->map_w;
+  p.map_h = c->map_h;
+  p.inv_res = (float)(1.0 / (double)c->res);
+  p.origin_x = c->origin_x;
+  p.origin_y = c->origin_y;
+  p.net = c->net;
+  p.costs = c->costs;
+  p.partials = c->partials;
+  p.scale = c->scale;
+  p.counter = c->counter;
+  p.stats = c->stats;
+  p.status = c->status;
+  return p;
+}
+
+void set_iter(IterParams &p, uint64_t iter, uint32_t instance) {
+  p.ctr2 = (uint32_t)iter;
+  p.ctr3 = (uint32_t)((iter >> 32) & 0xFFFFu) | (instance << 16);
+}
+
+itmpc_status ready(itmpc_ctx *c) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (!c->have_net) return fail(c, ITMPC_ERR_STATE, "itmpc_set_dynamics has not been called");
+  if (!c->have_map) return fail(c, ITMPC_ERR_STATE, "itmpc_set_costmap has not been called");
+  return ITMPC_OK;
+}
+
+itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
+                           float *weights, float *costs, float *states, int n_states, float *eps_out) {
+  IterParams p = make_params(c);
+  set_iter(p, iter, c->cfg.instance);
+  p.x0 = x0;
+  p.U = U;
+  p.U_out = U_out;
+  p.weights = weights;
+  p.weights_inline = c->cfg.K <= 16384;
+  p.states_out = states;
+  p.n_states = n_states;
+  p.eps_out = eps_out;
+  if (costs) p.costs = costs;  // write S_k straight into the caller's buffer
+  const Fp32Tile tile = fp32_pick_tile(p.K, p.H);
+  CK(c, fp32_launch_iterate(p, tile, c->stream), "fused FP32 iteration launch");
+  if (weights && !p.weights_inline) CK(c, launch_finalize_weights(p, c->stream), "weights launch");
+  return ITMPC_OK;
+}
+
+void free_ctx(itmpc_ctx *c) {
+  float *bufs[] = {c->net, c->map, c->partials, c->scale, c->costs, c->stats, c->x0_d, c->U_d, c->Uout_d, c->w_d};
+  for (float *b : bufs)
+    if (b) cudaFree(b);
+  if (c->counter) cudaFree(c->counter);
+  if (c->status) cudaFree(c->status);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
+  if (!out) return ITMPC_ERR_ARG;
+  *out = nullptr;
+  char msg[256];
+  itmpc_status st = check_config(cfg, msg, sizeof msg);
+  if (st != ITMPC_OK) return st;
+  itmpc_ctx *c = new itmpc_ctx();
+  c->cfg = *cfg;
+  c->K_cap = cfg->K;
+  c->T_max = cfg->T_max > 0 ? cfg->T_max : cfg->T;
+  c->cfg.T_max = c->T_max;
+  c->H = cfg->hidden;
+  c->stream = (cudaStream_t)cfg->stream;
+  auto bail = [&](cudaError_t e, const char *what) {
+    cudaGetLastError();
+    free_ctx(c);
+    return e == cudaErrorMemoryAllocation ? ITMPC_ERR_OOM : ITMPC_ERR_CUDA;
+    (void)what;
+  };
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return bail(e, "cudaGetDevice");
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (e != cudaSuccess) return bail(e, "attribute");
+  c->smem_optin = (size_t)optin;
+  const Fp32Tile tile = fp32_pick_tile(c->K_cap, c->H);
+  if (fp32_smem_bytes(c->T_max, c->H, tile) > c->smem_optin) {
+    free_ctx(c);
+    return ITMPC_ERR_ARG;
+  }
+  c->max_ctas = fp32_num_ctas(c->K_cap, tile);
+  const size_t PL = (size_t)partial_len(c->T_max);
+  struct { float **p; size_t n; } allocs[] = {
+      {&c->net, (size_t)net_floats(c->H)}, {&c->partials, PL * c->max_ctas}, {&c->scale, (size_t)c->max_ctas},
+      {&c->costs, (size_t)c->K_cap},       {&c->stats, ITMPC_STATS_LEN},     {&c->x0_d, 8},
+      {&c->U_d, 2 * (size_t)c->T_max},     {&c->Uout_d, 2 * (size_t)c->T_max}, {&c->w_d, (size_t)c->K_cap}};
+  for (auto &a : allocs) {
+    e = cudaMalloc((void **)a.p, sizeof(float) * a.n);
+    if (e != cudaSuccess) return bail(e, "cudaMalloc");
+  }
+  e = cudaMalloc((void **)&c->counter, sizeof(unsigned int));
+  if (e != cudaSuccess) return bail(e, "cudaMalloc");
+  e = cudaMalloc((void **)&c->status, sizeof(int));
+  if (e != cudaSuccess) return bail(e, "cudaMalloc");
+  e = cudaMemset(c->counter, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(float) * ITMPC_STATS_LEN);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return bail(e, "init");
+  *out = c;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_set_config(itmpc_ctx *c, const itmpc_config *cfg) {
+  if (!c) return ITMPC_ERR_ARG;
+  char msg[256];
+  itmpc_status st = check_config(cfg, msg, sizeof msg);
+  if (st != ITMPC_OK) return fail(c, st, "%s", msg);
+  if (cfg->K > c->K_cap) return fail(c, ITMPC_ERR_ARG, "K=%d exceeds the K=%d the context was created for", cfg->K, c->K_cap);
+  if (cfg->T > c->T_max) return fail(c, ITMPC_ERR_ARG, "T=%d exceeds T_max=%d", cfg->T, c->T_max);
+  if (cfg->hidden != c->H) return fail(c, ITMPC_ERR_ARG, "hidden width cannot change (%d -> %d)", c->H, cfg->hidden);
+  const int T_max = c->T_max;
+  c->cfg = *cfg;
+  c->cfg.T_max = T_max;
+  c->stream = (cudaStream_t)cfg->stream;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_set_stream(itmpc_ctx *c, void *stream) {
+  if (!c) return ITMPC_ERR_ARG;
+  c->stream = (cudaStream_t)stream;
+  c->cfg.stream = stream;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_set_dynamics(itmpc_ctx *c, int32_t n_layers, const int32_t *widths, const float *const *W,
+                                const float *const *b, int32_t on_device) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (n_layers != 3 || !widths || !W || !b) return fail(c, ITMPC_ERR_ARG, "need n_layers == 3 and non-NULL arrays");
+  const int H = c->H;
+  if (widths[0] != 6 || widths[1] != H || widths[2] != H || widths[3] != 4)
+    return fail(c, ITMPC_ERR_ARG, "widths must be {6, %d, %d, 4}", H, H);
+  for (int l = 0; l < 3; ++l)
+    if (!W[l] || !b[l]) return fail(c, ITMPC_ERR_ARG, "layer %d pointer is NULL", l);
+  const size_t nW[3] = {(size_t)6 * H, (size_t)H * H, (size_t)4 * H};
+  const size_t nb[3] = {(size_t)H, (size_t)H, 4};
+  const size_t offW[3] = {(size_t)net_off_W1(H), (size_t)net_off_W2(H), (size_t)net_off_W3(H)};
+  const size_t offb[3] = {(size_t)net_off_b1(H), (size_t)net_off_b2(H), (size_t)net_off_b3(H)};
+  for (int l = 0; l < 3; ++l) {
+    if (on_device) {
+      CK(c, cudaMemcpyAsync(c->net + offW[l], W[l], sizeof(float) * nW[l], cudaMemcpyDeviceToDevice, c->stream), "W copy");
+      CK(c, cudaMemcpyAsync(c->net + offb[l], b[l], sizeof(float) * nb[l], cudaMemcpyDeviceToDevice, c->stream), "b copy");
+    } else {
+      CK(c, cudaMemcpyAsync(c->net + offW[l], W[l], sizeof(float) * nW[l], cudaMemcpyHostToDevice, c->stream), "W copy");
+      CK(c, cudaMemcpyAsync(c->net + offb[l], b[l], sizeof(float) * nb[l], cudaMemcpyHostToDevice, c->stream), "b copy");
+    }
+  }
+  if (!on_device) CK(c, cudaStreamSynchronize(c->stream), "sync");
+  c->have_net = true;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_set_costmap(itmpc_ctx *c, const float *map, int32_t width, int32_t height, float res,
+                               float origin_x, float origin_y, int32_t on_device) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (!map || width < 1 || height < 1 || (int64_t)width * height > (int64_t)1 << 30)
+    return fail(c, ITMPC_ERR_ARG, "bad costmap shape %d x %d", width, height);
+  if (!(res > 0.f) || !finite(res) || !finite(origin_x) || !finite(origin_y))
+    return fail(c, ITMPC_ERR_ARG, "res must be finite and > 0, origin finite");
+  const size_t n = (size_t)width * height;
+  if (!c->map || (size_t)c->map_w * c->map_h != n) {
+    if (c->map) {
+      CK(c, cudaStreamSynchronize(c->stream), "sync");
+      cudaFree(c->map);
+      c->map = nullptr;
+      c->have_map = false;
+    }
+    CK(c, cudaMalloc((void **)&c->map, sizeof(float) * n), "costmap cudaMalloc");
+  }
+  CK(c, cudaMemcpyAsync(c->map, map, sizeof(float) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        c->stream), "costmap copy");
+  if (!on_device) CK(c, cudaStreamSynchronize(c->stream), "sync");
+  c->map_w = width;
+  c->map_h = height;
+  c->res = res;
+  c->origin_x = origin_x;
+  c->origin_y = origin_y;
+  c->have_map = true;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_iterate(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
+                           float *weights, float *costs) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (!x0 || !U || !U_out) return fail(c, ITMPC_ERR_ARG, "x0, U and U_out must be non-NULL");
+  return run_iteration(c, x0, U, iter, U_out, weights, costs, nullptr, 0, nullptr);
+}
+
+itmpc_status itmpc_iterate_host(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
+                                float *weights, float *costs) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (!x0 || !U || !U_out) return fail(c, ITMPC_ERR_ARG, "x0, U and U_out must be non-NULL");
+  for (int i = 0; i < 7; ++i)
+    if (!finite(x0[i])) return fail(c, ITMPC_ERR_ARG, "x0[%d] is not finite", i);
+  const int T = c->cfg.T, K = c->cfg.K;
+  CK(c, cudaMemcpyAsync(c->x0_d, x0, sizeof(float) * 7, cudaMemcpyHostToDevice, c->stream), "x0 copy");
+  CK(c, cudaMemcpyAsync(c->U_d, U, sizeof(float) * 2 * T, cudaMemcpyHostToDevice, c->stream), "U copy");
+  st = run_iteration(c, c->x0_d, c->U_d, iter, c->Uout_d, weights ? c->w_d : nullptr, nullptr, nullptr, 0, nullptr);
+  if (st != ITMPC_OK) return st;
+  CK(c, cudaMemcpyAsync(U_out, c->Uout_d, sizeof(float) * 2 * T, cudaMemcpyDeviceToHost, c->stream), "U_out copy");
+  if (weights) CK(c, cudaMemcpyAsync(weights, c->w_d, sizeof(float) * K, cudaMemcpyDeviceToHost, c->stream), "w copy");
+  if (costs) CK(c, cudaMemcpyAsync(costs, c->costs, sizeof(float) * K, cudaMemcpyDeviceToHost, c->stream), "S copy");
+  return itmpc_read_status(c);
+}
+
+itmpc_status itmpc_read_status(itmpc_ctx *c) {
+  if (!c) return ITMPC_ERR_ARG;
+  int s = 0;
+  CK(c, cudaMemcpyAsync(&s, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status copy");
+  CK(c, cudaStreamSynchronize(c->stream), "sync");
+  if (s != 0) {
+    CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "status reset");
+    CK(c, cudaStreamSynchronize(c->stream), "sync");
+    if (s == ITMPC_ERR_NONFINITE) return fail(c, ITMPC_ERR_NONFINITE, "every rollout cost was non-finite; U unchanged");
+    return fail(c, (itmpc_status)s, "device status %d", s);
+  }
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_get_stats(itmpc_ctx *c, float out[ITMPC_STATS_LEN]) {
+  if (!c || !out) return ITMPC_ERR_ARG;
+  CK(c, cudaMemcpyAsync(out, c->stats, sizeof(float) * ITMPC_STATS_LEN, cudaMemcpyDeviceToHost, c->stream), "stats copy");
+  CK(c, cudaStreamSynchronize(c->stream), "sync");
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_noise(itmpc_ctx *c, uint64_t iter, float *eps) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (!eps) return fail(c, ITMPC_ERR_ARG, "eps is NULL");
+  IterParams p = make_params(c);
+  set_iter(p, iter, c->cfg.instance);
+  CK(c, launch_noise(p, eps, c->stream), "noise launch");
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_rollout_states(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, int32_t n,
+                                  float *states, float *costs) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (!x0 || !U || !states || n < 0 || n > c->cfg.K) return fail(c, ITMPC_ERR_ARG, "bad rollout_states arguments");
+  return run_iteration(c, x0, U, iter, c->Uout_d, nullptr, costs, states, n, nullptr);
+}
+
+itmpc_status itmpc_philox4x32_10(const uint32_t *ctr, const uint32_t key[2], uint32_t *out, int64_t n, void *stream) {
+  if (!ctr || !key || !out || n < 0) return ITMPC_ERR_ARG;
+  cudaError_t e = launch_philox(ctr, key[0], key[1], out, n, (cudaStream_t)stream);
+  if (e != cudaSuccess) { cudaGetLastError(); return ITMPC_ERR_CUDA; }
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_tanh_f32(const float *x, float *y, int64_t n, void *stream) {
+  if (!x || !y || n < 0) return ITMPC_ERR_ARG;
+  cudaError_t e = launch_tanh(x, y, n, (cudaStream_t)stream);
+  if (e != cudaSuccess) { cudaGetLastError(); return ITMPC_ERR_CUDA; }
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *partials, const float *U, float lambda,
+                                  float *U_out) {
+  if (n_shards < 1 || T < 1 || !partials || !U || !U_out || !(lambda > 0.f)) return ITMPC_ERR_ARG;
+  const int PL = partial_len(T);
+  double rho = INFINITY;
+  for (int s = 0; s < n_shards; ++s) {
+    const double r = partials[(size_t)s * PL];
+    if (isfinite(r) && r < rho) rho = r;
+  }
+  if (!isfinite(rho)) {
+    for (int o = 0; o < 2 * T; ++o) U_out[o] = U[o];
+    return ITMPC_ERR_NONFINITE;
+  }
+  double eta = 0.0, eta_imp = 0.0;
+  for (int s = 0; s < n_shards; ++s) {
+    const float *r = partials + (size_t)s * PL;
+    const double sc = isfinite(r[0]) ? exp(-((double)r[0] - rho) / lambda) : 0.0;
+    eta += sc * r[1];
+    eta_imp += sc * r[2];
+  }
+  for (int o = 0; o < 2 * T; ++o) {
+    double E = 0.0;
+    for (int s = 0; s < n_shards; ++s) {
+      const float *r = partials + (size_t)s * PL;
+      const double sc = isfinite(r[0]) ? exp(-((double)r[0] - rho) / lambda) : 0.0;
+      E += sc * r[8 + o];
+    }
+    U_out[o] = (float)((double)U[o] * (eta_imp / eta) + E / eta);
+  }
+  return ITMPC_OK;
+}
+
+const char *itmpc_last_error(const itmpc_ctx *c) { return c ? c->err.c_str() : kNoCtx; }
+
+const char *itmpc_status_string(int32_t s) {
+  switch (s) {
+    case ITMPC_OK: return "ITMPC_OK";
+    case ITMPC_ERR_ARG: return "ITMPC_ERR_ARG";
+    case ITMPC_ERR_CUDA: return "ITMPC_ERR_CUDA";
+    case ITMPC_ERR_NONFINITE: return "ITMPC_ERR_NONFINITE";
+    case ITMPC_ERR_TIMEOUT: return "ITMPC_ERR_TIMEOUT";
+    case ITMPC_ERR_STATE: return "ITMPC_ERR_STATE";
+    case ITMPC_ERR_OOM: return "ITMPC_ERR_OOM";
+    default: return "unknown status";
+  }
+}
+
+int32_t itmpc_version(void) { return 100; }
+
+void itmpc_destroy(itmpc_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+}  // extern "C"

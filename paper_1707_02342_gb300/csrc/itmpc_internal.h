@@ -1,0 +1,74 @@
+// itmpc_internal.h -- shared between the C-ABI layer and the kernels (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace itmpc {
+
+// Packed network layout (floats): W1 [H][6], b1 [H], W2 [H][H], b2 [H], W3 [4][H], b3 [4].
+__host__ __device__ constexpr int net_off_W1(int) { return 0; }
+__host__ __device__ constexpr int net_off_b1(int H) { return 6 * H; }
+__host__ __device__ constexpr int net_off_W2(int H) { return 7 * H; }
+__host__ __device__ constexpr int net_off_b2(int H) { return 7 * H + H * H; }
+__host__ __device__ constexpr int net_off_W3(int H) { return 8 * H + H * H; }
+__host__ __device__ constexpr int net_off_b3(int H) { return 12 * H + H * H; }
+__host__ __device__ constexpr int net_floats(int H) { return 12 * H + H * H + 4; }
+
+// One partial record per CTA: [rho, eta, eta_imp, sum e^2, n_finite, -, -, -, E[T][2]].
+__host__ __device__ constexpr int partial_len(int T) { return 8 + 2 * T; }
+
+// Everything one fused iteration launch needs.  Built on the host per call.
+struct IterParams {
+  int K, T, n_imp, H;
+  int activation;
+  // noise: counter words 2 and 3, key words 0 and 1
+  uint32_t ctr2, ctr3, key0, key1;
+  float sigma0, sigma1;
+  // dynamics
+  float dt, umin0, umin1, umax0, umax1;
+  // cost
+  float w_track, w_speed, w_stab, w_crash;
+  float v_des, crash_cost, log2_decay, track_thresh, slip_thresh, map_cap;
+  float gamma, inv_sig2_0, inv_sig2_1;
+  float lambda, inv_lambda;
+  // map
+  const float *map;
+  int map_w, map_h;
+  float inv_res, origin_x, origin_y;
+  // network (packed, device)
+  const float *net;
+  // inputs
+  const float *x0, *U;
+  // outputs and scratch
+  float *U_out;
+  float *weights;      // may be null
+  float *costs;        // never null (context buffer when the caller gives none)
+  float *partials;     // n_cta x partial_len(T)
+  float *scale;        // n_cta
+  unsigned int *counter;
+  float *stats;        // ITMPC_STATS_LEN
+  int *status;
+  int weights_inline;  // last CTA writes the weights itself
+  // debug outputs (null in the hot path)
+  float *eps_out;      // K x T x 2
+  float *states_out;   // n_states x (T+1) x 7
+  int n_states;
+};
+
+// Tile shape of the FP32 fused kernel.
+struct Fp32Tile {
+  int spw;     // samples per warp
+  int nwarps;  // warps per CTA
+};
+
+Fp32Tile fp32_pick_tile(int K, int H);
+size_t fp32_smem_bytes(int T, int H, Fp32Tile tile);
+int fp32_num_ctas(int K, Fp32Tile tile);
+cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t s);
+cudaError_t launch_finalize_weights(const IterParams &p, cudaStream_t s);
+cudaError_t launch_noise(const IterParams &p, float *eps, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);
+cudaError_t launch_tanh(const float *x, float *y, int64_t n, cudaStream_t s);
+
+}  // namespace itmpc

@@ -1,0 +1,250 @@
+"""Thin ctypes binding of libitmpc.so (C ABI in include/itmpc.h).
+
+Only argument marshalling lives here: every step of the control iteration runs
+in the library's CUDA kernels.  PyTorch supplies device memory and streams;
+tensors are passed as raw device pointers.  Loading fails loudly when the
+library has not been built -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libitmpc.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_OOM = 0, -1, -2, -3, -4, -5, -6
+FP32, BF16, FP8 = 0, 1, 2
+ACT_TANH, ACT_IDENTITY = 0, 1
+MAX_K, MAX_T, STATS_LEN = 1 << 24, 512, 8
+
+# Every function the header declares, with (restype, argtypes).
+_vp, _i32, _i64, _u64, _f = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float
+
+
+class Config(C.Structure):
+    """Mirror of itmpc_config."""
+    _fields_ = [
+        ("K", C.c_int32), ("T", C.c_int32), ("T_max", C.c_int32), ("hidden", C.c_int32),
+        ("dt", C.c_float), ("lam", C.c_float), ("gamma", C.c_float), ("alpha_explore", C.c_float),
+        ("sigma", C.c_float * 2), ("u_min", C.c_float * 2), ("u_max", C.c_float * 2),
+        ("cost_w", C.c_float * 4),
+        ("v_des", C.c_float), ("crash_cost", C.c_float), ("crash_decay", C.c_float),
+        ("track_thresh", C.c_float), ("slip_thresh", C.c_float), ("map_cap", C.c_float),
+        ("seed", C.c_uint64), ("instance", C.c_uint32), ("precision", C.c_int32),
+        ("activation", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p),
+    ]
+
+
+SIGNATURES = {
+    "itmpc_create": (C.c_int, [C.POINTER(Config), C.POINTER(C.c_void_p)]),
+    "itmpc_set_config": (C.c_int, [_vp, C.POINTER(Config)]),
+    "itmpc_set_stream": (C.c_int, [_vp, _vp]),
+    "itmpc_set_dynamics": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i32]),
+    "itmpc_set_costmap": (C.c_int, [_vp, _vp, _i32, _i32, _f, _f, _f, _i32]),
+    "itmpc_iterate": (C.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp]),
+    "itmpc_iterate_host": (C.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp]),
+    "itmpc_read_status": (C.c_int, [_vp]),
+    "itmpc_get_stats": (C.c_int, [_vp, _vp]),
+    "itmpc_noise": (C.c_int, [_vp, _u64, _vp]),
+    "itmpc_rollout_states": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _vp, _vp]),
+    "itmpc_philox4x32_10": (C.c_int, [_vp, _vp, _vp, _i64, _vp]),
+    "itmpc_tanh_f32": (C.c_int, [_vp, _vp, _i64, _vp]),
+    "itmpc_merge_partials": (C.c_int, [_i32, _i32, _vp, _vp, _f, _vp]),
+    "itmpc_last_error": (C.c_char_p, [_vp]),
+    "itmpc_status_string": (C.c_char_p, [_i32]),
+    "itmpc_version": (C.c_int32, []),
+    "itmpc_destroy": (None, [_vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libitmpc.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; run paper_1707_02342_gb300.build.build() (nvcc, sm_103a)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class ItmpcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+def status_string(s: int) -> str:
+    return lib().itmpc_status_string(int(s)).decode()
+
+
+def make_config(K: int, T: int, *, T_max: int = 0, hidden: int = 32, dt=0.02, lam=1.0, gamma=0.0,
+                alpha_explore=0.0, sigma=(0.3, 0.35), u_min=(-1.0, -1.0), u_max=(1.0, 1.0),
+                cost_w=(1.0, 1.0, 1.0, 0.0), v_des=6.0, crash_cost=1e4, crash_decay=0.9, track_thresh=0.99,
+                slip_thresh=0.75, map_cap=2.5, seed=0x170702342, instance=0, precision=FP32,
+                activation=ACT_TANH, stream=None) -> Config:
+    c = Config()
+    c.K, c.T, c.T_max, c.hidden = K, T, T_max, hidden
+    c.dt, c.lam, c.gamma, c.alpha_explore = dt, lam, gamma, alpha_explore
+    c.sigma[:] = list(sigma)
+    c.u_min[:] = list(u_min)
+    c.u_max[:] = list(u_max)
+    c.cost_w[:] = list(cost_w)
+    c.v_des, c.crash_cost, c.crash_decay = v_des, crash_cost, crash_decay
+    c.track_thresh, c.slip_thresh, c.map_cap = track_thresh, slip_thresh, map_cap
+    c.seed, c.instance, c.precision, c.activation = seed & (2 ** 64 - 1), instance, precision, activation
+    c.stream = stream
+    return c
+
+
+def _dptr(t) -> int:
+    """Device pointer of a contiguous float32/uint32 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Controller:
+    """One IT-MPC context (itmpc_ctx) on the current CUDA device.
+
+    Parameters are those of ``make_config``; ``stream`` is a torch.cuda.Stream
+    (default: the current stream at construction).
+    """
+
+    def __init__(self, K: int, T: int, stream=None, **kw):
+        self._L = lib()
+        self.stream = stream
+        self.cfg = make_config(K, T, stream=_stream_handle(stream), **kw)
+        h = C.c_void_p()
+        st = self._L.itmpc_create(C.byref(self.cfg), C.byref(h))
+        if st != OK:
+            raise ItmpcError(st, "itmpc_create failed (bad config or no usable CUDA device)")
+        self._h = h
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, st: int):
+        if st != OK:
+            raise ItmpcError(st, self._L.itmpc_last_error(self._h).decode())
+
+    @property
+    def K(self) -> int:
+        return self.cfg.K
+
+    @property
+    def T(self) -> int:
+        return self.cfg.T
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.itmpc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI ------------------------------------------------------------------
+    def set_config(self, **kw):
+        d = {f: getattr(self.cfg, f) for f, _ in Config._fields_}
+        cfg = make_config(d.pop("K"), d.pop("T"), T_max=d.pop("T_max"), hidden=d.pop("hidden"),
+                          dt=d.pop("dt"), lam=d.pop("lam"), gamma=d.pop("gamma"),
+                          alpha_explore=d.pop("alpha_explore"), sigma=tuple(d.pop("sigma")),
+                          u_min=tuple(d.pop("u_min")), u_max=tuple(d.pop("u_max")),
+                          cost_w=tuple(d.pop("cost_w")), v_des=d.pop("v_des"), crash_cost=d.pop("crash_cost"),
+                          crash_decay=d.pop("crash_decay"), track_thresh=d.pop("track_thresh"),
+                          slip_thresh=d.pop("slip_thresh"), map_cap=d.pop("map_cap"), seed=d.pop("seed"),
+                          instance=d.pop("instance"), precision=d.pop("precision"),
+                          activation=d.pop("activation"), stream=d.pop("stream"))
+        for k, v in kw.items():
+            if k in ("sigma", "u_min", "u_max", "cost_w"):
+                getattr(cfg, k)[:] = list(v)
+            else:
+                setattr(cfg, k, v)
+        self._check(self._L.itmpc_set_config(self._h, C.byref(cfg)))
+        self.cfg = cfg
+
+    def set_dynamics(self, layers):
+        """layers: three (W, b) CUDA float32 tensors, W of shape (fan_out, fan_in)."""
+        H = self.cfg.hidden
+        widths = (C.c_int32 * 4)(6, H, H, 4)
+        Ws = (C.c_void_p * 3)(*[_dptr(W) for W, _ in layers])
+        bs = (C.c_void_p * 3)(*[_dptr(b) for _, b in layers])
+        self._check(self._L.itmpc_set_dynamics(self._h, 3, widths, Ws, bs, 1))
+
+    def set_costmap(self, cmap, res: float, origin_x: float, origin_y: float):
+        """cmap: (height, width) CUDA float32 tensor."""
+        h, w = cmap.shape
+        self._check(self._L.itmpc_set_costmap(self._h, _dptr(cmap), w, h, res, origin_x, origin_y, 1))
+
+    def iterate(self, x0, U, it: int, U_out, weights=None, costs=None):
+        """Queue one iteration on the context's stream (device tensors)."""
+        self._check(self._L.itmpc_iterate(self._h, _dptr(x0), _dptr(U), it, _dptr(U_out), _dptr(weights),
+                                          _dptr(costs)))
+
+    def iterate_host(self, x0, U, it: int, U_out, weights=None, costs=None) -> int:
+        """One synchronous iteration on host numpy float32 arrays; returns the status."""
+        def p(a):
+            return None if a is None else a.ctypes.data
+        st = self._L.itmpc_iterate_host(self._h, p(x0), p(U), it, p(U_out), p(weights), p(costs))
+        if st not in (OK, ERR_NONFINITE):
+            self._check(st)
+        return st
+
+    def read_status(self) -> int:
+        return int(self._L.itmpc_read_status(self._h))
+
+    def stats(self):
+        out = (C.c_float * STATS_LEN)()
+        self._check(self._L.itmpc_get_stats(self._h, out))
+        return list(out)
+
+    def noise(self, it: int, eps):
+        self._check(self._L.itmpc_noise(self._h, it, _dptr(eps)))
+
+    def rollout_states(self, x0, U, it: int, n: int, states, costs=None):
+        self._check(self._L.itmpc_rollout_states(self._h, _dptr(x0), _dptr(U), it, n, _dptr(states),
+                                                 _dptr(costs)))
+
+
+def philox(ctr, key, out, stream=None):
+    st = lib().itmpc_philox4x32_10(_dptr(ctr), (C.c_uint32 * 2)(*key), _dptr(out), ctr.shape[0],
+                                   _stream_handle(stream))
+    if st != OK:
+        raise ItmpcError(st, "itmpc_philox4x32_10")
+
+
+def tanh_f32(x, y, stream=None):
+    st = lib().itmpc_tanh_f32(_dptr(x), _dptr(y), x.numel(), _stream_handle(stream))
+    if st != OK:
+        raise ItmpcError(st, "itmpc_tanh_f32")
+
+
+def merge_partials(partials, U, lam: float):
+    """Host log-sum-exp merge of per-shard partial records (numpy float32)."""
+    import numpy as np
+
+    partials = np.ascontiguousarray(partials, np.float32)
+    U = np.ascontiguousarray(U, np.float32)
+    out = np.empty_like(U)
+    T = U.shape[0]
+    st = lib().itmpc_merge_partials(partials.shape[0], T, partials.ctypes.data, U.ctypes.data, lam,
+                                    out.ctypes.data)
+    return st, out
