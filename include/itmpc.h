@@ -178,14 +178,19 @@ itmpc_status itmpc_philox4x32_10(const uint32_t *ctr, const uint32_t key[2], uin
  * accuracy checks of the kernel's activation against a reference tanh. */
 itmpc_status itmpc_tanh_f32(const float *x, float *y, int64_t n, void *stream);
 
+/* Floats per partial record for horizon T: 8 header words plus 2T sums,
+ * padded to a multiple of 4 so that every record is 16-byte aligned. */
+#define ITMPC_PARTIAL_STRIDE(T) (8 + ((2 * (T) + 3) & ~3))
+
 /* Merge per-shard partial sums of one iteration whose K samples were split
  * into n_shards disjoint sets (e.g. one per GPU).  Host memory only; no GPU
- * needed.  Shard s contributes the record partials[s * (8 + 2T) ...]:
+ * needed.  Shard s contributes the record partials[s * ITMPC_PARTIAL_STRIDE(T) ...]:
  *   [0] rho_s = min S over the shard, [1] eta_s = sum exp(-(S - rho_s)/lambda),
  *   [2] the same sum over importance samples only, [3] sum of squared terms,
  *   [4] finite count, [5..7] unused, [8 + 2t + i] sum e * eps_{t,i}.
  * U_out (T x 2, may alias U) = U * eta_imp/eta + E/eta after rescaling every
- * shard by exp(-(rho_s - rho)/lambda), rho = min rho_s (log-sum-exp merge).
+ * shard by exp(-(rho_s - rho)/lambda), rho = min rho_s (log-sum-exp merge;
+ * Alg. 2's shift by the minimum cost, applied per shard and then globally).
  * Returns ITMPC_ERR_NONFINITE (U copied) when no shard has a finite cost. */
 itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *partials, const float *U,
                                   float lambda, float *U_out);

@@ -1,23 +1,26 @@
 // iterate_fp32.cu -- fused FP32 IT-MPC control iteration for sm_103a.
 //
-// One launch performs the whole iteration of Alg. 1 / Alg. 2:
-//   phase 1  noise      eps for the CTA's samples x T steps, Philox + Box-Muller,
-//                       kept in shared memory (never written to HBM);
+// One launch performs the whole iteration of Alg. 1 / Alg. 2.  Each warp owns
+// one sample k; a CTA owns NW consecutive samples.
+//   phase 1  noise      eps and the clamped control g(v) for the CTA's samples x T
+//                       steps (Philox-4x32-10 + Box-Muller), kept in shared memory;
 //   phase 2  dynamics   the serial recurrence x_d(t+1) = x_d(t) + dt f(x_d(t), g(v_t))
-//                       (Sec. V-B).  Only x_d feeds the network, so this is the
-//                       only serial chain; a warp owns SPW samples, lane j owns
-//                       hidden neuron j (+32, +64, ...), the hidden activations
-//                       go through a per-warp shared buffer, W2 sits in registers
-//                       when H = 32;
-//   phase 3  kinematics the heading and position of Sec. V-B are prefix sums over t
-//            and cost   of dt * theta_dot and dt * R(theta) v, evaluated with warp scans
-//                       (lane = time step), followed by the state cost of Sec. V-C at
-//                       every t = 1..T and the control-cost term of Sec. III-E;
-//   phase 4  partials   per-CTA rho_c = min S, eta_c = sum e, E_c = sum e eps over the
-//                       CTA's samples, with e = exp(-(S - rho_c)/lambda) (Alg. 2);
-//   phase 5  combine    the last CTA to finish rescales every CTA's partials by
-//                       exp(-(rho_c - rho)/lambda), forms U' (Sec. III-D), the
-//                       weights, and diagnostics (log-sum-exp merge).
+//                       of Sec. V-B.  Only x_d feeds the network, so this is the one
+//                       serial chain.  Lane j owns hidden neuron j (+32, +64, ...):
+//                       layer 1 in registers, h1 broadcast through a per-warp
+//                       shared row, layer 2 as four independent FMA chains with W2
+//                       in registers (H = 32), the 4 outputs of layer 3 reduced
+//                       across the warp with a register butterfly;
+//   phase 3  kinematics heading and position are prefix sums over t of dt*theta_dot
+//            and cost   and dt*R(theta)v (warp scans, lane = time step); then the state
+//                       cost of Sec. V-C at t = 1..T plus the control-cost term of
+//                       Sec. III-E, with every costmap load of a chunk in flight;
+//   phase 4  partials   per-CTA rho_c = min S, eta_c = sum e, E_c = sum e eps with
+//                       e = exp(-(S - rho_c)/lambda) (Alg. 2);
+//   phase 5  combine    the last CTA of each group of CTAs merges the group's records
+//                       (log-sum-exp rescaling by exp(-(rho_c - rho_g)/lambda)); the
+//                       last group merger merges the group records into U' (Sec. III-D),
+//                       the weights and the diagnostics.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -31,351 +34,200 @@ namespace {
 __host__ __device__ constexpr size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
 
 struct SmemLayout {
-  size_t U, eps, traj, W3, W2T, hbuf, S, e, total;
+  size_t U, eps, gv, traj, pos, W2T, hbuf, S, e, total;
 };
 
-__host__ __device__ inline SmemLayout fp32_layout(int T, int H, int spw, int nwarps) {
-  const int scta = spw * nwarps;
+__host__ __device__ inline SmemLayout fp32_layout(int T, int H, int nw) {
   SmemLayout L{};
   size_t off = 0;
   L.U = off;    off += align16(sizeof(float) * 2 * T);
-  L.eps = off;  off += align16(sizeof(float2) * (size_t)scta * T);
-  L.traj = off; off += align16(sizeof(float4) * (size_t)scta * (T + 1));
-  L.W3 = off;   off += align16(sizeof(float) * (4 * (H + 4) + 4));
+  L.eps = off;  off += align16(sizeof(float2) * (size_t)nw * T);
+  L.gv = off;   off += align16(sizeof(float2) * (size_t)nw * T);
+  L.traj = off; off += align16(sizeof(float4) * (size_t)nw * (T + 1));
+  L.pos = off;  off += align16(sizeof(float4) * (size_t)nw * T);
   L.W2T = off;  off += (H > 32) ? align16(sizeof(float) * (size_t)H * H) : 0;
-  L.hbuf = off; off += align16(sizeof(float) * (size_t)nwarps * 2 * spw * H);
-  L.S = off;    off += align16(sizeof(float) * scta);
-  L.e = off;    off += align16(sizeof(float) * scta);
+  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * H);
+  L.S = off;    off += align16(sizeof(float) * nw);
+  L.e = off;    off += align16(sizeof(float) * nw);
   L.total = off;
   return L;
 }
 
-template <int H, int SPW, int NWARPS>
-__global__ void __launch_bounds__(NWARPS * 32) iterate_fp32_kernel(const __grid_constant__ IterParams p) {
-  constexpr int NPL = H / 32;  // hidden neurons per lane
-  constexpr int SCTA = SPW * NWARPS;
-  constexpr bool W2_IN_REGS = (H == 32);
-  constexpr int W3S = H + 4;  // padded row stride of W3 in shared memory
+constexpr int kDevErrNonfinite = -3;  // ITMPC_ERR_NONFINITE
+constexpr int kDevErrTimeout = -4;    // ITMPC_ERR_TIMEOUT
+constexpr uint32_t kWaitPolls = 1u << 22;  // bounded mbarrier wait: ~0.3 s of 64 ns sleeps
 
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int T = p.T;
-  const SmemLayout L = fp32_layout(T, H, SPW, NWARPS);
-  float *U_s = reinterpret_cast<float *>(smem + L.U);
-  float2 *eps_s = reinterpret_cast<float2 *>(smem + L.eps);
-  float4 *traj_s = reinterpret_cast<float4 *>(smem + L.traj);
-  float *W3_s = reinterpret_cast<float *>(smem + L.W3);
-  float *W2T_s = reinterpret_cast<float *>(smem + L.W2T);
-  float *hbuf = reinterpret_cast<float *>(smem + L.hbuf);
-  float *S_s = reinterpret_cast<float *>(smem + L.S);
-  float *e_s = reinterpret_cast<float *>(smem + L.e);
-
+// Merge n records (stride PL floats, 16-byte aligned) with the log-sum-exp rule
+// of Alg. 2: rho = min rho_c, every record rescaled by exp(-(rho_c - rho)/lambda).
+// The whole CTA calls it.  If `out` is non-null the merged record is written
+// there; otherwise the final outputs (U', weights, stats) are written.
+// Records are staged into shared memory (`stage`, `cap` floats, 16-byte
+// aligned) one chunk at a time by a single cp.async.bulk copy completed on
+// `mbar`; the E sums are split over (output, record-slice) pairs.  Returns
+// false (status ITMPC_ERR_TIMEOUT) if a copy did not complete in time.
+template <int NT>
+__device__ bool merge_records(const IterParams &p, const float *recs, int n, float *out, float *stage, int cap,
+                              uint64_t *mbar, uint32_t &phase) {
+  const int T = p.T, PL = partial_len(T), T2 = 2 * T;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int k0 = blockIdx.x * SCTA;
-  const float *net = p.net;
+  constexpr int NWARP = NT / 32;
+  constexpr int MAXO = (2 * ITMPC_MAX_T_DEV + NT - 1) / NT;
+  __shared__ float red[NWARP][5];
+  __shared__ float tot[5];
 
-  // ---- phase 0: nominal controls, output layer, (W2 transposed for H > 32) ----
-  for (int i = tid; i < 2 * T; i += NWARPS * 32) U_s[i] = __ldg(p.U + i);
-  for (int i = tid; i < 4 * H; i += NWARPS * 32) W3_s[(i / H) * W3S + (i % H)] = __ldg(net + net_off_W3(H) + i);
-  if (tid < 4) W3_s[4 * W3S + tid] = __ldg(net + net_off_b3(H) + tid);
-  if constexpr (!W2_IN_REGS) {
-    for (int i = tid; i < H * H; i += NWARPS * 32) {
-      const int j = i / H, k = i % H;  // W2[j][k] -> W2T[k][j]
-      W2T_s[k * H + j] = __ldg(net + net_off_W2(H) + i);
-    }
+  // pass 1: rho
+  float4 hdr = make_float4(INFINITY, 0.f, 0.f, 0.f);
+  float hnf = 0.f;
+  if (tid < n) {
+    hdr = __ldcg(reinterpret_cast<const float4 *>(recs + (size_t)tid * PL));
+    hnf = __ldcg(recs + (size_t)tid * PL + 4);
   }
-
-  // ---- phase 1: noise for (s, t) of this CTA ----
-  for (int i = tid; i < SCTA * T; i += NWARPS * 32) {
-    const int s = i / T, t = i - s * T;
-    const int k = k0 + s;
-    float2 e = make_float2(0.0f, 0.0f);
-    if (k < p.K) {
-      e = noise_at(p, (uint32_t)k, (uint32_t)t);
-      if (p.eps_out) reinterpret_cast<float2 *>(p.eps_out)[(size_t)k * T + t] = e;
-    }
-    eps_s[i] = e;
-  }
-  __syncthreads();
-
-  // ---- phase 2: the serial network recurrence ----
-  const int sw0 = warp * SPW;  // first sample of this warp within the CTA
-  float xd[SPW][4];
-  bool imp[SPW];
-  const float x0r = __ldg(p.x0 + 3), x0vx = __ldg(p.x0 + 4), x0vy = __ldg(p.x0 + 5), x0w = __ldg(p.x0 + 6);
-#pragma unroll
-  for (int i = 0; i < SPW; ++i) {
-    xd[i][0] = x0r; xd[i][1] = x0vx; xd[i][2] = x0vy; xd[i][3] = x0w;
-    imp[i] = (k0 + sw0 + i) < p.n_imp;
-  }
-  if (lane < SPW) traj_s[(sw0 + lane) * (T + 1)] = make_float4(x0r, x0vx, x0vy, x0w);
-
-  float w1[NPL][6], b1r[NPL], b2r[NPL];
-  float w2[W2_IN_REGS ? NPL : 1][W2_IN_REGS ? H : 1];
-#pragma unroll
-  for (int n = 0; n < NPL; ++n) {
-    const int j = lane + 32 * n;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) w1[n][q] = __ldg(net + net_off_W1(H) + j * 6 + q);
-    b1r[n] = __ldg(net + net_off_b1(H) + j);
-    b2r[n] = __ldg(net + net_off_b2(H) + j);
-    if constexpr (W2_IN_REGS) {
-#pragma unroll
-      for (int k = 0; k < H; ++k) w2[n][k] = __ldg(net + net_off_W2(H) + j * H + k);
-    }
-  }
-  __syncthreads();  // W3_s, W2T_s ready
-
-  float *h1buf = hbuf + warp * 2 * SPW * H;
-  float *h2buf = h1buf + SPW * H;
-  const int act = p.activation;
-  const float dt = p.dt;
-
-  for (int t = 0; t < T; ++t) {
-    const float u0 = U_s[2 * t], u1 = U_s[2 * t + 1];
-    float z[SPW][6];
-#pragma unroll
-    for (int i = 0; i < SPW; ++i) {
-      const float2 e = eps_s[(sw0 + i) * T + t];
-      const float v0 = imp[i] ? u0 + e.x : e.x;
-      const float v1 = imp[i] ? u1 + e.y : e.y;
-      z[i][0] = xd[i][0]; z[i][1] = xd[i][1]; z[i][2] = xd[i][2]; z[i][3] = xd[i][3];
-      z[i][4] = fminf(fmaxf(v0, p.umin0), p.umax0);
-      z[i][5] = fminf(fmaxf(v1, p.umin1), p.umax1);
-    }
-    // layer 1: 6 -> H
-#pragma unroll
-    for (int n = 0; n < NPL; ++n) {
-#pragma unroll
-      for (int i = 0; i < SPW; ++i) {
-        float a = b1r[n];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) a = fmaf(w1[n][q], z[i][q], a);
-        h1buf[i * H + lane + 32 * n] = activation(a, act);
-      }
-    }
-    __syncwarp();
-    // layer 2: H -> H, h1 broadcast from shared memory
-    float acc[NPL][SPW];
-#pragma unroll
-    for (int n = 0; n < NPL; ++n)
-#pragma unroll
-      for (int i = 0; i < SPW; ++i) acc[n][i] = b2r[n];
-#pragma unroll
-    for (int k = 0; k < H; k += 4) {
-#pragma unroll
-      for (int i = 0; i < SPW; ++i) {
-        const float4 hv = *reinterpret_cast<const float4 *>(h1buf + i * H + k);
-#pragma unroll
-        for (int n = 0; n < NPL; ++n) {
-          float wa, wb, wc, wd;
-          if constexpr (W2_IN_REGS) {
-            wa = w2[n][k]; wb = w2[n][k + 1]; wc = w2[n][k + 2]; wd = w2[n][k + 3];
-          } else {
-            const int j = lane + 32 * n;
-            wa = W2T_s[k * H + j]; wb = W2T_s[(k + 1) * H + j];
-            wc = W2T_s[(k + 2) * H + j]; wd = W2T_s[(k + 3) * H + j];
-          }
-          acc[n][i] = fmaf(wa, hv.x, acc[n][i]);
-          acc[n][i] = fmaf(wb, hv.y, acc[n][i]);
-          acc[n][i] = fmaf(wc, hv.z, acc[n][i]);
-          acc[n][i] = fmaf(wd, hv.w, acc[n][i]);
-        }
-      }
-    }
-#pragma unroll
-    for (int n = 0; n < NPL; ++n)
-#pragma unroll
-      for (int i = 0; i < SPW; ++i) h2buf[i * H + lane + 32 * n] = activation(acc[n][i], act);
-    __syncwarp();
-    // layer 3: H -> 4, lane 4i + o computes output o of sample i
-    float d = 0.0f;
-    if (lane < 4 * SPW) {
-      const int i = lane >> 2, o = lane & 3;
-      float a0 = W3_s[4 * W3S + o], a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-#pragma unroll
-      for (int k = 0; k < H; k += 4) {
-        const float4 hv = *reinterpret_cast<const float4 *>(h2buf + i * H + k);
-        const float4 wv = *reinterpret_cast<const float4 *>(W3_s + o * W3S + k);
-        a0 = fmaf(wv.x, hv.x, a0);
-        a1 = fmaf(wv.y, hv.y, a1);
-        a2 = fmaf(wv.z, hv.z, a2);
-        a3 = fmaf(wv.w, hv.w, a3);
-      }
-      d = (a0 + a1) + (a2 + a3);
-    }
-#pragma unroll
-    for (int i = 0; i < SPW; ++i) {
-#pragma unroll
-      for (int o = 0; o < 4; ++o) xd[i][o] = fmaf(__shfl_sync(FULL_MASK, d, 4 * i + o), dt, xd[i][o]);
-      if (lane == i) traj_s[(sw0 + i) * (T + 1) + t + 1] = make_float4(xd[i][0], xd[i][1], xd[i][2], xd[i][3]);
-    }
-  }
-  __syncwarp();
-
-  // ---- phase 3: kinematics by prefix sums, then the running cost ----
-  const float gamma = p.gamma;
-  for (int i = 0; i < SPW; ++i) {
-    const int s = sw0 + i;
-    const int k = k0 + s;
-    const bool is_imp = k < p.n_imp;
-    float th_c = __ldg(p.x0 + 2), px_c = __ldg(p.x0 + 0), py_c = __ldg(p.x0 + 1);
-    float Sacc = 0.0f;
-    const bool dump = p.states_out != nullptr && k < p.n_states;
-    if (dump && lane == 0) {
-      float *o = p.states_out + (size_t)k * (T + 1) * 7;
-      for (int q = 0; q < 7; ++q) o[q] = __ldg(p.x0 + q);
-    }
-    for (int base = 0; base < T; base += 32) {
-      const int tau = base + lane;
-      const bool valid = tau < T;
-      const int tau_c = valid ? tau : T - 1;  // keep every shared-memory index in range
-      float4 xo = traj_s[s * (T + 1) + tau_c];
-      if (!valid) xo = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float dth = valid ? dt * xo.w : 0.0f;
-      const float incl_th = warp_incl_scan(dth, lane);
-      float excl_th = __shfl_up_sync(FULL_MASK, incl_th, 1);
-      if (lane == 0) excl_th = 0.0f;
-      const float th_old = th_c + excl_th;
-      float sn, cs;
-      sincosf(th_old, &sn, &cs);
-      const float dpx = valid ? dt * (cs * xo.y - sn * xo.z) : 0.0f;
-      const float dpy = valid ? dt * (sn * xo.y + cs * xo.z) : 0.0f;
-      const float incl_px = warp_incl_scan(dpx, lane);
-      const float incl_py = warp_incl_scan(dpy, lane);
-      const float px = px_c + incl_px, py = py_c + incl_py, th = th_c + incl_th;
-      if (valid) {
-        const float4 xn = traj_s[s * (T + 1) + tau + 1];
-        float c = state_cost(p, px, py, xn.y, xn.z, tau + 1);
-        if (gamma != 0.0f) {
-          const float2 e = eps_s[s * T + tau];
-          const float u0 = U_s[2 * tau], u1 = U_s[2 * tau + 1];
-          const float v0 = is_imp ? u0 + e.x : e.x, v1 = is_imp ? u1 + e.y : e.y;
-          c += gamma * (u0 * v0 * p.inv_sig2_0 + u1 * v1 * p.inv_sig2_1);
-        }
-        Sacc += c;
-        if (dump) {
-          float *o = p.states_out + ((size_t)k * (T + 1) + tau + 1) * 7;
-          o[0] = px; o[1] = py; o[2] = th; o[3] = xn.x; o[4] = xn.y; o[5] = xn.z; o[6] = xn.w;
-        }
-      }
-      th_c += __shfl_sync(FULL_MASK, incl_th, 31);
-      px_c += __shfl_sync(FULL_MASK, incl_px, 31);
-      py_c += __shfl_sync(FULL_MASK, incl_py, 31);
-    }
-    const float S = warp_sum(Sacc);
-    if (lane == 0) {
-      S_s[s] = S;
-      if (k < p.K) p.costs[k] = S;
-    }
-  }
-  __syncthreads();
-
-  // ---- phase 4: this CTA's partial sums ----
-  float *rec = p.partials + (size_t)blockIdx.x * partial_len(T);
-  if (warp == 0) {
-    float m = INFINITY;
-    for (int s = lane; s < SCTA; s += 32) {
-      const float S = S_s[s];
-      if (k0 + s < p.K && isfinite(S)) m = fminf(m, S);
-    }
-    m = warp_min(m);
-    float eta = 0.f, eta_imp = 0.f, sq = 0.f, nf = 0.f;
-    for (int s = lane; s < SCTA; s += 32) {
-      const int k = k0 + s;
-      const float S = S_s[s];
-      const bool ok = k < p.K && isfinite(S) && isfinite(m);
-      const float e = ok ? expf(-(S - m) * p.inv_lambda) : 0.0f;
-      e_s[s] = e;
-      eta += e;
-      eta_imp += (k < p.n_imp) ? e : 0.0f;
-      sq += e * e;
-      nf += (k < p.K && isfinite(S)) ? 1.0f : 0.0f;
-    }
-    eta = warp_sum(eta); eta_imp = warp_sum(eta_imp); sq = warp_sum(sq); nf = warp_sum(nf);
-    if (lane == 0) {
-      rec[0] = m; rec[1] = eta; rec[2] = eta_imp; rec[3] = sq; rec[4] = nf;
-      rec[5] = 0.f; rec[6] = 0.f; rec[7] = 0.f;
-    }
-  }
-  __syncthreads();
-  for (int o = tid; o < 2 * T; o += NWARPS * 32) {
-    const float *ef = reinterpret_cast<const float *>(eps_s);
-    float acc = 0.0f;
-#pragma unroll 4
-    for (int s = 0; s < SCTA; ++s) acc = fmaf(e_s[s], ef[(size_t)(s * T) * 2 + o], acc);
-    rec[8 + o] = acc;
-  }
-
-  // ---- phase 5: the last CTA merges every CTA's partials ----
-  __shared__ bool am_last;
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) am_last = (atomicAdd(p.counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-
-  const int nC = gridDim.x;
-  const int PL = partial_len(T);
-  __shared__ float red[NWARPS][4];
-  __shared__ float tot[4];
-  float m = INFINITY;
-  for (int c = tid; c < nC; c += NWARPS * 32) m = fminf(m, __ldcg(p.partials + (size_t)c * PL));
+  float m = hdr.x;
+  for (int c = tid + NT; c < n; c += NT) m = fminf(m, __ldcg(recs + (size_t)c * PL));
   m = warp_min(m);
   if (lane == 0) red[warp][0] = m;
   __syncthreads();
   if (tid == 0) {
     float r = INFINITY;
-    for (int w = 0; w < NWARPS; ++w) r = fminf(r, red[w][0]);
+    for (int w = 0; w < NWARP; ++w) r = fminf(r, red[w][0]);
     tot[0] = r;
   }
   __syncthreads();
   const float rho = tot[0];
   const bool ok = isfinite(rho);
+  // pass 2: the scalar sums
   float eta = 0.f, eta_imp = 0.f, sq = 0.f, nf = 0.f;
-  for (int c = tid; c < nC; c += NWARPS * 32) {
-    const float *r = p.partials + (size_t)c * PL;
-    const float rc = __ldcg(r);
-    const float sc = (ok && isfinite(rc)) ? expf(-(rc - rho) * p.inv_lambda) : 0.0f;
-    p.scale[c] = sc;
-    eta += sc * __ldcg(r + 1);
-    eta_imp += sc * __ldcg(r + 2);
-    sq += sc * sc * __ldcg(r + 3);
-    nf += __ldcg(r + 4);
+  for (int c = tid; c < n; c += NT) {
+    float4 h = hdr;
+    float hn = hnf;
+    if (c != tid) {
+      h = __ldcg(reinterpret_cast<const float4 *>(recs + (size_t)c * PL));
+      hn = __ldcg(recs + (size_t)c * PL + 4);
+    }
+    const float sc = (ok && isfinite(h.x)) ? expf(-(h.x - rho) * p.inv_lambda) : 0.0f;
+    eta += sc * h.y;
+    eta_imp += sc * h.z;
+    sq += sc * sc * h.w;
+    nf += hn;
   }
-  eta = warp_sum(eta); eta_imp = warp_sum(eta_imp); sq = warp_sum(sq); nf = warp_sum(nf);
-  __syncthreads();
-  if (lane == 0) { red[warp][0] = eta; red[warp][1] = eta_imp; red[warp][2] = sq; red[warp][3] = nf; }
+  eta = warp_sum(eta);
+  eta_imp = warp_sum(eta_imp);
+  sq = warp_sum(sq);
+  nf = warp_sum(nf);
+  __syncthreads();  // tot[0] consumed
+  if (lane == 0) {
+    red[warp][0] = eta; red[warp][1] = eta_imp; red[warp][2] = sq; red[warp][3] = nf;
+  }
   __syncthreads();
   if (tid == 0) {
     float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
-    for (int w = 0; w < NWARPS; ++w) { a += red[w][0]; b += red[w][1]; c += red[w][2]; d += red[w][3]; }
-    tot[0] = a; tot[1] = b; tot[2] = c; tot[3] = d;
+    for (int w = 0; w < NWARP; ++w) { a += red[w][0]; b += red[w][1]; c += red[w][2]; d += red[w][3]; }
+    tot[1] = a; tot[2] = b; tot[3] = c; tot[4] = d;
+  }
+
+  // pass 3: E sums.  Thread -> (output o, record slice r) when 2T <= NT.
+  const int S = T2 <= NT ? NT / T2 : 1;
+  const int r = T2 <= NT ? tid / T2 : 0;
+  const bool active = T2 <= NT ? (tid < S * T2) : true;
+  float acc[MAXO];
+#pragma unroll
+  for (int j = 0; j < MAXO; ++j) acc[j] = 0.f;
+  float *scs = stage;                       // per-record scale of the chunk
+  const int CH = max(1, (cap - 4) / (PL + 1));
+  float *rs = stage + ((CH + 3) & ~3);      // staged records, 16-byte aligned
+  bool copied = true;
+  for (int c0 = 0; c0 < n; c0 += CH) {
+    const int cn = min(CH, n - c0);
+    __syncthreads();  // the previous chunk has been consumed
+    if (tid == 0) {
+      fence_proxy_async();
+      const uint32_t bytes = (uint32_t)(cn * PL * sizeof(float));
+      mbar_expect_tx(mbar, bytes);
+      bulk_copy_g2s(rs, recs + (size_t)c0 * PL, bytes, mbar);
+    }
+    const bool done = mbar_wait_bounded(mbar, phase, kWaitPolls);
+    if (__syncthreads_or(!done)) {
+      copied = false;
+      break;
+    }
+    phase ^= 1u;
+    for (int c = tid; c < cn; c += NT) {
+      const float rc = rs[(size_t)c * PL];
+      scs[c] = (ok && isfinite(rc)) ? expf(-(rc - rho) * p.inv_lambda) : 0.0f;
+    }
+    __syncthreads();
+    if (ok && active) {
+#pragma unroll
+      for (int j = 0; j < MAXO; ++j) {
+        const int o = T2 <= NT ? tid % T2 : tid + j * NT;
+        if ((j == 0 || T2 > NT) && o < T2) {
+          float a0 = 0.f, a1 = 0.f;
+          int c = r;
+          for (; c + S < cn; c += 2 * S) {
+            a0 = fmaf(scs[c], rs[(size_t)c * PL + 8 + o], a0);
+            a1 = fmaf(scs[c + S], rs[(size_t)(c + S) * PL + 8 + o], a1);
+          }
+          if (c < cn) a0 = fmaf(scs[c], rs[(size_t)c * PL + 8 + o], a0);
+          acc[j] += a0 + a1;
+        }
+      }
+    }
+  }
+  if (!copied) {
+    // a copy is still in flight: record the error, wait for it (bounded), leave
+    if (tid == 0) *p.status = kDevErrTimeout;
+    mbar_wait_bounded(mbar, phase, kWaitPolls);
+    return false;
+  }
+  // combine the record slices through shared memory (reusing the stage)
+  __syncthreads();
+  float *part = stage;
+  if (T2 <= NT) {
+    if (active) part[r * T2 + (tid % T2)] = acc[0];
   }
   __syncthreads();
-  const float eta_t = tot[0], eta_imp_t = tot[1], sq_t = tot[2], nf_t = tot[3];
+  const float eta_t = tot[1], eta_imp_t = tot[2], sq_t = tot[3], nf_t = tot[4];
   const float inv_eta = ok ? 1.0f / eta_t : 0.0f;
   const float imp_frac = eta_imp_t * inv_eta;
-  for (int o = tid; o < 2 * T; o += NWARPS * 32) {
-    const float u = p.U[o];
-    float out = u;
-    if (ok) {
-      // Neumaier-compensated sum over CTAs
-      float sum = 0.0f, comp = 0.0f;
-      for (int c = 0; c < nC; ++c) {
-        const float term = __ldcg(p.scale + c) * __ldcg(p.partials + (size_t)c * PL + 8 + o);
-        const float tsum = sum + term;
-        comp += (fabsf(sum) >= fabsf(term)) ? (sum - tsum) + term : (term - tsum) + sum;
-        sum = tsum;
+#pragma unroll
+  for (int j = 0; j < MAXO; ++j) {
+    const int o = tid + j * NT;
+    if (o < T2) {
+      float E = 0.f;
+      if (T2 <= NT) {
+        for (int q = 0; q < S; ++q) E += part[q * T2 + o];
+      } else {
+        E = acc[j];
       }
-      out = u * imp_frac + (sum + comp) * inv_eta;
+      if (out) {
+        out[8 + o] = ok ? E : 0.0f;
+      } else {
+        const float u = p.U[o];
+        p.U_out[o] = ok ? u * imp_frac + E * inv_eta : u;
+      }
     }
-    p.U_out[o] = out;
+  }
+  if (out) {
+    if (tid == 0) {
+      out[0] = rho; out[1] = eta_t; out[2] = eta_imp_t; out[3] = sq_t; out[4] = nf_t;
+      out[5] = 0.f; out[6] = 0.f; out[7] = 0.f;
+    }
+    return true;
   }
   if (p.weights && p.weights_inline) {
-    for (int k = tid; k < p.K; k += NWARPS * 32) {
-      const float S = __ldcg(p.costs + k);
-      p.weights[k] = (ok && isfinite(S)) ? expf(-(S - rho) * p.inv_lambda) * inv_eta : 0.0f;
+    // all loads of a batch are issued before its stores
+    for (int kb = 0; kb < p.K; kb += 8 * NT) {
+      float v[8];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int k = kb + b * NT + tid;
+        v[b] = k < p.K ? __ldcg(p.costs + k) : 0.0f;
+      }
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int k = kb + b * NT + tid;
+        if (k < p.K) p.weights[k] = (ok && isfinite(v[b])) ? expf(-(v[b] - rho) * p.inv_lambda) * inv_eta : 0.0f;
+      }
     }
   }
   if (tid == 0) {
@@ -385,9 +237,302 @@ __global__ void __launch_bounds__(NWARPS * 32) iterate_fp32_kernel(const __grid_
     p.stats[3] = ok ? rho - p.lambda * logf(eta_t / (float)p.K) : INFINITY;
     p.stats[4] = nf_t;
     p.stats[5] = 0.f; p.stats[6] = 0.f; p.stats[7] = 0.f;
-    if (!ok) *p.status = -3;  // ITMPC_ERR_NONFINITE
-    *p.counter = 0u;          // ready for the next launch
+    if (!ok) *p.status = kDevErrNonfinite;
   }
+  return true;
+}
+
+template <int H, int NW, int ACT>
+__global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_constant__ IterParams p) {
+  constexpr int NT = NW * 32;
+  constexpr int NPL = H / 32;  // hidden neurons per lane
+  constexpr bool W2_IN_REGS = (H == 32);
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = p.T;
+  const SmemLayout L = fp32_layout(T, H, NW);
+  float *U_s = reinterpret_cast<float *>(smem + L.U);
+  float2 *eps_s = reinterpret_cast<float2 *>(smem + L.eps);
+  float2 *gv_s = reinterpret_cast<float2 *>(smem + L.gv);
+  float4 *traj_s = reinterpret_cast<float4 *>(smem + L.traj);
+  float4 *pos_s = reinterpret_cast<float4 *>(smem + L.pos);
+  float *W2T_s = reinterpret_cast<float *>(smem + L.W2T);
+  float *S_s = reinterpret_cast<float *>(smem + L.S);
+  float *e_s = reinterpret_cast<float *>(smem + L.e);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k0 = blockIdx.x * NW;
+  const float *net = p.net;
+
+  // ---- phase 0/1: nominal controls, W2 transposed (H > 32), noise and g(v) ----
+  for (int i = tid; i < 2 * T; i += NT) U_s[i] = __ldg(p.U + i);
+  if constexpr (!W2_IN_REGS) {
+    for (int i = tid; i < H * H; i += NT) {
+      const int j = i / H, kk = i - j * H;  // W2[j][kk] -> W2T[kk][j]
+      W2T_s[kk * H + j] = __ldg(net + net_off_W2(H) + i);
+    }
+  }
+  for (int i = tid; i < NW * T; i += NT) {
+    const int s = i / T, t = i - s * T;
+    const int k = k0 + s;
+    float2 e = make_float2(0.0f, 0.0f);
+    if (k < p.K) {
+      e = noise_at(p, (uint32_t)k, (uint32_t)t);
+      if (p.eps_out) reinterpret_cast<float2 *>(p.eps_out)[(size_t)k * T + t] = e;
+    }
+    const bool imp = k < p.n_imp;
+    const float v0 = imp ? __ldg(p.U + 2 * t) + e.x : e.x;
+    const float v1 = imp ? __ldg(p.U + 2 * t + 1) + e.y : e.y;
+    eps_s[i] = e;
+    gv_s[i] = make_float2(fminf(fmaxf(v0, p.umin0), p.umax0), fminf(fmaxf(v1, p.umin1), p.umax1));
+  }
+
+  // per-lane network slices
+  float w1[NPL][6], b1r[NPL], b2r[NPL], w3[NPL][4];
+  float w2[W2_IN_REGS ? H : 1];
+#pragma unroll
+  for (int n = 0; n < NPL; ++n) {
+    const int j = lane + 32 * n;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) w1[n][q] = __ldg(net + net_off_W1(H) + j * 6 + q);
+    b1r[n] = __ldg(net + net_off_b1(H) + j);
+    b2r[n] = __ldg(net + net_off_b2(H) + j);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) w3[n][o] = __ldg(net + net_off_W3(H) + o * H + j);
+  }
+  if constexpr (W2_IN_REGS) {
+#pragma unroll
+    for (int kk = 0; kk < H; ++kk) w2[kk] = __ldg(net + net_off_W2(H) + lane * H + kk);
+  }
+  float b3r[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) b3r[o] = __ldg(net + net_off_b3(H) + o);
+  __syncthreads();
+
+  const int s = warp;  // this warp's sample
+  const int k = k0 + s;
+  const bool live = k < p.K;
+  const float dt = p.dt;
+  const float x0px = __ldg(p.x0 + 0), x0py = __ldg(p.x0 + 1), x0th = __ldg(p.x0 + 2);
+
+  if (live) {
+    // ---- phase 2: the serial network recurrence ----
+    float xd0 = __ldg(p.x0 + 3), xd1 = __ldg(p.x0 + 4), xd2 = __ldg(p.x0 + 5), xd3 = __ldg(p.x0 + 6);
+    float *hrow = reinterpret_cast<float *>(smem + L.hbuf) + s * H;
+    const float4 *hrow4 = reinterpret_cast<const float4 *>(hrow);
+    float4 *traj = traj_s + s * (T + 1);
+    const float2 *gvr = gv_s + s * T;
+    if (lane == 0) traj[0] = make_float4(xd0, xd1, xd2, xd3);
+    const int hi16 = (lane >> 4) & 1, hi8 = (lane >> 3) & 1;
+    float2 g_next = gvr[0];
+    for (int t = 0; t < T; ++t) {
+      const float2 g = g_next;
+      g_next = gvr[t + 1 < T ? t + 1 : t];  // next step's control, off the critical path
+      // layer 1: 6 -> H
+      __syncwarp();  // every lane has finished reading the previous h1 row
+#pragma unroll
+      for (int n = 0; n < NPL; ++n) {
+        float a = b1r[n];
+        a = fmaf(w1[n][0], xd0, a);
+        a = fmaf(w1[n][1], xd1, a);
+        a = fmaf(w1[n][2], xd2, a);
+        a = fmaf(w1[n][3], xd3, a);
+        a = fmaf(w1[n][4], g.x, a);
+        a = fmaf(w1[n][5], g.y, a);
+        hrow[lane + 32 * n] = activation<ACT>(a);
+      }
+      __syncwarp();
+      // layer 2: H -> H, four independent chains per neuron
+      float acc[NPL][4];
+#pragma unroll
+      for (int n = 0; n < NPL; ++n) {
+        acc[n][0] = b2r[n]; acc[n][1] = 0.f; acc[n][2] = 0.f; acc[n][3] = 0.f;
+      }
+#pragma unroll
+      for (int kk = 0; kk < H; kk += 4) {
+        const float4 hv = hrow4[kk >> 2];
+#pragma unroll
+        for (int n = 0; n < NPL; ++n) {
+          float wa, wb, wc, wd;
+          if constexpr (W2_IN_REGS) {
+            wa = w2[kk]; wb = w2[kk + 1]; wc = w2[kk + 2]; wd = w2[kk + 3];
+          } else {
+            const int j = lane + 32 * n;
+            wa = W2T_s[kk * H + j]; wb = W2T_s[(kk + 1) * H + j];
+            wc = W2T_s[(kk + 2) * H + j]; wd = W2T_s[(kk + 3) * H + j];
+          }
+          acc[n][0] = fmaf(wa, hv.x, acc[n][0]);
+          acc[n][1] = fmaf(wb, hv.y, acc[n][1]);
+          acc[n][2] = fmaf(wc, hv.z, acc[n][2]);
+          acc[n][3] = fmaf(wd, hv.w, acc[n][3]);
+        }
+      }
+      // layer 3 partial products of this lane's neurons
+      float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+      for (int n = 0; n < NPL; ++n) {
+        const float h2 = activation<ACT>((acc[n][0] + acc[n][1]) + (acc[n][2] + acc[n][3]));
+        p0 = fmaf(w3[n][0], h2, p0);
+        p1 = fmaf(w3[n][1], h2, p1);
+        p2 = fmaf(w3[n][2], h2, p2);
+        p3 = fmaf(w3[n][3], h2, p3);
+      }
+      // butterfly reduce-scatter of (p0..p3) over the warp: lane ends with output (lane >> 3) & 3
+      const float s0 = hi16 ? p0 : p2, s1 = hi16 ? p1 : p3;
+      const float q0 = (hi16 ? p2 : p0) + __shfl_xor_sync(FULL_MASK, s0, 16);
+      const float q1 = (hi16 ? p3 : p1) + __shfl_xor_sync(FULL_MASK, s1, 16);
+      float v = (hi8 ? q1 : q0) + __shfl_xor_sync(FULL_MASK, hi8 ? q0 : q1, 8);
+      v += __shfl_xor_sync(FULL_MASK, v, 4);
+      v += __shfl_xor_sync(FULL_MASK, v, 2);
+      v += __shfl_xor_sync(FULL_MASK, v, 1);
+      const float d0 = __shfl_sync(FULL_MASK, v, 0) + b3r[0];
+      const float d1 = __shfl_sync(FULL_MASK, v, 8) + b3r[1];
+      const float d2 = __shfl_sync(FULL_MASK, v, 16) + b3r[2];
+      const float d3 = __shfl_sync(FULL_MASK, v, 24) + b3r[3];
+      xd0 = fmaf(d0, dt, xd0);
+      xd1 = fmaf(d1, dt, xd1);
+      xd2 = fmaf(d2, dt, xd2);
+      xd3 = fmaf(d3, dt, xd3);
+      if (lane == 0) traj[t + 1] = make_float4(xd0, xd1, xd2, xd3);
+    }
+    __syncwarp();
+
+    // ---- phase 3a: heading and position by prefix sums over t ----
+    float th_c = x0th, px_c = x0px, py_c = x0py;
+    float4 *pos = pos_s + s * T;
+    for (int base = 0; base < T; base += 32) {
+      const int tau = base + lane;
+      const bool valid = tau < T;
+      float4 xo = traj[valid ? tau : T - 1];
+      if (!valid) xo = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float dth = dt * xo.w;
+      const float incl_th = warp_incl_scan(dth, lane);
+      float excl_th = __shfl_up_sync(FULL_MASK, incl_th, 1);
+      if (lane == 0) excl_th = 0.0f;
+      float sn, cs;
+      sincosf(th_c + excl_th, &sn, &cs);
+      const float dpx = dt * (cs * xo.y - sn * xo.z);
+      const float dpy = dt * (sn * xo.y + cs * xo.z);
+      const float incl_px = warp_incl_scan(dpx, lane);
+      const float incl_py = warp_incl_scan(dpy, lane);
+      if (valid) pos[tau] = make_float4(px_c + incl_px, py_c + incl_py, th_c + incl_th, 0.f);
+      th_c += __shfl_sync(FULL_MASK, incl_th, 31);
+      px_c += __shfl_sync(FULL_MASK, incl_px, 31);
+      py_c += __shfl_sync(FULL_MASK, incl_py, 31);
+    }
+    __syncwarp();
+
+    // ---- phase 3b: running cost at x(t), t = 1..T ----
+    const bool is_imp = k < p.n_imp;
+    const bool dump = p.states_out != nullptr && k < p.n_states;
+    const float gamma = p.gamma;
+    float Sacc = 0.0f;
+#pragma unroll 2
+    for (int base = 0; base < T; base += 32) {
+      const int tau = base + lane;
+      if (tau < T) {
+        const float4 ps = pos[tau];
+        const float4 xn = traj[tau + 1];
+        float c = state_cost(p, ps.x, ps.y, xn.y, xn.z, tau + 1);
+        if (gamma != 0.0f) {
+          const float2 e = eps_s[s * T + tau];
+          const float u0 = U_s[2 * tau], u1 = U_s[2 * tau + 1];
+          const float v0 = is_imp ? u0 + e.x : e.x, v1 = is_imp ? u1 + e.y : e.y;
+          c += gamma * (u0 * v0 * p.inv_sig2_0 + u1 * v1 * p.inv_sig2_1);
+        }
+        Sacc += c;
+        if (dump) {
+          float *o = p.states_out + ((size_t)k * (T + 1) + tau + 1) * 7;
+          o[0] = ps.x; o[1] = ps.y; o[2] = ps.z; o[3] = xn.x; o[4] = xn.y; o[5] = xn.z; o[6] = xn.w;
+        }
+      }
+    }
+    if (dump && lane < 7) p.states_out[(size_t)k * (T + 1) * 7 + lane] = __ldg(p.x0 + lane);
+    const float S = warp_sum(Sacc);
+    if (lane == 0) {
+      S_s[s] = S;
+      p.costs[k] = S;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 4: this CTA's partial record ----
+  float *rec = p.partials + (size_t)blockIdx.x * partial_len(T);
+  if (warp == 0) {
+    float m = INFINITY;
+    for (int q = lane; q < NW; q += 32)
+      if (k0 + q < p.K && isfinite(S_s[q])) m = fminf(m, S_s[q]);
+    m = warp_min(m);
+    float eta = 0.f, eta_imp = 0.f, sq = 0.f, nf = 0.f;
+    for (int q = lane; q < NW; q += 32) {
+      const int kq = k0 + q;
+      const bool fin = kq < p.K && isfinite(S_s[q]);
+      const float e = (fin && isfinite(m)) ? expf(-(S_s[q] - m) * p.inv_lambda) : 0.0f;
+      e_s[q] = e;
+      eta += e;
+      eta_imp += (kq < p.n_imp) ? e : 0.0f;
+      sq += e * e;
+      nf += fin ? 1.0f : 0.0f;
+    }
+    eta = warp_sum(eta); eta_imp = warp_sum(eta_imp); sq = warp_sum(sq); nf = warp_sum(nf);
+    if (lane == 0) {
+      rec[0] = m; rec[1] = eta; rec[2] = eta_imp; rec[3] = sq; rec[4] = nf;
+      rec[5] = 0.f; rec[6] = 0.f; rec[7] = 0.f;
+    }
+  }
+  __syncthreads();
+  {
+    const float *ef = reinterpret_cast<const float *>(eps_s);
+    for (int o = tid; o < 2 * T; o += NT) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) acc = fmaf(e_s[q], ef[(size_t)q * T * 2 + o], acc);
+      rec[8 + o] = acc;
+    }
+  }
+
+  // ---- phase 5: merge by the last CTA of each group; a second level when there are several groups ----
+  __shared__ bool am_last;
+  __shared__ __align__(8) uint64_t mbar;
+  const int nC = gridDim.x;
+  const int G = p.group;
+  const int g = blockIdx.x / G;
+  const int nG = (nC + G - 1) / G;
+  const int g0 = g * G, gn = min(G, nC - g0);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) am_last = (atomicAdd(p.counters + 1 + g, 1u) == (unsigned)(gn - 1));
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  // every phase-1..4 buffer is dead now: stage the merge through them
+  float *stage = reinterpret_cast<float *>(smem + L.eps);
+  const int cap = (int)((L.hbuf - L.eps) / sizeof(float));
+  if (tid == 0) mbar_init(&mbar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  const int PL = partial_len(T);
+  if (nG == 1) {
+    merge_records<NT>(p, p.partials, gn, nullptr, stage, cap, &mbar, phase);
+    if (tid == 0) p.counters[1] = 0u;  // ready for the next launch
+    return;
+  }
+  if (!merge_records<NT>(p, p.partials + (size_t)g0 * PL, gn, p.group_rec + (size_t)g * PL, stage, cap, &mbar,
+                         phase)) {
+    if (tid == 0) p.counters[1 + g] = 0u;
+    return;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    p.counters[1 + g] = 0u;
+    am_last = (atomicAdd(p.counters, 1u) == (unsigned)(nG - 1));
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  merge_records<NT>(p, p.group_rec, nG, nullptr, stage, cap, &mbar, phase);
+  if (tid == 0) p.counters[0] = 0u;  // ready for the next launch
 }
 
 __global__ void finalize_weights_kernel(const __grid_constant__ IterParams p) {
@@ -415,35 +560,69 @@ __global__ void tanh_kernel(const float *x, float *y, int64_t n) {
   if (i < n) y[i] = tanh_f32(x[i]);
 }
 
-template <int H, int SPW, int NWARPS>
-cudaError_t launch_tile(const IterParams &p, cudaStream_t s) {
-  const SmemLayout L = fp32_layout(p.T, H, SPW, NWARPS);
-  auto kern = iterate_fp32_kernel<H, SPW, NWARPS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+template <int H, int NW, int ACT>
+cudaError_t launch_tile(const IterParams &p, int group, cudaStream_t s) {
+  const SmemLayout L = fp32_layout(p.T, H, NW);
+  auto kern = iterate_fp32_kernel<H, NW, ACT>;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const int nC = (p.K + SPW * NWARPS - 1) / (SPW * NWARPS);
-  kern<<<nC, NWARPS * 32, L.total, s>>>(p);
+  static size_t configured[64] = {};  // largest dynamic shared memory size set so far, per device
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (L.total > configured[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    configured[dev] = L.total;
+  }
+  IterParams q = p;
+  q.group = group;
+  const int nC = (p.K + NW - 1) / NW;
+  kern<<<nC, NW * 32, L.total, s>>>(q);
   return cudaGetLastError();
 }
 
+constexpr int kMinWarps = 4;         // smallest CTA the picker returns
+constexpr int kSingleLevel = 256;    // at most this many CTA records: one merge level
+constexpr int kGroup = 128;          // otherwise: CTAs per first-level merge group
+
+int group_for(int nC) { return nC <= kSingleLevel ? nC : kGroup; }
+
 }  // namespace
 
-Fp32Tile fp32_pick_tile(int K, int H) {
-  (void)K;
-  if (H == 128) return {2, 4};
-  return {4, 4};
+Fp32Tile fp32_pick_tile(int K, int T, int H, size_t smem_limit) {
+  // Large CTAs give few partial records (a short merge); small ones spread small K over more SMs.
+  int nw = K >= 2048 ? 16 : (K >= 1024 ? 8 : 4);
+  while (nw > kMinWarps && fp32_layout(T, H, nw).total > smem_limit) nw /= 2;
+  const int nC = (K + nw - 1) / nw;
+  return {nw, group_for(nC)};
 }
 
-size_t fp32_smem_bytes(int T, int H, Fp32Tile t) { return fp32_layout(T, H, t.spw, t.nwarps).total; }
+Fp32Scratch fp32_scratch(int K, int T_max, int H) {
+  (void)H;
+  const size_t PL = (size_t)partial_len(T_max);
+  const size_t nC = (size_t)(K + kMinWarps - 1) / kMinWarps;
+  const size_t G = (size_t)group_for((int)nC);
+  const size_t nG = (nC + G - 1) / G;
+  return {PL * nC, PL * nG, nC > nG ? nC : nG, 1 + nG};
+}
 
-int fp32_num_ctas(int K, Fp32Tile t) { return (K + t.spw * t.nwarps - 1) / (t.spw * t.nwarps); }
+size_t fp32_smem_bytes(int T, int H, Fp32Tile t) { return fp32_layout(T, H, t.nwarps).total; }
+
+int fp32_num_ctas(int K, Fp32Tile t) { return (K + t.nwarps - 1) / t.nwarps; }
 
 cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t s) {
-#define ITMPC_TILE(HH, SS, WW) \
-  if (p.H == HH && tile.spw == SS && tile.nwarps == WW) return launch_tile<HH, SS, WW>(p, s);
-  ITMPC_TILE(32, 4, 4)
-  ITMPC_TILE(64, 4, 4)
-  ITMPC_TILE(128, 2, 4)
+#define ITMPC_TILE(HH, WW)                                                                 \
+  if (p.H == HH && tile.nwarps == WW)                                                      \
+    return p.activation == 1 ? launch_tile<HH, WW, 1>(p, tile.group, s) : launch_tile<HH, WW, 0>(p, tile.group, s);
+  ITMPC_TILE(32, 4)
+  ITMPC_TILE(32, 8)
+  ITMPC_TILE(32, 16)
+  ITMPC_TILE(64, 4)
+  ITMPC_TILE(64, 8)
+  ITMPC_TILE(64, 16)
+  ITMPC_TILE(128, 4)
+  ITMPC_TILE(128, 8)
+  ITMPC_TILE(128, 16)
 #undef ITMPC_TILE
   return cudaErrorInvalidConfiguration;
 }

@@ -23,12 +23,12 @@ struct itmpc_ctx {
   int map_w = 0, map_h = 0;
   float res = 1.f, origin_x = 0.f, origin_y = 0.f;
   bool have_map = false;
-  float *partials = nullptr, *scale = nullptr, *costs = nullptr, *stats = nullptr;
-  unsigned int *counter = nullptr;
+  float *partials = nullptr, *group_rec = nullptr, *scale = nullptr, *costs = nullptr, *stats = nullptr;
+  unsigned int *counters = nullptr;
+  size_t n_counters = 0;
   int *status = nullptr;
   // device staging for the host-pointer entry point
   float *x0_d = nullptr, *U_d = nullptr, *Uout_d = nullptr, *w_d = nullptr;
-  int max_ctas = 0;
   size_t smem_optin = 0;
   std::string err;
 };
@@ -133,8 +133,8 @@ IterParams make_params(const itmpc_ctx *c) {
   p.net = c->net;
   p.costs = c->costs;
   p.partials = c->partials;
-  p.scale = c->scale;
-  p.counter = c->counter;
+  p.group_rec = c->group_rec;
+  p.counters = c->counters;
   p.stats = c->stats;
   p.status = c->status;
   return p;
@@ -165,17 +165,18 @@ itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64
   p.n_states = n_states;
   p.eps_out = eps_out;
   if (costs) p.costs = costs;  // write S_k straight into the caller's buffer
-  const Fp32Tile tile = fp32_pick_tile(p.K, p.H);
+  const Fp32Tile tile = fp32_pick_tile(p.K, p.T, p.H, c->smem_optin);
   CK(c, fp32_launch_iterate(p, tile, c->stream), "fused FP32 iteration launch");
   if (weights && !p.weights_inline) CK(c, launch_finalize_weights(p, c->stream), "weights launch");
   return ITMPC_OK;
 }
 
 void free_ctx(itmpc_ctx *c) {
-  float *bufs[] = {c->net, c->map, c->partials, c->scale, c->costs, c->stats, c->x0_d, c->U_d, c->Uout_d, c->w_d};
+  float *bufs[] = {c->net,   c->map,   c->partials, c->group_rec, c->scale, c->costs,
+                   c->stats, c->x0_d, c->U_d,      c->Uout_d,    c->w_d};
   for (float *b : bufs)
     if (b) cudaFree(b);
-  if (c->counter) cudaFree(c->counter);
+  if (c->counters) cudaFree(c->counters);
   if (c->status) cudaFree(c->status);
   delete c;
 }
@@ -209,26 +210,27 @@ itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   if (e != cudaSuccess) return bail(e, "attribute");
   c->smem_optin = (size_t)optin;
-  const Fp32Tile tile = fp32_pick_tile(c->K_cap, c->H);
+  const Fp32Tile tile = fp32_pick_tile(c->K_cap, c->T_max, c->H, c->smem_optin);
   if (fp32_smem_bytes(c->T_max, c->H, tile) > c->smem_optin) {
     free_ctx(c);
     return ITMPC_ERR_ARG;
   }
-  c->max_ctas = fp32_num_ctas(c->K_cap, tile);
-  const size_t PL = (size_t)partial_len(c->T_max);
+  const Fp32Scratch sc = fp32_scratch(c->K_cap, c->T_max, c->H);
   struct { float **p; size_t n; } allocs[] = {
-      {&c->net, (size_t)net_floats(c->H)}, {&c->partials, PL * c->max_ctas}, {&c->scale, (size_t)c->max_ctas},
-      {&c->costs, (size_t)c->K_cap},       {&c->stats, ITMPC_STATS_LEN},     {&c->x0_d, 8},
-      {&c->U_d, 2 * (size_t)c->T_max},     {&c->Uout_d, 2 * (size_t)c->T_max}, {&c->w_d, (size_t)c->K_cap}};
+      {&c->net, (size_t)net_floats(c->H)}, {&c->partials, sc.partial_floats}, {&c->group_rec, sc.group_floats},
+      {&c->scale, sc.scale_floats > 0 ? sc.scale_floats : 1}, {&c->costs, (size_t)c->K_cap},     {&c->stats, ITMPC_STATS_LEN},
+      {&c->x0_d, 8},                       {&c->U_d, 2 * (size_t)c->T_max},   {&c->Uout_d, 2 * (size_t)c->T_max},
+      {&c->w_d, (size_t)c->K_cap}};
   for (auto &a : allocs) {
     e = cudaMalloc((void **)a.p, sizeof(float) * a.n);
     if (e != cudaSuccess) return bail(e, "cudaMalloc");
   }
-  e = cudaMalloc((void **)&c->counter, sizeof(unsigned int));
+  c->n_counters = sc.counters;
+  e = cudaMalloc((void **)&c->counters, sizeof(unsigned int) * c->n_counters);
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
   e = cudaMalloc((void **)&c->status, sizeof(int));
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
-  e = cudaMemset(c->counter, 0, sizeof(unsigned int));
+  e = cudaMemset(c->counters, 0, sizeof(unsigned int) * c->n_counters);
   if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(float) * ITMPC_STATS_LEN);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -56,18 +56,22 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// tanh x = (e^{2x} - 1) / (e^{2x} + 1) with the hardware base-2 exponential
-// (e^{2x} = 2^{2x log2 e}) and reciprocal.  |x| is clamped to 9, where
-// tanh differs from +-1 by less than half an FP32 ulp of 1.  The absolute
-// error is a few 1e-8 (relative error grows only for |x| << 1e-6, where the
-// result is below the rounding noise of the dot products it feeds).
+// tanh x = 1 - 2 / (1 + e^{2x}), with e^{2x} = 2^{2x log2 e} from the hardware
+// base-2 exponential and the division from the hardware reciprocal.  Both ends
+// saturate without a clamp: e^{2x} = +inf gives 1 - 2/inf = 1 and e^{2x} -> 0
+// gives 1 - 2 = -1.  Near 0 the subtraction cancels, leaving an absolute error
+// of about two FP32 ulps of 1 -- below the rounding noise of the dot products
+// the activation feeds.
 __device__ __forceinline__ float tanh_f32(float x) {
-  const float xc = fminf(fmaxf(x, -9.0f), 9.0f);
-  const float e = ex2_approx(xc * 2.8853900817779268f);
-  return (e - 1.0f) * rcp_approx(e + 1.0f);
+  const float e = ex2_approx(x * 2.8853900817779268f);
+  return fmaf(-2.0f, rcp_approx(1.0f + e), 1.0f);
 }
 
-__device__ __forceinline__ float activation(float a, int act) { return act == 1 ? a : tanh_f32(a); }
+template <int ACT>
+__device__ __forceinline__ float activation(float a) {
+  if constexpr (ACT == 1) return a;
+  else return tanh_f32(a);
+}
 
 // h(p_x, p_y): bilinear, texel (i, j) centred at origin + (j + 1/2, i + 1/2) res,
 // clamp-to-edge.  NaN positions give NaN (indices stay in range).
@@ -99,6 +103,50 @@ __device__ __forceinline__ float state_cost(const IterParams &p, float px, float
   if (fabsf(zeta) > p.slip_thresh) imp += p.crash_cost;
   return p.w_track * h + p.w_speed * sp * sp + p.w_stab * zeta * zeta + p.w_crash * imp;
 }
+
+// ---- asynchronous bulk copies (cp.async.bulk) completed on an mbarrier ----
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+// Order this thread's earlier generic-proxy accesses before later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 template <typename F>
 __device__ __forceinline__ float warp_reduce(float v, F op) {

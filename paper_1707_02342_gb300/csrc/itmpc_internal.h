@@ -15,8 +15,11 @@ __host__ __device__ constexpr int net_off_W3(int H) { return 8 * H + H * H; }
 __host__ __device__ constexpr int net_off_b3(int H) { return 12 * H + H * H; }
 __host__ __device__ constexpr int net_floats(int H) { return 12 * H + H * H + 4; }
 
-// One partial record per CTA: [rho, eta, eta_imp, sum e^2, n_finite, -, -, -, E[T][2]].
-__host__ __device__ constexpr int partial_len(int T) { return 8 + 2 * T; }
+// One partial record per CTA: [rho, eta, eta_imp, sum e^2, n_finite, -, -, -, E[T][2], pad]
+// padded to a multiple of 4 floats so every record starts 16-byte aligned.
+__host__ __device__ constexpr int partial_len(int T) { return 8 + ((2 * T + 3) & ~3); }
+
+constexpr int ITMPC_MAX_T_DEV = 512;  // equals ITMPC_MAX_T of the public header
 
 // Everything one fused iteration launch needs.  Built on the host per call.
 struct IterParams {
@@ -44,9 +47,10 @@ struct IterParams {
   float *U_out;
   float *weights;      // may be null
   float *costs;        // never null (context buffer when the caller gives none)
-  float *partials;     // n_cta x partial_len(T)
-  float *scale;        // n_cta
-  unsigned int *counter;
+  float *partials;     // n_cta x partial_len(T): one record per CTA
+  float *group_rec;    // n_group x partial_len(T): one record per group of CTAs
+  unsigned int *counters;  // 1 + n_group arrival counters, zero between launches
+  int group;           // CTAs per first-level merge group
   float *stats;        // ITMPC_STATS_LEN
   int *status;
   int weights_inline;  // last CTA writes the weights itself
@@ -56,13 +60,21 @@ struct IterParams {
   int n_states;
 };
 
-// Tile shape of the FP32 fused kernel.
+// Launch shape of the FP32 fused kernel: one warp per sample, nwarps samples
+// per CTA, and `group` CTAs per first-level merge group.
 struct Fp32Tile {
-  int spw;     // samples per warp
-  int nwarps;  // warps per CTA
+  int nwarps;
+  int group;
 };
 
-Fp32Tile fp32_pick_tile(int K, int H);
+// Scratch sizes (in floats / counters) an iteration of K samples and horizon
+// T_max needs for any tile the picker may return.
+struct Fp32Scratch {
+  size_t partial_floats, group_floats, scale_floats, counters;  // scale_floats: reserved, unused
+};
+Fp32Scratch fp32_scratch(int K, int T_max, int H);
+
+Fp32Tile fp32_pick_tile(int K, int T, int H, size_t smem_limit);
 size_t fp32_smem_bytes(int T, int H, Fp32Tile tile);
 int fp32_num_ctas(int K, Fp32Tile tile);
 cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t s);

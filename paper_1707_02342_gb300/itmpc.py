@@ -237,6 +237,11 @@ def tanh_f32(x, y, stream=None):
         raise ItmpcError(st, "itmpc_tanh_f32")
 
 
+def partial_stride(T: int) -> int:
+    """ITMPC_PARTIAL_STRIDE(T): floats per partial record."""
+    return 8 + ((2 * T + 3) & ~3)
+
+
 def merge_partials(partials, U, lam: float):
     """Host log-sum-exp merge of per-shard partial records (numpy float32)."""
     import numpy as np
@@ -245,6 +250,8 @@ def merge_partials(partials, U, lam: float):
     U = np.ascontiguousarray(U, np.float32)
     out = np.empty_like(U)
     T = U.shape[0]
+    if partials.shape[1] != partial_stride(T):
+        raise ValueError(f"partial records must have {partial_stride(T)} floats for T={T}")
     st = lib().itmpc_merge_partials(partials.shape[0], T, partials.ctypes.data, U.ctypes.data, lam,
                                     out.ctypes.data)
     return st, out

@@ -64,18 +64,19 @@ def test_null_arguments(L):
 def test_merge_partials_host_math(L):
     # two shards with known sums; lambda = 2: shard 1 is rescaled by exp(-(3 - 1)/2)
     T = 3
-    rec = np.zeros((2, 8 + 2 * T), np.float32)
+    stride = 8 + ((2 * T + 3) & ~3)  # ITMPC_PARTIAL_STRIDE(T)
+    rec = np.zeros((2, stride), np.float32)
     rec[0, :5] = [1.0, 2.0, 2.0, 0, 2]
     rec[1, :5] = [3.0, 4.0, 1.0, 0, 2]
-    rec[0, 8:] = np.arange(6) * 0.1
-    rec[1, 8:] = 1.0
+    rec[0, 8:8 + 2 * T] = np.arange(6) * 0.1
+    rec[1, 8:8 + 2 * T] = 1.0
     U = np.linspace(-0.5, 0.5, 2 * T).astype(np.float32).reshape(T, 2)
     st, out = itmpc.merge_partials(rec, U, 2.0)
     assert st == 0
     s1 = math.exp(-1.0)
     eta = 2.0 + s1 * 4.0
     eta_imp = 2.0 + s1 * 1.0
-    ref = U.reshape(-1).astype(np.float64) * eta_imp / eta + (rec[0, 8:] + s1 * rec[1, 8:]) / eta
+    ref = U.reshape(-1).astype(np.float64) * eta_imp / eta + (rec[0, 8:14] + s1 * rec[1, 8:14]) / eta
     np.testing.assert_allclose(out.reshape(-1), ref, rtol=1e-6)
     rec[:, 0] = np.inf
     st, out = itmpc.merge_partials(rec, U, 2.0)
