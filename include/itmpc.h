@@ -195,6 +195,35 @@ itmpc_status itmpc_tanh_f32(const float *x, float *y, int64_t n, void *stream);
 itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *partials, const float *U,
                                   float lambda, float *U_out);
 
+/* One FP32 control iteration that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate GPU memory when they iterate -- a real-time control loop
+ * that forbids allocation after start-up (cudaMalloc can synchronise the
+ * device and has no latency bound), or a plug-in whose host application has
+ * already reserved the device memory.  It computes what itmpc_create +
+ * itmpc_set_dynamics + itmpc_set_costmap + itmpc_iterate compute, without a
+ * context:
+ *   cfg      iteration parameters as for itmpc_create (precision FP32);
+ *            K <= ITMPC_NOALLOC_MAX_K, T <= ITMPC_NOALLOC_MAX_T, else ITMPC_ERR_ARG
+ *   W, b     device pointers of the three network layers, as itmpc_set_dynamics
+ *   map ...  device costmap and its placement, as itmpc_set_costmap (not copied)
+ *   x0, U, iter, U_out, weights, costs   as itmpc_iterate (device pointers)
+ * Scratch comes from one file-scope device array of ITMPC_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading the library keeps until the process exits.  The
+ * first call on a device resolves that array's address on the current device,
+ * so make that first call before any stream capture.  Every call on a device
+ * shares the array: calls whose work overlaps on the GPU (different streams or
+ * threads without ordering) race and give wrong results.  The call queues its
+ * work on cfg->stream, waits for it and returns the device-side status
+ * (ITMPC_OK, ITMPC_ERR_NONFINITE with U copied to U_out, ITMPC_ERR_TIMEOUT). */
+#define ITMPC_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define ITMPC_NOALLOC_MAX_K 8192
+#define ITMPC_NOALLOC_MAX_T 256
+itmpc_status itmpc_iterate_noalloc(const itmpc_config *cfg, const float *const *W, const float *const *b,
+                                   const float *map, int32_t width, int32_t height, float res, float origin_x,
+                                   float origin_y, const float *x0, const float *U, uint64_t iter, float *U_out,
+                                   float *weights, float *costs);
+
 /* Message for the last failing call on ctx (never NULL). */
 const char *itmpc_last_error(const itmpc_ctx *ctx);
 

@@ -17,6 +17,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_OOM = 0, -1, -
 FP32, BF16, FP8 = 0, 1, 2
 ACT_TANH, ACT_IDENTITY = 0, 1
 MAX_K, MAX_T, STATS_LEN = 1 << 24, 512, 8
+NOALLOC_MAX_K, NOALLOC_MAX_T, NOALLOC_SCRATCH_BYTES = 8192, 256, 4 << 20
 
 # Every function the header declares, with (restype, argtypes).
 _vp, _i32, _i64, _u64, _f = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float
@@ -51,6 +52,8 @@ SIGNATURES = {
     "itmpc_philox4x32_10": (C.c_int, [_vp, _vp, _vp, _i64, _vp]),
     "itmpc_tanh_f32": (C.c_int, [_vp, _vp, _i64, _vp]),
     "itmpc_merge_partials": (C.c_int, [_i32, _i32, _vp, _vp, _f, _vp]),
+    "itmpc_iterate_noalloc": (C.c_int, [C.POINTER(Config), _vp, _vp, _vp, _i32, _i32, _f, _f, _f, _vp, _vp, _u64,
+                                        _vp, _vp, _vp]),
     "itmpc_last_error": (C.c_char_p, [_vp]),
     "itmpc_status_string": (C.c_char_p, [_i32]),
     "itmpc_version": (C.c_int32, []),
@@ -255,3 +258,17 @@ def merge_partials(partials, U, lam: float):
     st = lib().itmpc_merge_partials(partials.shape[0], T, partials.ctypes.data, U.ctypes.data, lam,
                                     out.ctypes.data)
     return st, out
+
+
+def iterate_noalloc(cfg: Config, layers, cmap, res: float, origin_x: float, origin_y: float, x0, U, it: int, U_out,
+                    weights=None, costs=None) -> int:
+    """itmpc_iterate_noalloc on CUDA tensors; waits for the GPU and returns the status.
+
+    For callers that cannot allocate device memory while iterating; the
+    library's scratch is a fixed device array shared by all calls on a device.
+    """
+    Ws = (C.c_void_p * 3)(*[_dptr(W) for W, _ in layers])
+    bs = (C.c_void_p * 3)(*[_dptr(b) for _, b in layers])
+    h, w = cmap.shape
+    return int(lib().itmpc_iterate_noalloc(C.byref(cfg), Ws, bs, _dptr(cmap), w, h, res, origin_x, origin_y,
+                                           _dptr(x0), _dptr(U), it, _dptr(U_out), _dptr(weights), _dptr(costs)))
