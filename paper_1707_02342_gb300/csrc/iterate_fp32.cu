@@ -34,7 +34,7 @@ namespace {
 __host__ __device__ constexpr size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
 
 struct SmemLayout {
-  size_t U, eps, gv, traj, pos, W2T, hbuf, S, e, total;
+  size_t U, eps, gv, traj, pos, W2T, hbuf, W3b3, S, e, total;
 };
 
 __host__ __device__ inline SmemLayout fp32_layout(int T, int H, int nw) {
@@ -46,7 +46,8 @@ __host__ __device__ inline SmemLayout fp32_layout(int T, int H, int nw) {
   L.traj = off; off += align16(sizeof(float4) * (size_t)nw * (T + 1));
   L.pos = off;  off += align16(sizeof(float4) * (size_t)nw * T);
   L.W2T = off;  off += (H > 32) ? align16(sizeof(float) * (size_t)H * H) : 0;
-  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * H);
+  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * (H == 32 ? 32 * 36 + 32 : 2 * H));
+  L.W3b3 = off; off += align16(sizeof(float) * (4 * H + 4));
   L.S = off;    off += align16(sizeof(float) * nw);
   L.e = off;    off += align16(sizeof(float) * nw);
   L.total = off;
@@ -62,9 +63,10 @@ constexpr uint32_t kWaitPolls = 1u << 22;  // bounded mbarrier wait: ~0.3 s of 6
 // The whole CTA calls it.  If `out` is non-null the merged record is written
 // there; otherwise the final outputs (U', weights, stats) are written.
 // Records are staged into shared memory (`stage`, `cap` floats, 16-byte
-// aligned) one chunk at a time by a single cp.async.bulk copy completed on
-// `mbar`; the E sums are split over (output, record-slice) pairs.  Returns
-// false (status ITMPC_ERR_TIMEOUT) if a copy did not complete in time.
+// aligned) by cp.async.bulk copies completed on `mbar`: all of them with one
+// copy when they fit, else chunk by chunk.  The E sums are split over
+// (output, record-slice) pairs.  Returns false (status ITMPC_ERR_TIMEOUT) if a
+// copy did not complete in time.
 template <int NT>
 __device__ bool merge_records(const IterParams &p, const float *recs, int n, float *out, float *stage, int cap,
                               uint64_t *mbar, uint32_t &phase) {
@@ -75,15 +77,39 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
   __shared__ float red[NWARP][5];
   __shared__ float tot[5];
 
-  // pass 1: rho
-  float4 hdr = make_float4(INFINITY, 0.f, 0.f, 0.f);
-  float hnf = 0.f;
-  if (tid < n) {
-    hdr = __ldcg(reinterpret_cast<const float4 *>(recs + (size_t)tid * PL));
-    hnf = __ldcg(recs + (size_t)tid * PL + 4);
-  }
-  float m = hdr.x;
-  for (int c = tid + NT; c < n; c += NT) m = fminf(m, __ldcg(recs + (size_t)c * PL));
+  // stage layout: [per-record scale: CH floats, padded to 4][CH records]
+  const int CH = max(1, min(n, (cap - 4) / (PL + 1)));
+  float *scs = stage;
+  float *rs = stage + ((CH + 3) & ~3);
+  const bool whole = CH >= n;
+
+  auto copy_chunk = [&](int c0, int cn) -> bool {
+    __syncthreads();  // the stage is free (previous chunk consumed, earlier phases done)
+    if (tid == 0) {
+      fence_proxy_async();
+      const uint32_t bytes = (uint32_t)(cn * PL * sizeof(float));
+      mbar_expect_tx(mbar, bytes);
+      bulk_copy_g2s(rs, recs + (size_t)c0 * PL, bytes, mbar);
+    }
+    const bool done = mbar_wait_bounded(mbar, phase, kWaitPolls);
+    if (__syncthreads_or(!done)) {
+      if (tid == 0) *p.status = kDevErrTimeout;
+      mbar_wait_bounded(mbar, phase, kWaitPolls);  // let the copy land before the CTA leaves
+      return false;
+    }
+    phase ^= 1u;
+    return true;
+  };
+
+  // pass 1 + 2: rho and the scalar sums, from the staged records when they all fit
+  if (whole && !copy_chunk(0, n)) return false;
+  auto header = [&](int c) -> float4 {
+    return whole ? *reinterpret_cast<const float4 *>(rs + (size_t)c * PL)
+                 : __ldcg(reinterpret_cast<const float4 *>(recs + (size_t)c * PL));
+  };
+  auto nfin = [&](int c) -> float { return whole ? rs[(size_t)c * PL + 4] : __ldcg(recs + (size_t)c * PL + 4); };
+  float m = INFINITY;
+  for (int c = tid; c < n; c += NT) m = fminf(m, header(c).x);
   m = warp_min(m);
   if (lane == 0) red[warp][0] = m;
   __syncthreads();
@@ -95,26 +121,21 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
   __syncthreads();
   const float rho = tot[0];
   const bool ok = isfinite(rho);
-  // pass 2: the scalar sums
   float eta = 0.f, eta_imp = 0.f, sq = 0.f, nf = 0.f;
   for (int c = tid; c < n; c += NT) {
-    float4 h = hdr;
-    float hn = hnf;
-    if (c != tid) {
-      h = __ldcg(reinterpret_cast<const float4 *>(recs + (size_t)c * PL));
-      hn = __ldcg(recs + (size_t)c * PL + 4);
-    }
+    const float4 h = header(c);
     const float sc = (ok && isfinite(h.x)) ? expf(-(h.x - rho) * p.inv_lambda) : 0.0f;
+    if (whole) scs[c] = sc;
     eta += sc * h.y;
     eta_imp += sc * h.z;
     sq += sc * sc * h.w;
-    nf += hn;
+    nf += nfin(c);
   }
   eta = warp_sum(eta);
   eta_imp = warp_sum(eta_imp);
   sq = warp_sum(sq);
   nf = warp_sum(nf);
-  __syncthreads();  // tot[0] consumed
+  __syncthreads();  // tot[0] consumed, scs written
   if (lane == 0) {
     red[warp][0] = eta; red[warp][1] = eta_imp; red[warp][2] = sq; red[warp][3] = nf;
   }
@@ -132,30 +153,16 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
   float acc[MAXO];
 #pragma unroll
   for (int j = 0; j < MAXO; ++j) acc[j] = 0.f;
-  float *scs = stage;                       // per-record scale of the chunk
-  const int CH = max(1, (cap - 4) / (PL + 1));
-  float *rs = stage + ((CH + 3) & ~3);      // staged records, 16-byte aligned
-  bool copied = true;
   for (int c0 = 0; c0 < n; c0 += CH) {
     const int cn = min(CH, n - c0);
-    __syncthreads();  // the previous chunk has been consumed
-    if (tid == 0) {
-      fence_proxy_async();
-      const uint32_t bytes = (uint32_t)(cn * PL * sizeof(float));
-      mbar_expect_tx(mbar, bytes);
-      bulk_copy_g2s(rs, recs + (size_t)c0 * PL, bytes, mbar);
+    if (!whole) {
+      if (!copy_chunk(c0, cn)) return false;
+      for (int c = tid; c < cn; c += NT) {
+        const float rc = rs[(size_t)c * PL];
+        scs[c] = (ok && isfinite(rc)) ? expf(-(rc - rho) * p.inv_lambda) : 0.0f;
+      }
+      __syncthreads();
     }
-    const bool done = mbar_wait_bounded(mbar, phase, kWaitPolls);
-    if (__syncthreads_or(!done)) {
-      copied = false;
-      break;
-    }
-    phase ^= 1u;
-    for (int c = tid; c < cn; c += NT) {
-      const float rc = rs[(size_t)c * PL];
-      scs[c] = (ok && isfinite(rc)) ? expf(-(rc - rho) * p.inv_lambda) : 0.0f;
-    }
-    __syncthreads();
     if (ok && active) {
 #pragma unroll
       for (int j = 0; j < MAXO; ++j) {
@@ -173,18 +180,10 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
       }
     }
   }
-  if (!copied) {
-    // a copy is still in flight: record the error, wait for it (bounded), leave
-    if (tid == 0) *p.status = kDevErrTimeout;
-    mbar_wait_bounded(mbar, phase, kWaitPolls);
-    return false;
-  }
   // combine the record slices through shared memory (reusing the stage)
   __syncthreads();
   float *part = stage;
-  if (T2 <= NT) {
-    if (active) part[r * T2 + (tid % T2)] = acc[0];
-  }
+  if (T2 <= NT && active) part[r * T2 + (tid % T2)] = acc[0];
   __syncthreads();
   const float eta_t = tot[1], eta_imp_t = tot[2], sq_t = tot[3], nf_t = tot[4];
   const float inv_eta = ok ? 1.0f / eta_t : 0.0f;
@@ -242,6 +241,123 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
   return true;
 }
 
+// Phase 2 for H = 32.  Layers 3 and 1 are affine, so with M = dt W1x W3
+// (32 x 32), beta = dt W1x b3 and the Euler step x_d(t+1) = x_d(t) + dt d(t),
+// d(t) = W3 h2(t) + b3, the input-layer pre-activation obeys
+//   a1(t+1) = a1(t) + M h2(t) + beta + W1u (g(t+1) - g(t))
+// (W1x, W1u: the state and control columns of W1; g the clamped control).
+// The serial chain of a step is then two 32-term dot products with a tanh
+// each, and x_d is not needed inside the loop: a1 is carried as a compensated
+// (Kahan) sum, h2 rows go to a 32-step ring in shared memory (which is also the
+// broadcast row of the M h2 product), and every 32 steps the output layer
+// d = W3 h2 + b3 is applied to the whole block with lane = time step.  d(t) is
+// left in traj[t + 1]; phase 3 turns it into x_d by prefix sums.
+constexpr int kRingStride = 36;  // padded row: lanes reading rows t, t+1, .. hit distinct banks
+
+template <int ACT>
+__device__ __forceinline__ void recurrence_ring32(const IterParams &p, const float *net, float *ring, float *hB,
+                                                  const float *W3b3_s, const float2 *gvr, float4 *traj, int T,
+                                                  int lane) {
+  constexpr int H = 32;
+  const float dt = p.dt;
+  float w1x[4], b3[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    w1x[o] = __ldg(net + net_off_W1(H) + lane * 6 + o);
+    b3[o] = __ldg(net + net_off_b3(H) + o);
+  }
+  const float w1u0 = __ldg(net + net_off_W1(H) + lane * 6 + 4);
+  const float w1u1 = __ldg(net + net_off_W1(H) + lane * 6 + 5);
+  const float b1 = __ldg(net + net_off_b1(H) + lane);
+  const float b2 = __ldg(net + net_off_b2(H) + lane);
+  float beta = 0.f;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) beta = fmaf(dt * w1x[o], b3[o], beta);
+  float m[H], w2[H];
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    float a = 0.f;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) a = fmaf(w1x[o], W3b3_s[o * H + i], a);
+    m[i] = dt * a;
+    w2[i] = __ldg(net + net_off_W2(H) + lane * H + i);
+  }
+  const float4 *hB4 = reinterpret_cast<const float4 *>(hB);
+
+  // a1(0) = b1 + W1x x_d(0) + W1u g(0)
+  float2 g = gvr[0];
+  float a1 = b1;
+  a1 = fmaf(w1x[0], __ldg(p.x0 + 3), a1);
+  a1 = fmaf(w1x[1], __ldg(p.x0 + 4), a1);
+  a1 = fmaf(w1x[2], __ldg(p.x0 + 5), a1);
+  a1 = fmaf(w1x[3], __ldg(p.x0 + 6), a1);
+  a1 = fmaf(w1u0, g.x, a1);
+  a1 = fmaf(w1u1, g.y, a1);
+  float a1c = 0.f;  // Kahan compensation of the running sum a1
+  for (int t = 0; t < T; ++t) {
+    const float2 gn = gvr[t + 1 < T ? t + 1 : t];
+    // layer 1 activation, broadcast through hB
+    hB[lane] = activation<ACT>(a1);
+    __syncwarp();
+    // layer 2
+    float c0 = b2, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < H; kk += 4) {
+      const float4 hv = hB4[kk >> 2];
+      c0 = fmaf(w2[kk], hv.x, c0);
+      c1 = fmaf(w2[kk + 1], hv.y, c1);
+      c2 = fmaf(w2[kk + 2], hv.z, c2);
+      c3 = fmaf(w2[kk + 3], hv.w, c3);
+    }
+    const float h2 = activation<ACT>((c0 + c1) + (c2 + c3));
+    float *row = ring + (t & 31) * kRingStride;
+    row[lane] = h2;
+    __syncwarp();
+    // next step's pre-activation: a1 += M h2 + beta + W1u (g(t+1) - g(t))
+    if (t + 1 < T) {
+      const float4 *row4 = reinterpret_cast<const float4 *>(row);
+      float e0 = beta, e1 = 0.f, e2 = 0.f, e3 = 0.f;
+      e0 = fmaf(w1u0, gn.x - g.x, e0);
+      e1 = fmaf(w1u1, gn.y - g.y, e1);
+#pragma unroll
+      for (int kk = 0; kk < H; kk += 4) {
+        const float4 hv = row4[kk >> 2];
+        e0 = fmaf(m[kk], hv.x, e0);
+        e1 = fmaf(m[kk + 1], hv.y, e1);
+        e2 = fmaf(m[kk + 2], hv.z, e2);
+        e3 = fmaf(m[kk + 3], hv.w, e3);
+      }
+      const float y = ((e0 + e1) + (e2 + e3)) - a1c;
+      const float sum = a1 + y;
+      a1c = (sum - a1) - y;
+      a1 = sum;
+      g = gn;
+    }
+    // every 32 steps (and at the end): the output layer for the block, lane = step
+    if ((t & 31) == 31 || t + 1 == T) {
+      const int t0 = t & ~31;
+      if (t0 + lane <= t) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(ring + lane * kRingStride);
+        float d0 = W3b3_s[4 * H + 0], d1 = W3b3_s[4 * H + 1], d2 = W3b3_s[4 * H + 2], d3 = W3b3_s[4 * H + 3];
+#pragma unroll
+        for (int kk = 0; kk < H; kk += 4) {
+          const float4 hv = r4[kk >> 2];
+          const float4 w0 = *reinterpret_cast<const float4 *>(W3b3_s + 0 * H + kk);
+          const float4 wq1 = *reinterpret_cast<const float4 *>(W3b3_s + 1 * H + kk);
+          const float4 wq2 = *reinterpret_cast<const float4 *>(W3b3_s + 2 * H + kk);
+          const float4 wq3 = *reinterpret_cast<const float4 *>(W3b3_s + 3 * H + kk);
+          d0 = fmaf(w0.x, hv.x, fmaf(w0.y, hv.y, fmaf(w0.z, hv.z, fmaf(w0.w, hv.w, d0))));
+          d1 = fmaf(wq1.x, hv.x, fmaf(wq1.y, hv.y, fmaf(wq1.z, hv.z, fmaf(wq1.w, hv.w, d1))));
+          d2 = fmaf(wq2.x, hv.x, fmaf(wq2.y, hv.y, fmaf(wq2.z, hv.z, fmaf(wq2.w, hv.w, d2))));
+          d3 = fmaf(wq3.x, hv.x, fmaf(wq3.y, hv.y, fmaf(wq3.z, hv.z, fmaf(wq3.w, hv.w, d3))));
+        }
+        traj[t0 + lane + 1] = make_float4(d0, d1, d2, d3);
+      }
+      __syncwarp();  // the ring is reused by the next block
+    }
+  }
+}
+
 template <int H, int NW, int ACT>
 __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_constant__ IterParams p) {
   constexpr int NT = NW * 32;
@@ -264,8 +380,10 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
   const int k0 = blockIdx.x * NW;
   const float *net = p.net;
 
-  // ---- phase 0/1: nominal controls, W2 transposed (H > 32), noise and g(v) ----
+  // ---- phase 0/1: nominal controls, W3|b3, W2 transposed (H > 32), noise and g(v) ----
+  float *W3b3_s = reinterpret_cast<float *>(smem + L.W3b3);
   for (int i = tid; i < 2 * T; i += NT) U_s[i] = __ldg(p.U + i);
+  for (int i = tid; i < 4 * H + 4; i += NT) W3b3_s[i] = __ldg(net + net_off_W3(H) + i);  // W3 then b3
   if constexpr (!W2_IN_REGS) {
     for (int i = tid; i < H * H; i += NT) {
       const int j = i / H, kk = i - j * H;  // W2[j][kk] -> W2T[kk][j]
@@ -318,11 +436,14 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
   if (live) {
     // ---- phase 2: the serial network recurrence ----
     float xd0 = __ldg(p.x0 + 3), xd1 = __ldg(p.x0 + 4), xd2 = __ldg(p.x0 + 5), xd3 = __ldg(p.x0 + 6);
-    float *hrow = reinterpret_cast<float *>(smem + L.hbuf) + s * H;
+    float *hrow = reinterpret_cast<float *>(smem + L.hbuf) + s * (H == 32 ? 32 * kRingStride + 32 : 2 * H);
     const float4 *hrow4 = reinterpret_cast<const float4 *>(hrow);
     float4 *traj = traj_s + s * (T + 1);
     const float2 *gvr = gv_s + s * T;
     if (lane == 0) traj[0] = make_float4(xd0, xd1, xd2, xd3);
+    if constexpr (H == 32) {
+      recurrence_ring32<ACT>(p, net, hrow, hrow + 32 * kRingStride, W3b3_s, gv_s + s * T, traj, T, lane);
+    } else {
     const int hi16 = (lane >> 4) & 1, hi8 = (lane >> 3) & 1;
     float2 g_next = gvr[0];
     for (int t = 0; t < T; ++t) {
@@ -396,14 +517,37 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
       if (lane == 0) traj[t + 1] = make_float4(xd0, xd1, xd2, xd3);
     }
     __syncwarp();
+    }
+    __syncwarp();
 
-    // ---- phase 3a: heading and position by prefix sums over t ----
+    // ---- phase 3a: x_d (H = 32: from the stored d), heading and position by prefix sums over t ----
     float th_c = x0th, px_c = x0px, py_c = x0py;
+    float4 xd_c = traj[0];
     float4 *pos = pos_s + s * T;
     for (int base = 0; base < T; base += 32) {
       const int tau = base + lane;
       const bool valid = tau < T;
-      float4 xo = traj[valid ? tau : T - 1];
+      float4 xo;
+      if constexpr (H == 32) {
+        // traj[tau + 1] holds d(tau): x_d(tau + 1) = x_d(0) + dt sum_{s <= tau} d(s)
+        float4 dd = traj[valid ? tau + 1 : T];
+        if (!valid) dd = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float i0 = warp_incl_scan(dt * dd.x, lane), i1 = warp_incl_scan(dt * dd.y, lane);
+        const float i2 = warp_incl_scan(dt * dd.z, lane), i3 = warp_incl_scan(dt * dd.w, lane);
+        // every lane takes part in each shuffle; lane 0 then drops the value
+        float e0 = __shfl_up_sync(FULL_MASK, i0, 1), e1 = __shfl_up_sync(FULL_MASK, i1, 1);
+        float e2 = __shfl_up_sync(FULL_MASK, i2, 1), e3 = __shfl_up_sync(FULL_MASK, i3, 1);
+        if (lane == 0) e0 = e1 = e2 = e3 = 0.f;
+        xo = make_float4(xd_c.x + e0, xd_c.y + e1, xd_c.z + e2, xd_c.w + e3);
+        __syncwarp();  // every lane has read its d before any x_d overwrites it
+        if (valid) traj[tau + 1] = make_float4(xd_c.x + i0, xd_c.y + i1, xd_c.z + i2, xd_c.w + i3);
+        xd_c.x += __shfl_sync(FULL_MASK, i0, 31);
+        xd_c.y += __shfl_sync(FULL_MASK, i1, 31);
+        xd_c.z += __shfl_sync(FULL_MASK, i2, 31);
+        xd_c.w += __shfl_sync(FULL_MASK, i3, 31);
+      } else {
+        xo = traj[valid ? tau : T - 1];
+      }
       if (!valid) xo = make_float4(0.f, 0.f, 0.f, 0.f);
       const float dth = dt * xo.w;
       const float incl_th = warp_incl_scan(dth, lane);
@@ -507,7 +651,7 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
   __threadfence();
   // every phase-1..4 buffer is dead now: stage the merge through them
   float *stage = reinterpret_cast<float *>(smem + L.eps);
-  const int cap = (int)((L.hbuf - L.eps) / sizeof(float));
+  const int cap = p.stage_floats;
   if (tid == 0) mbar_init(&mbar, 1);
   __syncthreads();
   uint32_t phase = 0;
@@ -560,24 +704,62 @@ __global__ void tanh_kernel(const float *x, float *y, int64_t n) {
   if (i < n) y[i] = tanh_f32(x[i]);
 }
 
+struct DeviceInfo {
+  int sms = 0;
+  size_t smem_optin = 0, smem_per_sm = 0;
+};
+
+cudaError_t device_info(DeviceInfo &out) {
+  static DeviceInfo cache[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (cache[dev].sms == 0) {
+    int sms = 0, optin = 0, per_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+      return e;
+    cache[dev].smem_optin = (size_t)optin;
+    cache[dev].smem_per_sm = (size_t)per_sm;
+    cache[dev].sms = sms;
+  }
+  out = cache[dev];
+  return cudaSuccess;
+}
+
 template <int H, int NW, int ACT>
 cudaError_t launch_tile(const IterParams &p, int group, cudaStream_t s) {
   const SmemLayout L = fp32_layout(p.T, H, NW);
   auto kern = iterate_fp32_kernel<H, NW, ACT>;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  DeviceInfo di;
+  cudaError_t e = device_info(di);
   if (e != cudaSuccess) return e;
+  const int nC = (p.K + NW - 1) / NW;
+  // Shared memory for staging one merge (all of a group's records) when the
+  // occupancy the grid needs still fits; otherwise the merge works in chunks.
+  const int per_merge = nC <= group ? nC : group;
+  const size_t PLb = sizeof(float) * (size_t)partial_len(p.T);
+  const size_t want = L.eps + sizeof(float) * (size_t)((per_merge + 3) & ~3) + PLb * per_merge;
+  const int ctas_per_sm = (nC + di.sms - 1) / di.sms;
+  size_t budget = di.smem_per_sm / (size_t)ctas_per_sm;
+  budget = budget > 1024 ? budget - 1024 : 0;  // per-CTA reservation
+  if (budget > di.smem_optin) budget = di.smem_optin;
+  size_t smem = L.total;
+  if (want > smem && want <= budget) smem = want;
   static size_t configured[64] = {};  // largest dynamic shared memory size set so far, per device
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (L.total > configured[dev]) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (smem > configured[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured[dev] = L.total;
+    configured[dev] = smem;
   }
   IterParams q = p;
   q.group = group;
-  const int nC = (p.K + NW - 1) / NW;
-  kern<<<nC, NW * 32, L.total, s>>>(q);
+  q.stage_floats = (int)((smem - L.eps) / sizeof(float));
+  kern<<<nC, NW * 32, smem, s>>>(q);
   return cudaGetLastError();
 }
 
@@ -590,9 +772,16 @@ int group_for(int nC) { return nC <= kSingleLevel ? nC : kGroup; }
 }  // namespace
 
 Fp32Tile fp32_pick_tile(int K, int T, int H, size_t smem_limit) {
-  // Large CTAs give few partial records (a short merge); small ones spread small K over more SMs.
-  int nw = K >= 2048 ? 16 : (K >= 1024 ? 8 : 4);
-  while (nw > kMinWarps && fp32_layout(T, H, nw).total > smem_limit) nw /= 2;
+  // One warp per sample.  Large CTAs give few partial records (a short merge);
+  // when all samples fit on the GPU at once, spread them evenly over the SMs.
+  DeviceInfo di;
+  const int sms = device_info(di) == cudaSuccess && di.sms > 0 ? di.sms : 148;
+  int nw;
+  if (K >= 8 * sms && K <= 14 * sms && H == 32) nw = 14;
+  else if (K >= 2048) nw = 16;
+  else if (K >= 1024) nw = 8;
+  else nw = 4;
+  while (nw > kMinWarps && fp32_layout(T, H, nw).total > smem_limit) nw = nw > 8 ? 8 : nw / 2;
   const int nC = (K + nw - 1) / nw;
   return {nw, group_for(nC)};
 }
@@ -616,6 +805,7 @@ cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t
     return p.activation == 1 ? launch_tile<HH, WW, 1>(p, tile.group, s) : launch_tile<HH, WW, 0>(p, tile.group, s);
   ITMPC_TILE(32, 4)
   ITMPC_TILE(32, 8)
+  ITMPC_TILE(32, 14)
   ITMPC_TILE(32, 16)
   ITMPC_TILE(64, 4)
   ITMPC_TILE(64, 8)

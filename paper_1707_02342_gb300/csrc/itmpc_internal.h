@@ -51,6 +51,7 @@ struct IterParams {
   float *group_rec;    // n_group x partial_len(T): one record per group of CTAs
   unsigned int *counters;  // 1 + n_group arrival counters, zero between launches
   int group;           // CTAs per first-level merge group
+  int stage_floats;    // shared memory (floats) from the end of the U block available to the merge
   float *stats;        // ITMPC_STATS_LEN
   int *status;
   int weights_inline;  // last CTA writes the weights itself
