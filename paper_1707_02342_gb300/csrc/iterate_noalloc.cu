@@ -118,7 +118,7 @@ extern "C" itmpc_status itmpc_iterate_noalloc(const itmpc_config *cfg, const flo
   float *partials = (float *)take(sizeof(float) * PL * (size_t)nC);
   float *group_rec = (float *)take(sizeof(float) * PL * (size_t)nG);
   float *stats = (float *)take(sizeof(float) * ITMPC_STATS_LEN);
-  unsigned int *counters = (unsigned int *)take(sizeof(unsigned int) * (size_t)(1 + nG));
+  unsigned int *counters = (unsigned int *)take(sizeof(unsigned int) * (size_t)(1 + nG + 2));
   int *status = (int *)take(sizeof(int));
   if (off > (size_t)ITMPC_NOALLOC_SCRATCH_BYTES) return ITMPC_ERR_ARG;  // cannot happen within the stated limits
 
@@ -133,7 +133,7 @@ extern "C" itmpc_status itmpc_iterate_noalloc(const itmpc_config *cfg, const flo
     if (e == cudaSuccess) e = cudaMemcpyAsync(net + offb[l], b[l], sizeof(float) * nb[l], cudaMemcpyDeviceToDevice, s);
   }
   // the scratch keeps the previous call's contents: the counters and the status must start at zero
-  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * (size_t)(1 + nG), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(unsigned int) * (size_t)(1 + nG + 2), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -184,6 +184,7 @@ extern "C" itmpc_status itmpc_iterate_noalloc(const itmpc_config *cfg, const flo
   p.partials = partials;
   p.group_rec = group_rec;
   p.counters = counters;
+  p.grid_bar = counters + 1 + nG;
   p.stats = stats;
   p.status = status;
   e = fp32_launch_iterate(p, tile, s);

@@ -135,6 +135,7 @@ IterParams make_params(const itmpc_ctx *c) {
   p.partials = c->partials;
   p.group_rec = c->group_rec;
   p.counters = c->counters;
+  p.grid_bar = c->counters + (c->n_counters - 2);
   p.stats = c->stats;
   p.status = c->status;
   return p;
@@ -350,6 +351,9 @@ itmpc_status itmpc_read_status(itmpc_ctx *c) {
   CK(c, cudaStreamSynchronize(c->stream), "sync");
   if (s != 0) {
     CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "status reset");
+    // a wait that ran out may have left merge counters or the grid barrier half-way
+    if (s == ITMPC_ERR_TIMEOUT)
+      CK(c, cudaMemsetAsync(c->counters, 0, sizeof(unsigned int) * c->n_counters, c->stream), "counter reset");
     CK(c, cudaStreamSynchronize(c->stream), "sync");
     if (s == ITMPC_ERR_NONFINITE) return fail(c, ITMPC_ERR_NONFINITE, "every rollout cost was non-finite; U unchanged");
     return fail(c, (itmpc_status)s, "device status %d", s);

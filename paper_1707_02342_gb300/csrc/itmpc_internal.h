@@ -50,6 +50,8 @@ struct IterParams {
   float *partials;     // n_cta x partial_len(T): one record per CTA
   float *group_rec;    // n_group x partial_len(T): one record per group of CTAs
   unsigned int *counters;  // 1 + n_group arrival counters, zero between launches
+  unsigned int *grid_bar;  // 2 words (arrivals, generation) of the grid barrier
+  int coop;                // 1: cooperative launch, every CTA resident (grid barrier + distributed merge)
   int group;           // CTAs per first-level merge group
   int stage_floats;    // shared memory (floats) from the end of the U block available to the merge
   float *stats;        // ITMPC_STATS_LEN
@@ -61,11 +63,12 @@ struct IterParams {
   int n_states;
 };
 
-// Launch shape of the FP32 fused kernel: one warp per sample, nwarps samples
-// per CTA, and `group` CTAs per first-level merge group.
+// Launch shape of the FP32 fused kernel: nwarps warps per CTA, spw samples per
+// warp, and `group` CTAs per first-level merge group.
 struct Fp32Tile {
   int nwarps;
   int group;
+  int spw;
 };
 
 // Scratch sizes (in floats / counters) an iteration of K samples and horizon
