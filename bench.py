@@ -308,7 +308,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": n * launches_per_step,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "iterate_fp32_kernel<32,4> (fused noise, rollout, cost, weights, update)",
+                     "kernel": "iterate_fp32_kernel (fused noise, rollout, cost, weights, update)",
                      "peak_derivation": f"{n_sm} SMs x 128 FP32 lanes x 2 FLOP x {sm_max:.0f} MHz (max SM clock)",
                      "algorithmic_flop_per_launch": FLOP_PER_SAMPLE_STEP * K_WORK * T_WORK},
         "clocks": clocks,

@@ -47,7 +47,7 @@ __host__ __device__ inline SmemLayout fp32_layout(int T, int H, int nw, int spw)
   L.traj = off; off += align16(sizeof(float4) * (size_t)scta * (T + 1));
   L.pos = off;  off += align16(sizeof(float4) * (size_t)scta * T);
   L.W2T = off;  off += (H > 32) ? align16(sizeof(float) * (size_t)H * H) : 0;
-  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * (spw == 2 ? 2 * 32 * 36 + 2 * 36 : (H == 32 ? 32 * 36 + 32 : 2 * H)));
+  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * (spw == 2 ? 2 * 32 * 36 + 16 + 80 : (H == 32 ? 32 * 36 + 32 : 2 * H)));
   L.W3b3 = off; off += align16(sizeof(float) * (4 * H + 4));
   L.S = off;    off += align16(sizeof(float) * scta);
   L.e = off;    off += align16(sizeof(float) * scta);
@@ -515,7 +515,12 @@ __device__ __forceinline__ void recurrence_ring32(const IterParams &p, const flo
 // every 32 steps with lane = step), but every activation broadcast now feeds
 // two FMAs per lane, halving the shared-memory -> register traffic per sample
 // step, which bounds the one-neuron-per-lane form at this sample count.
-constexpr int kHalfWarpBuf = 2 * 32 * kRingStride + 2 * kRingStride;  // two rings + two h1 rows
+// Per-warp buffer: ring 0 at 0, ring 1 at 32 rows + 16 floats (the other 16
+// banks), then the two h1 rows at +0 and +48 floats: the halves' stores and
+// loads never share a bank.
+constexpr int kRing1 = 32 * kRingStride + 16;
+constexpr int kHrows = kRing1 + 32 * kRingStride;
+constexpr int kHalfWarpBuf = kHrows + 80;
 
 template <int ACT>
 __device__ __forceinline__ void recurrence_half32(const IterParams &p, const float *net, float *wbuf,
@@ -524,8 +529,8 @@ __device__ __forceinline__ void recurrence_half32(const IterParams &p, const flo
   constexpr int H = 32;
   const int h = lane >> 4, j = lane & 15;
   const int s = s_first + h;
-  float *ring = wbuf + h * 32 * kRingStride;
-  float *hB = wbuf + 2 * 32 * kRingStride + h * kRingStride;
+  float *ring = wbuf + h * kRing1;
+  float *hB = wbuf + kHrows + h * 48;
   const float4 *hB4 = reinterpret_cast<const float4 *>(hB);
   const float2 *gvr = gv_s + (size_t)s * T;
   float4 *traj = traj_s + (size_t)s * (T + 1);
