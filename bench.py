@@ -153,6 +153,58 @@ def cpu_oracle_rate(seconds: float = 10.0, min_iters: int = 2):
                       f"in {dt:.1f} s"}, dt / n
 
 
+def measure_batched(params, layers, steps: int = 10, warmup: int = 3):
+    """The batching form: 256 independent instances (K in {512..8192}, T in {40, 60, 100, 150},
+    8 seeded 1024 x 1024 spline maps; instance table seed 7) in one itmpc_iterate_batch call."""
+    import numpy as np
+    import torch
+
+    from paper_1707_02342_gb300 import inputs, itmpc
+
+    Ks, Ts, ms = inputs.instance_table(256, seed=7)
+    maps = [inputs.track_costmap(inputs.spline_centerline(seed), 1024, 0.1, 2.5) for seed in range(1, 9)]
+    p = dict(params)
+    ctl = itmpc.Controller(int(Ks.max()), int(Ts.max()), T_max=int(Ts.max()), hidden=H_WORK, **p)
+    ctl.set_dynamics([(torch.tensor(W, device="cuda"), torch.tensor(b, device="cuda")) for W, b in layers])
+    ctl.set_costmaps([torch.tensor(m.data, device="cuda") for m in maps], maps[0].res, maps[0].origin_x,
+                     maps[0].origin_y)
+    ctl.reserve_batch(256, int(Ks.sum()))
+    insts = []
+    for i, (K, T, m) in enumerate(zip(Ks, Ts, ms)):
+        x0 = inputs.start_state(maps[m].centerline)
+        x0[4] = 4.0
+        U = torch.tensor(inputs.nominal_controls(int(T), seed=100 + i, scale=0.2), device="cuda")
+        insts.append(dict(K=int(K), T=int(T), map_index=int(m), instance=i, iter=0,
+                          x0=torch.tensor(x0, device="cuda"), U=U, U_out=U))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for it in range(warmup):
+        for d in insts:
+            d["iter"] = it
+        ctl.iterate_batch(insts)
+    torch.cuda.synchronize()
+    assert ctl.read_status() == itmpc.OK
+    times = []
+    for it in range(steps):
+        for d in insts:
+            d["iter"] = warmup + it
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctl.iterate_batch(insts)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    assert ctl.read_status() == itmpc.OK
+    ctl.close()
+    ms_per = float(np.mean(times))
+    sample_steps = int((Ks.astype(np.int64) * Ts).sum())
+    achieved = FLOP_PER_SAMPLE_STEP * sample_steps / (ms_per * 1e-3) / 1e12
+    return {"workload": "256 instances, K~U{512..8192}, T~U{40,60,100,150}, 8 spline maps 1024^2, H=32 FP32",
+            "sample_steps_per_launch": sample_steps, "ms_per_step": ms_per, "value": sample_steps / (ms_per * 1e-3),
+            "unit": UNIT, "gpu_launches_per_step": 2, "achieved_tflops": achieved}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     d = json.load(open(path)) if os.path.exists(path) else {}
@@ -313,6 +365,12 @@ def run_ours(args, rank, world, local_rank):
                      "algorithmic_flop_per_launch": FLOP_PER_SAMPLE_STEP * K_WORK * T_WORK},
         "clocks": clocks,
     }
+    if world == 1 and not args.no_forms:
+        bt = measure_batched(params, layers)
+        bt["roofline"] = {"bound": "alu", "achieved": bt.pop("achieved_tflops"), "peak": peak_tflops,
+                          "unit": "TFLOP/s"}
+        bt["roofline"]["frac"] = bt["roofline"]["achieved"] / peak_tflops
+        line["forms"] = {"batched": bt}
     if world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_oracle_rate(seconds=args.cpu_seconds)
         line["cpu_baseline"] = cb
@@ -328,6 +386,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / precision / adjoint forms")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -161,6 +161,43 @@ itmpc_status itmpc_read_status(itmpc_ctx *ctx);
  * out[4] number of finite costs, out[5..7] reserved. */
 itmpc_status itmpc_get_stats(itmpc_ctx *ctx, float out[ITMPC_STATS_LEN]);
 
+/* Several costmaps of one size (the batched form's maps), map i at maps[i].
+ * Replaces the map set by itmpc_set_costmap (which is the n_maps = 1 case);
+ * single-instance iterations use map 0. */
+itmpc_status itmpc_set_costmaps(itmpc_ctx *ctx, int32_t n_maps, const float *const *maps, int32_t width,
+                                int32_t height, float res, float origin_x, float origin_y, int32_t on_device);
+
+/* One independent MPC problem of a batched iteration (SURVEY config "batching").
+ * Every instance shares the context's network and parameters (lambda, sigma,
+ * costs, seed); it has its own size, costmap, start state and nominal
+ * controls.  Pointers are device pointers; weights, costs and stats may be
+ * NULL (stats: ITMPC_STATS_LEN floats as itmpc_get_stats). */
+typedef struct {
+  int32_t K, T;       /* samples and horizon (T <= the context's T_max) */
+  int32_t map_index;  /* index into itmpc_set_costmaps */
+  uint32_t instance;  /* Philox instance tag (high half of counter word 3) */
+  uint64_t iter;      /* Philox counter words 2-3 */
+  const float *x0;    /* 7 floats */
+  const float *U;     /* T x 2 */
+  float *U_out;       /* T x 2, may alias U */
+  float *weights;     /* K or NULL */
+  float *costs;       /* K or NULL */
+  float *stats;       /* ITMPC_STATS_LEN or NULL */
+} itmpc_instance;
+
+/* Reserve device memory for batched iterations of up to max_instances
+ * instances with at most max_total_samples samples in all (no allocation
+ * happens in itmpc_iterate_batch).  Requires hidden == 32. */
+itmpc_status itmpc_reserve_batch(itmpc_ctx *ctx, int32_t max_instances, int64_t max_total_samples);
+
+/* One control iteration of n independent instances in one launch (Alg. 1 and
+ * Alg. 2 per instance; the thread-per-sample kernels of iterate_tps.cu): a
+ * persistent kernel pulls (instance, 128-sample tile) work units, longest
+ * horizon first, then one CTA per instance merges its partial sums.  inst is
+ * a host array of n descriptors.  Asynchronous; an instance whose costs are
+ * all non-finite gets U_out = U and records ITMPC_ERR_NONFINITE. */
+itmpc_status itmpc_iterate_batch(itmpc_ctx *ctx, int32_t n, const itmpc_instance *inst);
+
 /* Diagnostics for stage-wise checks.
  * itmpc_noise: eps of iteration iter for every (k, t), device K x T x 2.
  * itmpc_rollout_states: the full rollout of samples 0..n-1 (device,

@@ -1,0 +1,286 @@
+// iterate_tps.cu -- thread-per-sample FP32 IT-MPC iterations for many samples:
+// a single instance with large K, or many independent instances in one launch.
+//
+// One thread rolls out one sample (Alg. 1, inner loop) through the whole
+// network of Sec. V-B: the weights live in the kernel parameter space, so
+// every FMA reads its weight straight from the constant bank and nothing is
+// broadcast through shared memory; each layer offers H independent FMA
+// chains per thread.  The thread draws its own noise (Philox + Box-Muller),
+// integrates the kinematics and adds the running cost of Sec. V-C after every
+// step, so a step needs no communication at all.  This wins when there are
+// enough samples to keep every SM busy; at a few thousand samples the
+// warp-per-sample kernel of iterate_fp32.cu is faster.
+//
+// Kernel 1 (persistent): CTAs pull work units -- kTpsThreads consecutive
+// samples of one instance, longest horizon first -- from a global counter and
+// write one partial record per unit (rho_c, eta_c, ..., E_c: Alg. 2 shifted by
+// the unit's own minimum).  Kernel 2: one CTA per instance merges that
+// instance's records into U', the weights and the diagnostics (log-sum-exp
+// merge of itmpc_merge.cuh) and resets the unit counter for the next launch.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "itmpc_device.cuh"
+#include "itmpc_merge.cuh"
+
+namespace itmpc {
+
+namespace {
+
+template <int H>
+struct TpsParams {
+  TpsShared sh;
+  TpsNet<H> net;
+};
+
+__device__ __forceinline__ float2 tps_noise(const TpsShared &sh, uint32_t k, uint32_t t, uint32_t c2, uint32_t c3) {
+  const uint4 w = philox4x32_10(make_uint4(k, t, c2, c3), sh.key0, sh.key1);
+  const float2 z = box_muller(w.x, w.y);
+  return make_float2(sh.sigma0 * z.x, sh.sigma1 * z.y);
+}
+
+// h(p_x, p_y): bilinear, texel (i, j) centred at origin + (j + 1/2, i + 1/2) res, clamp-to-edge.
+__device__ __forceinline__ float tps_costmap(const TpsShared &sh, const float *map, float px, float py) {
+  const float fx = (px - sh.origin_x) * sh.inv_res - 0.5f;
+  const float fy = (py - sh.origin_y) * sh.inv_res - 0.5f;
+  const float jf = floorf(fx), if_ = floorf(fy);
+  const float a = fx - jf, b = fy - if_;
+  const float jc = fminf(fmaxf(jf, -1.0f), (float)sh.map_w);
+  const float ic = fminf(fmaxf(if_, -1.0f), (float)sh.map_h);
+  const int jj = (int)jc, ii = (int)ic;
+  const int j0 = min(max(jj, 0), sh.map_w - 1), j1 = min(max(jj + 1, 0), sh.map_w - 1);
+  const int i0 = min(max(ii, 0), sh.map_h - 1), i1 = min(max(ii + 1, 0), sh.map_h - 1);
+  const float *r0 = map + (size_t)i0 * sh.map_w;
+  const float *r1 = map + (size_t)i1 * sh.map_w;
+  const float m00 = __ldg(r0 + j0), m01 = __ldg(r0 + j1);
+  const float m10 = __ldg(r1 + j0), m11 = __ldg(r1 + j1);
+  return (1.0f - a) * (1.0f - b) * m00 + a * (1.0f - b) * m01 + (1.0f - a) * b * m10 + a * b * m11;
+}
+
+// State cost at loop index t (Sec. V-C).
+__device__ __forceinline__ float tps_state_cost(const TpsShared &sh, const float *map, float px, float py, float vx,
+                                                float vy, int t) {
+  float h = tps_costmap(sh, map, px, py);
+  h = h > sh.map_cap ? sh.map_cap : h;  // NaN stays NaN
+  const float zeta = -atan2f(vy, fabsf(vx));
+  const float sp = vx - sh.v_des;
+  float imp = 0.0f;
+  if (h > sh.track_thresh) imp += exp2f((float)t * sh.log2_decay) * sh.crash_cost;
+  if (fabsf(zeta) > sh.slip_thresh) imp += sh.crash_cost;
+  return sh.w_track * h + sh.w_speed * sp * sp + sh.w_stab * zeta * zeta + sh.w_crash * imp;
+}
+
+template <int H, int ACT>
+__global__ void __launch_bounds__(kTpsThreads) tps_rollout_kernel(const __grid_constant__ TpsParams<H> P) {
+  constexpr int NWARP = kTpsThreads / 32;
+  const TpsShared &sh = P.sh;
+  const TpsNet<H> &N = P.net;
+  __shared__ float U_s[2 * ITMPC_MAX_T_DEV];
+  __shared__ float e_s[kTpsThreads];
+  __shared__ float red[NWARP][5];
+  __shared__ int unit_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (;;) {
+    __syncthreads();  // the previous unit is done with the shared buffers
+    if (tid == 0) unit_s = (int)atomicAdd(sh.unit_counter, 1u);
+    __syncthreads();
+    const int u = unit_s;
+    if (u >= sh.n_units) return;
+    const TpsUnit un = sh.units[u];
+    const TpsInstance &I = sh.inst[un.inst];
+    const int K = I.K, T = I.T;
+    for (int i = tid; i < 2 * T; i += kTpsThreads) U_s[i] = __ldg(I.U + i);
+    __syncthreads();
+
+    const int k = un.k0 + tid;
+    const bool live = k < K;
+    const bool imp = k < I.n_imp;
+    const float *map = sh.maps + (size_t)I.map * (size_t)sh.map_stride;
+    float S = 0.0f;
+    if (live) {
+      float px = __ldg(I.x0 + 0), py = __ldg(I.x0 + 1), th = __ldg(I.x0 + 2);
+      float xd0 = __ldg(I.x0 + 3), xd1 = __ldg(I.x0 + 4), xd2 = __ldg(I.x0 + 5), xd3 = __ldg(I.x0 + 6);
+      for (int t = 0; t < T; ++t) {
+        const float2 e = tps_noise(sh, (uint32_t)k, (uint32_t)t, I.ctr2, I.ctr3);
+        const float u0 = U_s[2 * t], u1 = U_s[2 * t + 1];
+        const float v0 = imp ? u0 + e.x : e.x, v1 = imp ? u1 + e.y : e.y;
+        const float g0 = fminf(fmaxf(v0, sh.umin0), sh.umax0), g1 = fminf(fmaxf(v1, sh.umin1), sh.umax1);
+        // f(x_d, g(v)): 6 -> H -> H -> 4, weights from the constant bank
+        float h1[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+          float a = N.b1[j];
+          a = fmaf(N.W1[j * 6 + 0], xd0, a);
+          a = fmaf(N.W1[j * 6 + 1], xd1, a);
+          a = fmaf(N.W1[j * 6 + 2], xd2, a);
+          a = fmaf(N.W1[j * 6 + 3], xd3, a);
+          a = fmaf(N.W1[j * 6 + 4], g0, a);
+          a = fmaf(N.W1[j * 6 + 5], g1, a);
+          h1[j] = activation<ACT>(a);
+        }
+        float d0 = N.b3[0], d1 = N.b3[1], d2 = N.b3[2], d3 = N.b3[3];
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+          float a = N.b2[j];
+#pragma unroll
+          for (int i = 0; i < H; ++i) a = fmaf(N.W2[j * H + i], h1[i], a);
+          const float h2 = activation<ACT>(a);
+          d0 = fmaf(N.W3[0 * H + j], h2, d0);
+          d1 = fmaf(N.W3[1 * H + j], h2, d1);
+          d2 = fmaf(N.W3[2 * H + j], h2, d2);
+          d3 = fmaf(N.W3[3 * H + j], h2, d3);
+        }
+        // explicit Euler from the old state (Sec. V-B)
+        float sn, cs;
+        sincosf(th, &sn, &cs);
+        px = fmaf(cs * xd1 - sn * xd2, sh.dt, px);
+        py = fmaf(sn * xd1 + cs * xd2, sh.dt, py);
+        th = fmaf(xd3, sh.dt, th);
+        xd0 = fmaf(d0, sh.dt, xd0);
+        xd1 = fmaf(d1, sh.dt, xd1);
+        xd2 = fmaf(d2, sh.dt, xd2);
+        xd3 = fmaf(d3, sh.dt, xd3);
+        // running cost at x(t + 1) (Alg. 1) and the control-cost term (Sec. III-E)
+        float c = tps_state_cost(sh, map, px, py, xd1, xd2, t + 1);
+        if (sh.gamma != 0.0f) c += sh.gamma * (u0 * v0 * sh.inv_sig2_0 + u1 * v1 * sh.inv_sig2_1);
+        S += c;
+      }
+      I.costs[k] = S;
+    }
+
+    // this unit's partial record (Alg. 2 shifted by the unit's own minimum)
+    const bool fin = live && isfinite(S);
+    float m = warp_min(fin ? S : INFINITY);
+    if (lane == 0) red[warp][0] = m;
+    __syncthreads();
+    float rho = INFINITY;
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) rho = fminf(rho, red[w][0]);
+    const float e = (fin && isfinite(rho)) ? expf(-(S - rho) * sh.inv_lambda) : 0.0f;
+    e_s[tid] = e;
+    const float eta = warp_sum(e), eta_imp = warp_sum(imp && live ? e : 0.0f);
+    const float sq = warp_sum(e * e), nf = warp_sum(fin ? 1.0f : 0.0f);
+    __syncthreads();  // every thread has read red[.][0]
+    if (lane == 0) {
+      red[warp][1] = eta; red[warp][2] = eta_imp; red[warp][3] = sq; red[warp][4] = nf;
+    }
+    __syncthreads();
+    const int PL = partial_len(T);
+    float *rec = sh.partials + I.rec_off + (size_t)un.idx * PL;
+    if (tid == 0) {
+      float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
+      for (int w = 0; w < NWARP; ++w) { a += red[w][1]; b += red[w][2]; c += red[w][3]; d += red[w][4]; }
+      rec[0] = rho; rec[1] = a; rec[2] = b; rec[3] = c; rec[4] = d;
+      rec[5] = 0.f; rec[6] = 0.f; rec[7] = 0.f;
+    }
+    // E_c[t] = sum_s e_s eps_s(t): item (t, quarter) sums 32 samples; the noise is
+    // drawn again from its counter (samples with e = 0 are skipped)
+    const int rounds = (4 * T + kTpsThreads - 1) / kTpsThreads;
+    for (int r = 0; r < rounds; ++r) {
+      const int item = tid + r * kTpsThreads;
+      const bool valid = item < 4 * T;
+      const int t = item >> 2, q = item & 3;
+      float a0 = 0.f, a1 = 0.f;
+      if (valid) {
+        for (int s2 = q * 32; s2 < q * 32 + 32; ++s2) {
+          const float es = e_s[s2];
+          if (es != 0.0f) {
+            const float2 ep = tps_noise(sh, (uint32_t)(un.k0 + s2), (uint32_t)t, I.ctr2, I.ctr3);
+            a0 = fmaf(es, ep.x, a0);
+            a1 = fmaf(es, ep.y, a1);
+          }
+        }
+      }
+      a0 += __shfl_xor_sync(FULL_MASK, a0, 1);
+      a1 += __shfl_xor_sync(FULL_MASK, a1, 1);
+      a0 += __shfl_xor_sync(FULL_MASK, a0, 2);
+      a1 += __shfl_xor_sync(FULL_MASK, a1, 2);
+      if (valid && q == 0) {
+        rec[8 + 2 * t] = a0;
+        rec[8 + 2 * t + 1] = a1;
+      }
+    }
+  }
+}
+
+constexpr int kMergeThreads = 256;
+
+__global__ void __launch_bounds__(kMergeThreads) tps_merge_kernel(const __grid_constant__ TpsShared sh,
+                                                                  int stage_floats) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sh.unit_counter = 0u;  // the rollout kernel has finished
+  const TpsInstance &I = sh.inst[blockIdx.x];
+  IterParams q{};
+  q.K = I.K;
+  q.T = I.T;
+  q.lambda = sh.lambda;
+  q.inv_lambda = sh.inv_lambda;
+  q.U = I.U;
+  q.U_out = I.U_out;
+  q.weights = I.weights;
+  q.weights_inline = 1;
+  q.costs = I.costs;
+  q.stats = I.stats;
+  q.status = sh.status;
+  if (threadIdx.x == 0) mbar_init(&mbar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  merge_records<kMergeThreads>(q, sh.partials + I.rec_off, I.n_units, nullptr, reinterpret_cast<float *>(smem),
+                               stage_floats, &mbar, phase);
+}
+
+template <int H, int ACT>
+cudaError_t tps_launch_h(const TpsShared &sh, const float *net_host, cudaStream_t s) {
+  TpsParams<H> P;
+  P.sh = sh;
+  // packed layout W1 [H][6], b1 [H], W2 [H][H], b2 [H], W3 [4][H], b3 [4] (== TpsNet field order)
+  static_assert(sizeof(TpsNet<H>) == sizeof(float) * (size_t)net_floats(H), "network layout");
+  memcpy(&P.net, net_host, sizeof(TpsNet<H>));
+  auto kern = tps_rollout_kernel<H, ACT>;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTpsThreads, 0)) != cudaSuccess) return e;
+  const int grid = std::min(sh.n_units, std::max(1, per_sm) * sms);
+  kern<<<grid, kTpsThreads, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tps_merge_smem_bytes(int max_units_per_instance, int T_max) {
+  const size_t n = (size_t)max_units_per_instance;
+  return sizeof(float) * (((n + 3) & ~size_t(3)) + n * (size_t)partial_len(T_max) + 4);
+}
+
+cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, cudaStream_t s) {
+  if (sh.n_units <= 0 || sh.n_inst <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (H == 32) e = activation == 1 ? tps_launch_h<32, 1>(sh, net_host, s) : tps_launch_h<32, 0>(sh, net_host, s);
+  else return cudaErrorInvalidValue;  // the weights of wider networks do not fit the parameter space
+  if (e != cudaSuccess) return e;
+  // merge: stage as many records as the device allows (the merge chunks the rest)
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  size_t smem = 96 * 1024;
+  if (smem > (size_t)optin) smem = (size_t)optin;
+  static size_t configured[64] = {};
+  if (dev >= 0 && dev < 64 && configured[dev] < smem) {
+    if ((e = cudaFuncSetAttribute(tps_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    configured[dev] = smem;
+  }
+  tps_merge_kernel<<<sh.n_inst, kMergeThreads, smem, s>>>(sh, (int)(smem / sizeof(float)));
+  return cudaGetLastError();
+}
+
+}  // namespace itmpc

@@ -6,7 +6,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "itmpc.h"
 #include "itmpc_internal.h"
@@ -19,8 +21,9 @@ struct itmpc_ctx {
   cudaStream_t stream = nullptr;
   float *net = nullptr;
   bool have_net = false;
-  float *map = nullptr;
-  int map_w = 0, map_h = 0;
+  std::vector<float> net_host;  // host copy of the packed network (kernel-parameter weights)
+  float *map = nullptr;         // n_maps maps of map_w x map_h, contiguous
+  int map_w = 0, map_h = 0, n_maps = 0;
   float res = 1.f, origin_x = 0.f, origin_y = 0.f;
   bool have_map = false;
   float *partials = nullptr, *group_rec = nullptr, *scale = nullptr, *costs = nullptr, *stats = nullptr;
@@ -30,6 +33,14 @@ struct itmpc_ctx {
   // device staging for the host-pointer entry point
   float *x0_d = nullptr, *U_d = nullptr, *Uout_d = nullptr, *w_d = nullptr;
   size_t smem_optin = 0;
+  // batched iterations (itmpc_reserve_batch)
+  int batch_max_inst = 0, batch_max_units = 0;
+  int64_t batch_max_samples = 0;
+  TpsInstance *inst_d = nullptr, *inst_h = nullptr;
+  TpsUnit *units_d = nullptr, *units_h = nullptr;
+  float *batch_partials = nullptr, *batch_costs = nullptr, *batch_stats = nullptr;
+  unsigned int *unit_counter = nullptr;
+  cudaEvent_t staged = nullptr;  // the last H2D copy of the staging buffers
   std::string err;
 };
 
@@ -179,6 +190,12 @@ void free_ctx(itmpc_ctx *c) {
     if (b) cudaFree(b);
   if (c->counters) cudaFree(c->counters);
   if (c->status) cudaFree(c->status);
+  void *bbufs[] = {c->inst_d, c->units_d, c->batch_partials, c->batch_costs, c->batch_stats, c->unit_counter};
+  for (void *b : bbufs)
+    if (b) cudaFree(b);
+  if (c->inst_h) cudaFreeHost(c->inst_h);
+  if (c->units_h) cudaFreeHost(c->units_h);
+  if (c->staged) cudaEventDestroy(c->staged);
   delete c;
 }
 
@@ -284,37 +301,180 @@ itmpc_status itmpc_set_dynamics(itmpc_ctx *c, int32_t n_layers, const int32_t *w
       CK(c, cudaMemcpyAsync(c->net + offb[l], b[l], sizeof(float) * nb[l], cudaMemcpyHostToDevice, c->stream), "b copy");
     }
   }
-  if (!on_device) CK(c, cudaStreamSynchronize(c->stream), "sync");
+  c->net_host.resize((size_t)net_floats(H));
+  CK(c, cudaMemcpyAsync(c->net_host.data(), c->net, sizeof(float) * c->net_host.size(), cudaMemcpyDeviceToHost,
+                        c->stream), "network read-back");
+  CK(c, cudaStreamSynchronize(c->stream), "sync");
   c->have_net = true;
   return ITMPC_OK;
 }
 
-itmpc_status itmpc_set_costmap(itmpc_ctx *c, const float *map, int32_t width, int32_t height, float res,
-                               float origin_x, float origin_y, int32_t on_device) {
+itmpc_status itmpc_set_costmaps(itmpc_ctx *c, int32_t n_maps, const float *const *maps, int32_t width,
+                                int32_t height, float res, float origin_x, float origin_y, int32_t on_device) {
   if (!c) return ITMPC_ERR_ARG;
-  if (!map || width < 1 || height < 1 || (int64_t)width * height > (int64_t)1 << 30)
-    return fail(c, ITMPC_ERR_ARG, "bad costmap shape %d x %d", width, height);
+  if (n_maps < 1 || !maps || width < 1 || height < 1 || (int64_t)width * height > (int64_t)1 << 30)
+    return fail(c, ITMPC_ERR_ARG, "bad costmap shape %d x %d (x %d)", width, height, n_maps);
+  for (int i = 0; i < n_maps; ++i)
+    if (!maps[i]) return fail(c, ITMPC_ERR_ARG, "costmap %d is NULL", i);
   if (!(res > 0.f) || !finite(res) || !finite(origin_x) || !finite(origin_y))
     return fail(c, ITMPC_ERR_ARG, "res must be finite and > 0, origin finite");
   const size_t n = (size_t)width * height;
-  if (!c->map || (size_t)c->map_w * c->map_h != n) {
+  if (!c->map || (size_t)c->map_w * c->map_h * c->n_maps != n * n_maps) {
     if (c->map) {
       CK(c, cudaStreamSynchronize(c->stream), "sync");
       cudaFree(c->map);
       c->map = nullptr;
       c->have_map = false;
     }
-    CK(c, cudaMalloc((void **)&c->map, sizeof(float) * n), "costmap cudaMalloc");
+    CK(c, cudaMalloc((void **)&c->map, sizeof(float) * n * n_maps), "costmap cudaMalloc");
   }
-  CK(c, cudaMemcpyAsync(c->map, map, sizeof(float) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                        c->stream), "costmap copy");
+  for (int i = 0; i < n_maps; ++i)
+    CK(c, cudaMemcpyAsync(c->map + n * i, maps[i], sizeof(float) * n,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+       "costmap copy");
   if (!on_device) CK(c, cudaStreamSynchronize(c->stream), "sync");
   c->map_w = width;
   c->map_h = height;
+  c->n_maps = n_maps;
   c->res = res;
   c->origin_x = origin_x;
   c->origin_y = origin_y;
   c->have_map = true;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_set_costmap(itmpc_ctx *c, const float *map, int32_t width, int32_t height, float res,
+                               float origin_x, float origin_y, int32_t on_device) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (!map) return fail(c, ITMPC_ERR_ARG, "costmap is NULL");
+  const float *maps[1] = {map};
+  return itmpc_set_costmaps(c, 1, maps, width, height, res, origin_x, origin_y, on_device);
+}
+
+itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances, int64_t max_total_samples) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (c->H != 32) return fail(c, ITMPC_ERR_ARG, "batched iterations need hidden == 32");
+  if (max_instances < 1 || max_total_samples < 1 || max_total_samples > ((int64_t)1 << 31))
+    return fail(c, ITMPC_ERR_ARG, "bad batch capacity");
+  CK(c, cudaStreamSynchronize(c->stream), "sync");
+  void *old[] = {c->inst_d, c->units_d, c->batch_partials, c->batch_costs, c->batch_stats, c->unit_counter};
+  for (void *b : old)
+    if (b) cudaFree(b);
+  if (c->inst_h) cudaFreeHost(c->inst_h);
+  if (c->units_h) cudaFreeHost(c->units_h);
+  c->inst_d = c->inst_h = nullptr;
+  c->units_d = c->units_h = nullptr;
+  c->batch_partials = c->batch_costs = c->batch_stats = nullptr;
+  c->unit_counter = nullptr;
+  const int64_t max_units = max_total_samples / kTpsThreads + max_instances;
+  if (max_units > ((int64_t)1 << 30)) return fail(c, ITMPC_ERR_ARG, "batch too large");
+  CK(c, cudaMalloc((void **)&c->inst_d, sizeof(TpsInstance) * max_instances), "batch cudaMalloc");
+  CK(c, cudaMalloc((void **)&c->units_d, sizeof(TpsUnit) * max_units), "batch cudaMalloc");
+  CK(c, cudaMalloc((void **)&c->batch_partials, sizeof(float) * max_units * partial_len(c->T_max)),
+     "batch cudaMalloc");
+  CK(c, cudaMalloc((void **)&c->batch_costs, sizeof(float) * max_total_samples), "batch cudaMalloc");
+  CK(c, cudaMalloc((void **)&c->batch_stats, sizeof(float) * ITMPC_STATS_LEN * max_instances), "batch cudaMalloc");
+  CK(c, cudaMalloc((void **)&c->unit_counter, sizeof(unsigned int)), "batch cudaMalloc");
+  CK(c, cudaMallocHost((void **)&c->inst_h, sizeof(TpsInstance) * max_instances), "batch cudaMallocHost");
+  CK(c, cudaMallocHost((void **)&c->units_h, sizeof(TpsUnit) * max_units), "batch cudaMallocHost");
+  if (!c->staged) CK(c, cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming), "event");
+  CK(c, cudaMemsetAsync(c->unit_counter, 0, sizeof(unsigned int), c->stream), "memset");
+  CK(c, cudaStreamSynchronize(c->stream), "sync");
+  c->batch_max_inst = max_instances;
+  c->batch_max_units = (int)max_units;
+  c->batch_max_samples = max_total_samples;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_iterate_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (!c->inst_d) return fail(c, ITMPC_ERR_STATE, "itmpc_reserve_batch has not been called");
+  if (n < 1 || n > c->batch_max_inst || !inst) return fail(c, ITMPC_ERR_ARG, "n=%d outside [1, %d]", n, c->batch_max_inst);
+  int64_t total = 0;
+  int units = 0;
+  for (int i = 0; i < n; ++i) {
+    const itmpc_instance &q = inst[i];
+    if (q.K < 1 || q.T < 1 || q.T > c->T_max) return fail(c, ITMPC_ERR_ARG, "instance %d: bad K/T", i);
+    if (q.map_index < 0 || q.map_index >= c->n_maps) return fail(c, ITMPC_ERR_ARG, "instance %d: bad map", i);
+    if (!q.x0 || !q.U || !q.U_out) return fail(c, ITMPC_ERR_ARG, "instance %d: NULL pointer", i);
+    total += q.K;
+    units += (q.K + kTpsThreads - 1) / kTpsThreads;
+  }
+  if (total > c->batch_max_samples || units > c->batch_max_units)
+    return fail(c, ITMPC_ERR_ARG, "batch exceeds the reserved capacity");
+  // the previous call's copies out of the staging buffers must have finished
+  CK(c, cudaEventSynchronize(c->staged), "event sync");
+  const itmpc_config &g = c->cfg;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return inst[a].T > inst[b].T; });
+  int64_t rec_off = 0, cost_off = 0;
+  for (int i = 0; i < n; ++i) {
+    const itmpc_instance &q = inst[i];
+    TpsInstance &d = c->inst_h[i];
+    d.K = q.K;
+    d.T = q.T;
+    const double nimp = ceil((1.0 - (double)g.alpha_explore) * (double)q.K);
+    d.n_imp = (int)(nimp < 0 ? 0 : (nimp > q.K ? q.K : nimp));
+    d.map = q.map_index;
+    d.ctr2 = (uint32_t)q.iter;
+    d.ctr3 = (uint32_t)((q.iter >> 32) & 0xFFFFu) | (q.instance << 16);
+    d.n_units = (q.K + kTpsThreads - 1) / kTpsThreads;
+    d.rec_off = (int)rec_off;
+    rec_off += (int64_t)d.n_units * partial_len(q.T);
+    d.x0 = q.x0;
+    d.U = q.U;
+    d.U_out = q.U_out;
+    d.weights = q.weights;
+    d.costs = q.costs ? q.costs : c->batch_costs + cost_off;
+    d.stats = q.stats ? q.stats : c->batch_stats + (size_t)ITMPC_STATS_LEN * i;
+    cost_off += q.K;
+  }
+  int u = 0;
+  for (int oi = 0; oi < n; ++oi) {
+    const int i = order[oi];
+    for (int j = 0; j < c->inst_h[i].n_units; ++j) c->units_h[u++] = TpsUnit{i, j * kTpsThreads, j, 0};
+  }
+  CK(c, cudaMemcpyAsync(c->inst_d, c->inst_h, sizeof(TpsInstance) * n, cudaMemcpyHostToDevice, c->stream), "copy");
+  CK(c, cudaMemcpyAsync(c->units_d, c->units_h, sizeof(TpsUnit) * u, cudaMemcpyHostToDevice, c->stream), "copy");
+  CK(c, cudaEventRecord(c->staged, c->stream), "event");
+  TpsShared sh{};
+  sh.key0 = (uint32_t)g.seed;
+  sh.key1 = (uint32_t)(g.seed >> 32);
+  sh.sigma0 = g.sigma[0];
+  sh.sigma1 = g.sigma[1];
+  sh.dt = g.dt;
+  sh.umin0 = g.u_min[0]; sh.umin1 = g.u_min[1];
+  sh.umax0 = g.u_max[0]; sh.umax1 = g.u_max[1];
+  sh.w_track = g.cost_w[0]; sh.w_speed = g.cost_w[1]; sh.w_stab = g.cost_w[2]; sh.w_crash = g.cost_w[3];
+  sh.v_des = g.v_des;
+  sh.crash_cost = g.crash_cost;
+  sh.log2_decay = (float)log2((double)g.crash_decay);
+  sh.track_thresh = g.track_thresh;
+  sh.slip_thresh = g.slip_thresh;
+  sh.map_cap = g.map_cap;
+  sh.gamma = g.gamma;
+  sh.inv_sig2_0 = g.sigma[0] > 0 ? (float)(1.0 / ((double)g.sigma[0] * g.sigma[0])) : 0.f;
+  sh.inv_sig2_1 = g.sigma[1] > 0 ? (float)(1.0 / ((double)g.sigma[1] * g.sigma[1])) : 0.f;
+  sh.lambda = g.lambda;
+  sh.inv_lambda = (float)(1.0 / (double)g.lambda);
+  sh.maps = c->map;
+  sh.map_w = c->map_w;
+  sh.map_h = c->map_h;
+  sh.map_stride = (long long)c->map_w * c->map_h;
+  sh.inv_res = (float)(1.0 / (double)c->res);
+  sh.origin_x = c->origin_x;
+  sh.origin_y = c->origin_y;
+  sh.inst = c->inst_d;
+  sh.units = c->units_d;
+  sh.n_units = u;
+  sh.n_inst = n;
+  sh.T_max = c->T_max;
+  sh.partials = c->batch_partials;
+  sh.unit_counter = c->unit_counter;
+  sh.status = c->status;
+  CK(c, tps_launch(sh, c->net_host.data(), c->H, g.activation, c->stream), "batched launch");
   return ITMPC_OK;
 }
 

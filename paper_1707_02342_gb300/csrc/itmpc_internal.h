@@ -83,6 +83,54 @@ size_t fp32_smem_bytes(int T, int H, Fp32Tile tile);
 int fp32_num_ctas(int K, Fp32Tile tile);
 cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t s);
 cudaError_t launch_finalize_weights(const IterParams &p, cudaStream_t s);
+
+// ---- thread-per-sample path (many samples: large K, or many instances) ----
+constexpr int kTpsThreads = 128;  // samples per work unit (one thread each)
+
+// One MPC instance, as the device sees it.
+struct TpsInstance {
+  int K, T, n_imp, map;
+  uint32_t ctr2, ctr3;
+  int rec_off;   // float offset of its first partial record
+  int n_units;   // its work units = its records (stride partial_len(T))
+  const float *x0, *U;
+  float *U_out, *weights, *costs, *stats;
+};
+
+// A work unit: kTpsThreads consecutive samples of one instance.
+struct TpsUnit {
+  int inst, k0, idx, pad;  // idx: the unit's index within its instance
+};
+
+// Everything the instances share.
+struct TpsShared {
+  uint32_t key0, key1;
+  float sigma0, sigma1, dt, umin0, umin1, umax0, umax1;
+  float w_track, w_speed, w_stab, w_crash;
+  float v_des, crash_cost, log2_decay, track_thresh, slip_thresh, map_cap;
+  float gamma, inv_sig2_0, inv_sig2_1, lambda, inv_lambda;
+  const float *maps;
+  int map_w, map_h;
+  long long map_stride;
+  float inv_res, origin_x, origin_y;
+  const TpsInstance *inst;
+  const TpsUnit *units;
+  int n_units, n_inst, T_max, pad;
+  float *partials;
+  unsigned int *unit_counter;
+  int *status;
+};
+
+// Network values in kernel parameter space (constant bank): FMA operands read
+// the weights directly.
+template <int H>
+struct TpsNet {
+  float W1[H * 6], b1[H], W2[H * H], b2[H], W3[4 * H], b3[4];
+};
+
+// Launch the rollout (persistent over work units) and the per-instance merge.
+cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, cudaStream_t s);
+size_t tps_merge_smem_bytes(int max_units_per_instance, int T_max);
 cudaError_t launch_noise(const IterParams &p, float *eps, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);
 cudaError_t launch_tanh(const float *x, float *y, int64_t n, cudaStream_t s);

@@ -37,12 +37,24 @@ class Config(C.Structure):
     ]
 
 
+class Instance(C.Structure):
+    """Mirror of itmpc_instance (device pointers)."""
+    _fields_ = [
+        ("K", C.c_int32), ("T", C.c_int32), ("map_index", C.c_int32), ("instance", C.c_uint32),
+        ("iter", C.c_uint64), ("x0", C.c_void_p), ("U", C.c_void_p), ("U_out", C.c_void_p),
+        ("weights", C.c_void_p), ("costs", C.c_void_p), ("stats", C.c_void_p),
+    ]
+
+
 SIGNATURES = {
     "itmpc_create": (C.c_int, [C.POINTER(Config), C.POINTER(C.c_void_p)]),
     "itmpc_set_config": (C.c_int, [_vp, C.POINTER(Config)]),
     "itmpc_set_stream": (C.c_int, [_vp, _vp]),
     "itmpc_set_dynamics": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i32]),
     "itmpc_set_costmap": (C.c_int, [_vp, _vp, _i32, _i32, _f, _f, _f, _i32]),
+    "itmpc_set_costmaps": (C.c_int, [_vp, _i32, _vp, _i32, _i32, _f, _f, _f, _i32]),
+    "itmpc_reserve_batch": (C.c_int, [_vp, _i32, _i64]),
+    "itmpc_iterate_batch": (C.c_int, [_vp, _i32, _vp]),
     "itmpc_iterate": (C.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "itmpc_iterate_host": (C.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "itmpc_read_status": (C.c_int, [_vp]),
@@ -196,6 +208,26 @@ class Controller:
         """cmap: (height, width) CUDA float32 tensor."""
         h, w = cmap.shape
         self._check(self._L.itmpc_set_costmap(self._h, _dptr(cmap), w, h, res, origin_x, origin_y, 1))
+
+    def set_costmaps(self, cmaps, res: float, origin_x: float, origin_y: float):
+        """cmaps: list of (height, width) CUDA float32 tensors of one size."""
+        h, w = cmaps[0].shape
+        ptrs = (C.c_void_p * len(cmaps))(*[_dptr(m) for m in cmaps])
+        self._check(self._L.itmpc_set_costmaps(self._h, len(cmaps), ptrs, w, h, res, origin_x, origin_y, 1))
+
+    def reserve_batch(self, max_instances: int, max_total_samples: int):
+        self._check(self._L.itmpc_reserve_batch(self._h, max_instances, max_total_samples))
+
+    def iterate_batch(self, instances):
+        """instances: list of dicts with K, T, map_index, instance, iter, x0, U, U_out and optional
+        weights, costs, stats (CUDA tensors).  Queued on the context's stream."""
+        arr = (Instance * len(instances))()
+        for a, d in zip(arr, instances):
+            a.K, a.T, a.map_index = d["K"], d["T"], d.get("map_index", 0)
+            a.instance, a.iter = d.get("instance", 0), d.get("iter", 0)
+            a.x0, a.U, a.U_out = _dptr(d["x0"]), _dptr(d["U"]), _dptr(d["U_out"])
+            a.weights, a.costs, a.stats = _dptr(d.get("weights")), _dptr(d.get("costs")), _dptr(d.get("stats"))
+        self._check(self._L.itmpc_iterate_batch(self._h, len(instances), arr))
 
     def iterate(self, x0, U, it: int, U_out, weights=None, costs=None):
         """Queue one iteration on the context's stream (device tensors)."""
