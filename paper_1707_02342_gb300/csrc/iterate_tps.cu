@@ -74,8 +74,59 @@ __device__ __forceinline__ float tps_state_cost(const TpsShared &sh, const float
   return sh.w_track * h + sh.w_speed * sp * sp + sh.w_stab * zeta * zeta + sh.w_crash * imp;
 }
 
+// Weight pair (w[i], w[i + 1]) from the parameter space; i even, the array 8-byte aligned.
+__device__ __forceinline__ unsigned long long wpair(const float *w, int i) {
+  return *reinterpret_cast<const unsigned long long *>(w + i);
+}
+
+// d = W3 tanh(W2 tanh(W1 z + b1) + b2) + b3 for one sample, z = (x_d, g(v)).
 template <int H, int ACT>
-__global__ void __launch_bounds__(kTpsThreads) tps_rollout_kernel(const __grid_constant__ TpsParams<H> P) {
+__device__ __forceinline__ void tps_network(const TpsNet<H> &N, float x0, float x1, float x2, float x3, float g0,
+                                            float g1, float &d0, float &d1, float &d2, float &d3) {
+  const unsigned long long zero = f2pack(0.0f, 0.0f);
+  const unsigned long long z01 = f2pack(x0, x1), z23 = f2pack(x2, x3), z45 = f2pack(g0, g1);
+  unsigned long long h1[H / 2];
+#pragma unroll
+  for (int j = 0; j < H; j += 2) {
+    float a[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      unsigned long long acc = ffma2(wpair(N.W1, (j + q) * 6), z01, zero);
+      acc = ffma2(wpair(N.W1, (j + q) * 6 + 2), z23, acc);
+      acc = ffma2(wpair(N.W1, (j + q) * 6 + 4), z45, acc);
+      const float2 r = f2unpack(acc);
+      a[q] = activation<ACT>((r.x + N.b1[j + q]) + r.y);
+    }
+    h1[j / 2] = f2pack(a[0], a[1]);
+  }
+  unsigned long long h2[H / 2];
+#pragma unroll
+  for (int j = 0; j < H; j += 2) {
+    float a[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      unsigned long long acc = ffma2(wpair(N.W2, (j + q) * H), h1[0], zero);
+#pragma unroll
+      for (int i = 2; i < H; i += 2) acc = ffma2(wpair(N.W2, (j + q) * H + i), h1[i / 2], acc);
+      const float2 r = f2unpack(acc);
+      a[q] = activation<ACT>((r.x + N.b2[j + q]) + r.y);
+    }
+    h2[j / 2] = f2pack(a[0], a[1]);
+  }
+  float d[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    unsigned long long acc = ffma2(wpair(N.W3, o * H), h2[0], zero);
+#pragma unroll
+    for (int i = 2; i < H; i += 2) acc = ffma2(wpair(N.W3, o * H + i), h2[i / 2], acc);
+    const float2 r = f2unpack(acc);
+    d[o] = (r.x + N.b3[o]) + r.y;
+  }
+  d0 = d[0]; d1 = d[1]; d2 = d[2]; d3 = d[3];
+}
+
+template <int H, int ACT>
+__global__ void __launch_bounds__(kTpsThreads, 5) tps_rollout_kernel(const __grid_constant__ TpsParams<H> P) {
   constexpr int NWARP = kTpsThreads / 32;
   const TpsShared &sh = P.sh;
   const TpsNet<H> &N = P.net;
@@ -110,31 +161,10 @@ __global__ void __launch_bounds__(kTpsThreads) tps_rollout_kernel(const __grid_c
         const float u0 = U_s[2 * t], u1 = U_s[2 * t + 1];
         const float v0 = imp ? u0 + e.x : e.x, v1 = imp ? u1 + e.y : e.y;
         const float g0 = fminf(fmaxf(v0, sh.umin0), sh.umax0), g1 = fminf(fmaxf(v1, sh.umin1), sh.umax1);
-        // f(x_d, g(v)): 6 -> H -> H -> 4, weights from the constant bank
-        float h1[H];
-#pragma unroll
-        for (int j = 0; j < H; ++j) {
-          float a = N.b1[j];
-          a = fmaf(N.W1[j * 6 + 0], xd0, a);
-          a = fmaf(N.W1[j * 6 + 1], xd1, a);
-          a = fmaf(N.W1[j * 6 + 2], xd2, a);
-          a = fmaf(N.W1[j * 6 + 3], xd3, a);
-          a = fmaf(N.W1[j * 6 + 4], g0, a);
-          a = fmaf(N.W1[j * 6 + 5], g1, a);
-          h1[j] = activation<ACT>(a);
-        }
-        float d0 = N.b3[0], d1 = N.b3[1], d2 = N.b3[2], d3 = N.b3[3];
-#pragma unroll
-        for (int j = 0; j < H; ++j) {
-          float a = N.b2[j];
-#pragma unroll
-          for (int i = 0; i < H; ++i) a = fmaf(N.W2[j * H + i], h1[i], a);
-          const float h2 = activation<ACT>(a);
-          d0 = fmaf(N.W3[0 * H + j], h2, d0);
-          d1 = fmaf(N.W3[1 * H + j], h2, d1);
-          d2 = fmaf(N.W3[2 * H + j], h2, d2);
-          d3 = fmaf(N.W3[3 * H + j], h2, d3);
-        }
+        // f(x_d, g(v)): 6 -> H -> H -> 4 with weights from the constant bank, two
+        // products per instruction (packed FP32 pairs, even/odd partial sums)
+        float d0, d1, d2, d3;
+        tps_network<H, ACT>(N, xd0, xd1, xd2, xd3, g0, g1, d0, d1, d2, d3);
         // explicit Euler from the old state (Sec. V-B)
         float sn, cs;
         sincosf(th, &sn, &cs);

@@ -164,8 +164,33 @@ itmpc_status ready(itmpc_ctx *c) {
   return ITMPC_OK;
 }
 
+constexpr int kTpsMinK = 4096;  // from here on one thread per sample beats a warp per sample
+
+}  // namespace
+
+extern "C" itmpc_status itmpc_iterate_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst);
+extern "C" itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances, int64_t max_total_samples);
+
+namespace {
+
 itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
                            float *weights, float *costs, float *states, int n_states, float *eps_out) {
+  if (!states && !eps_out && c->H == 32 && c->cfg.K >= kTpsMinK && c->inst_d) {
+    // many samples: the thread-per-sample kernels, as a batch of one instance
+    itmpc_instance q{};
+    q.K = c->cfg.K;
+    q.T = c->cfg.T;
+    q.map_index = 0;
+    q.instance = c->cfg.instance;
+    q.iter = iter;
+    q.x0 = x0;
+    q.U = U;
+    q.U_out = U_out;
+    q.weights = weights;
+    q.costs = costs ? costs : c->costs;
+    q.stats = c->stats;
+    return itmpc_iterate_batch(c, 1, &q);
+  }
   IterParams p = make_params(c);
   set_iter(p, iter, c->cfg.instance);
   p.x0 = x0;
@@ -248,6 +273,13 @@ itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
   e = cudaMalloc((void **)&c->status, sizeof(int));
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
+  if (c->H == 32 && c->K_cap >= kTpsMinK) {
+    itmpc_status bs = itmpc_reserve_batch(c, 1, c->K_cap);
+    if (bs != ITMPC_OK) {
+      free_ctx(c);
+      return bs;
+    }
+  }
   e = cudaMemset(c->counters, 0, sizeof(unsigned int) * c->n_counters);
   if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(float) * ITMPC_STATS_LEN);

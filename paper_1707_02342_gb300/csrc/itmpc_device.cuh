@@ -67,6 +67,27 @@ __device__ __forceinline__ float tanh_f32(float x) {
   return fmaf(-2.0f, rcp_approx(1.0f + e), 1.0f);
 }
 
+// ---- packed FP32 pairs (sm_100+ fma.rn.f32x2: two IEEE FMAs per instruction) ----
+__device__ __forceinline__ unsigned long long f2pack(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+
+__device__ __forceinline__ float2 f2unpack(unsigned long long r) {
+  float x, y;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
+  return make_float2(x, y);
+}
+
+// (a.x b.x + c.x, a.y b.y + c.y), each rounded once as by fmaf
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 template <int ACT>
 __device__ __forceinline__ float activation(float a) {
   if constexpr (ACT == 1) return a;

@@ -221,3 +221,23 @@ def test_working_size_sampled_parity():
     check_costs(S[ks], S_ref, margins)
     check_stagewise(P, 5, U, Uo, w, S, params["sigma"])
     assert abs(w.sum() - 1) < 1e-5
+
+
+def test_large_K_single_instance_thread_per_sample_path():
+    """K = 8192 through itmpc_iterate runs the thread-per-sample kernels (K >= 4096)."""
+    tmap = problems.spline_map(1)
+    layers = problems.network(32)
+    params = problems.params_working(K=8192, T=60)
+    ctl = G.controller(params, tmap, layers)
+    P = oracle_for(params, tmap, layers)
+    x0 = problems.x0_for(tmap, speed=4.0)
+    U = inputs.nominal_controls(60, seed=19, scale=0.2)
+    Uo, w, S, st = G.run(ctl, x0, U, 8)
+    assert st == 0
+    ks = np.concatenate([np.random.default_rng(5).choice(8192, size=64, replace=False), [0, 4095, 4096, 8191]])
+    S_ref, margins = oracle.rollout_many(P, x0, U, 8, ks)
+    check_costs(S[ks], S_ref, margins)
+    check_stagewise(P, 8, U, Uo, w, S, params["sigma"])
+    stats = ctl.stats()
+    assert stats[0] == pytest.approx(S.min(), rel=1e-6)
+    assert stats[4] == 8192
