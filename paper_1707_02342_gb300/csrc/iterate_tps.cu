@@ -26,6 +26,7 @@
 
 #include "itmpc_device.cuh"
 #include "itmpc_merge.cuh"
+#include "itmpc_units.cuh"
 
 namespace itmpc {
 
@@ -36,43 +37,6 @@ struct TpsParams {
   TpsShared sh;
   TpsNet<H> net;
 };
-
-__device__ __forceinline__ float2 tps_noise(const TpsShared &sh, uint32_t k, uint32_t t, uint32_t c2, uint32_t c3) {
-  const uint4 w = philox4x32_10(make_uint4(k, t, c2, c3), sh.key0, sh.key1);
-  const float2 z = box_muller(w.x, w.y);
-  return make_float2(sh.sigma0 * z.x, sh.sigma1 * z.y);
-}
-
-// h(p_x, p_y): bilinear, texel (i, j) centred at origin + (j + 1/2, i + 1/2) res, clamp-to-edge.
-__device__ __forceinline__ float tps_costmap(const TpsShared &sh, const float *map, float px, float py) {
-  const float fx = (px - sh.origin_x) * sh.inv_res - 0.5f;
-  const float fy = (py - sh.origin_y) * sh.inv_res - 0.5f;
-  const float jf = floorf(fx), if_ = floorf(fy);
-  const float a = fx - jf, b = fy - if_;
-  const float jc = fminf(fmaxf(jf, -1.0f), (float)sh.map_w);
-  const float ic = fminf(fmaxf(if_, -1.0f), (float)sh.map_h);
-  const int jj = (int)jc, ii = (int)ic;
-  const int j0 = min(max(jj, 0), sh.map_w - 1), j1 = min(max(jj + 1, 0), sh.map_w - 1);
-  const int i0 = min(max(ii, 0), sh.map_h - 1), i1 = min(max(ii + 1, 0), sh.map_h - 1);
-  const float *r0 = map + (size_t)i0 * sh.map_w;
-  const float *r1 = map + (size_t)i1 * sh.map_w;
-  const float m00 = __ldg(r0 + j0), m01 = __ldg(r0 + j1);
-  const float m10 = __ldg(r1 + j0), m11 = __ldg(r1 + j1);
-  return (1.0f - a) * (1.0f - b) * m00 + a * (1.0f - b) * m01 + (1.0f - a) * b * m10 + a * b * m11;
-}
-
-// State cost at loop index t (Sec. V-C).
-__device__ __forceinline__ float tps_state_cost(const TpsShared &sh, const float *map, float px, float py, float vx,
-                                                float vy, int t) {
-  float h = tps_costmap(sh, map, px, py);
-  h = h > sh.map_cap ? sh.map_cap : h;  // NaN stays NaN
-  const float zeta = -atan2f(vy, fabsf(vx));
-  const float sp = vx - sh.v_des;
-  float imp = 0.0f;
-  if (h > sh.track_thresh) imp += exp2f((float)t * sh.log2_decay) * sh.crash_cost;
-  if (fabsf(zeta) > sh.slip_thresh) imp += sh.crash_cost;
-  return sh.w_track * h + sh.w_speed * sp * sp + sh.w_stab * zeta * zeta + sh.w_crash * imp;
-}
 
 // Weight pair (w[i], w[i + 1]) from the parameter space; i even, the array 8-byte aligned.
 __device__ __forceinline__ unsigned long long wpair(const float *w, int i) {
@@ -290,14 +254,10 @@ size_t tps_merge_smem_bytes(int max_units_per_instance, int T_max) {
   return sizeof(float) * (((n + 3) & ~size_t(3)) + n * (size_t)partial_len(T_max) + 4);
 }
 
-cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, cudaStream_t s) {
-  if (sh.n_units <= 0 || sh.n_inst <= 0) return cudaSuccess;
-  cudaError_t e;
-  if (H == 32) e = activation == 1 ? tps_launch_h<32, 1>(sh, net_host, s) : tps_launch_h<32, 0>(sh, net_host, s);
-  else return cudaErrorInvalidValue;  // the weights of wider networks do not fit the parameter space
-  if (e != cudaSuccess) return e;
-  // merge: stage as many records as the device allows (the merge chunks the rest)
+cudaError_t tps_merge(const TpsShared &sh, cudaStream_t s) {
+  // stage as many records as the device allows (the merge chunks the rest)
   int dev = 0, optin = 0;
+  cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
   size_t smem = 96 * 1024;
@@ -311,6 +271,15 @@ cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int ac
   }
   tps_merge_kernel<<<sh.n_inst, kMergeThreads, smem, s>>>(sh, (int)(smem / sizeof(float)));
   return cudaGetLastError();
+}
+
+cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, cudaStream_t s) {
+  if (sh.n_units <= 0 || sh.n_inst <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (H == 32) e = activation == 1 ? tps_launch_h<32, 1>(sh, net_host, s) : tps_launch_h<32, 0>(sh, net_host, s);
+  else return cudaErrorInvalidValue;  // the weights of wider networks do not fit the parameter space
+  if (e != cudaSuccess) return e;
+  return tps_merge(sh, s);
 }
 
 }  // namespace itmpc

@@ -41,6 +41,8 @@ struct itmpc_ctx {
   float *batch_partials = nullptr, *batch_costs = nullptr, *batch_stats = nullptr;
   unsigned int *unit_counter = nullptr;
   cudaEvent_t staged = nullptr;  // the last H2D copy of the staging buffers
+  // tensor-core operand images of the H = 128 network: [0] BF16, [1] FP8 layer 2
+  unsigned char *tc_img[2] = {nullptr, nullptr};
   std::string err;
 };
 
@@ -101,7 +103,14 @@ itmpc_status check_config(const itmpc_config *cfg, char *msg, size_t n) {
   for (int i = 0; i < 4; ++i)
     if (!finite(cfg->cost_w[i])) { snprintf(msg, n, "cost_w[%d] not finite", i); return ITMPC_ERR_ARG; }
   if (!(cfg->crash_decay > 0.f) || !finite(cfg->crash_decay)) { snprintf(msg, n, "crash_decay must be > 0"); return ITMPC_ERR_ARG; }
-  if (cfg->precision != ITMPC_FP32) { snprintf(msg, n, "precision %d not supported by this entry point", cfg->precision); return ITMPC_ERR_ARG; }
+  if (cfg->precision != ITMPC_FP32 && cfg->precision != ITMPC_BF16 && cfg->precision != ITMPC_FP8) {
+    snprintf(msg, n, "unknown precision %d", cfg->precision);
+    return ITMPC_ERR_ARG;
+  }
+  if (cfg->precision != ITMPC_FP32 && cfg->hidden != kTcHidden) {
+    snprintf(msg, n, "BF16 / FP8 iterations need hidden == %d", kTcHidden);
+    return ITMPC_ERR_ARG;
+  }
   if (cfg->activation != ITMPC_ACT_TANH && cfg->activation != ITMPC_ACT_IDENTITY) { snprintf(msg, n, "bad activation"); return ITMPC_ERR_ARG; }
   return ITMPC_OK;
 }
@@ -166,17 +175,23 @@ itmpc_status ready(itmpc_ctx *c) {
 
 constexpr int kTpsMinK = 4096;  // from here on one thread per sample beats a warp per sample
 
+// Batched contexts: the thread-per-sample FP32 kernels (H = 32) and the tensor-core kernels (H = 128).
+bool batch_capable(int H) { return H == 32 || H == kTcHidden; }
+
 }  // namespace
 
-extern "C" itmpc_status itmpc_iterate_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst);
 extern "C" itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances, int64_t max_total_samples);
 
 namespace {
 
+itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states);
+
 itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
                            float *weights, float *costs, float *states, int n_states, float *eps_out) {
-  if (!states && !eps_out && c->H == 32 && c->cfg.K >= kTpsMinK && c->inst_d) {
-    // many samples: the thread-per-sample kernels, as a batch of one instance
+  const bool tc = c->cfg.precision != ITMPC_FP32;
+  if (tc || (!states && !eps_out && c->H == 32 && c->cfg.K >= kTpsMinK && c->inst_d)) {
+    // the tensor-core kernels, or many samples: the thread-per-sample kernels, as a batch of one instance
+    if (eps_out) return fail(c, ITMPC_ERR_ARG, "noise output is not available for this precision");
     itmpc_instance q{};
     q.K = c->cfg.K;
     q.T = c->cfg.T;
@@ -189,7 +204,7 @@ itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64
     q.weights = weights;
     q.costs = costs ? costs : c->costs;
     q.stats = c->stats;
-    return itmpc_iterate_batch(c, 1, &q);
+    return run_batch(c, 1, &q, states, n_states);
   }
   IterParams p = make_params(c);
   set_iter(p, iter, c->cfg.instance);
@@ -221,6 +236,8 @@ void free_ctx(itmpc_ctx *c) {
   if (c->inst_h) cudaFreeHost(c->inst_h);
   if (c->units_h) cudaFreeHost(c->units_h);
   if (c->staged) cudaEventDestroy(c->staged);
+  for (unsigned char *b : c->tc_img)
+    if (b) cudaFree(b);
   delete c;
 }
 
@@ -273,7 +290,13 @@ itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
   e = cudaMalloc((void **)&c->status, sizeof(int));
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
-  if (c->H == 32 && c->K_cap >= kTpsMinK) {
+  if (c->H == kTcHidden) {
+    for (int i = 0; i < 2; ++i) {
+      e = cudaMalloc((void **)&c->tc_img[i], tc_image_bytes(i + 1));
+      if (e != cudaSuccess) return bail(e, "cudaMalloc");
+    }
+  }
+  if ((c->H == 32 && c->K_cap >= kTpsMinK) || c->H == kTcHidden) {
     itmpc_status bs = itmpc_reserve_batch(c, 1, c->K_cap);
     if (bs != ITMPC_OK) {
       free_ctx(c);
@@ -333,6 +356,7 @@ itmpc_status itmpc_set_dynamics(itmpc_ctx *c, int32_t n_layers, const int32_t *w
       CK(c, cudaMemcpyAsync(c->net + offb[l], b[l], sizeof(float) * nb[l], cudaMemcpyHostToDevice, c->stream), "b copy");
     }
   }
+  if (H == kTcHidden) CK(c, tc_pack(c->net, c->tc_img[0], c->tc_img[1], c->stream), "operand image pack");
   c->net_host.resize((size_t)net_floats(H));
   CK(c, cudaMemcpyAsync(c->net_host.data(), c->net, sizeof(float) * c->net_host.size(), cudaMemcpyDeviceToHost,
                         c->stream), "network read-back");
@@ -385,7 +409,7 @@ itmpc_status itmpc_set_costmap(itmpc_ctx *c, const float *map, int32_t width, in
 
 itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances, int64_t max_total_samples) {
   if (!c) return ITMPC_ERR_ARG;
-  if (c->H != 32) return fail(c, ITMPC_ERR_ARG, "batched iterations need hidden == 32");
+  if (!batch_capable(c->H)) return fail(c, ITMPC_ERR_ARG, "batched iterations need hidden == 32 or %d", kTcHidden);
   if (max_instances < 1 || max_total_samples < 1 || max_total_samples > ((int64_t)1 << 31))
     return fail(c, ITMPC_ERR_ARG, "bad batch capacity");
   CK(c, cudaStreamSynchronize(c->stream), "sync");
@@ -419,8 +443,18 @@ itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances, int64_t ma
 }
 
 itmpc_status itmpc_iterate_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst) {
+  return run_batch(c, n, inst, nullptr, 0);
+}
+
+}  // extern "C"
+
+namespace {
+
+itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states) {
   itmpc_status st = ready(c);
   if (st != ITMPC_OK) return st;
+  const bool tc = c->cfg.precision != ITMPC_FP32;
+  if (!tc && c->H != 32) return fail(c, ITMPC_ERR_ARG, "batched FP32 iterations need hidden == 32");
   if (!c->inst_d) return fail(c, ITMPC_ERR_STATE, "itmpc_reserve_batch has not been called");
   if (n < 1 || n > c->batch_max_inst || !inst) return fail(c, ITMPC_ERR_ARG, "n=%d outside [1, %d]", n, c->batch_max_inst);
   int64_t total = 0;
@@ -506,9 +540,20 @@ itmpc_status itmpc_iterate_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *
   sh.partials = c->batch_partials;
   sh.unit_counter = c->unit_counter;
   sh.status = c->status;
-  CK(c, tps_launch(sh, c->net_host.data(), c->H, g.activation, c->stream), "batched launch");
+  sh.states_out = states;
+  sh.n_states = states ? n_states : 0;
+  if (tc) {
+    CK(c, tc_launch(sh, c->tc_img[g.precision == ITMPC_FP8 ? 1 : 0], g.precision, g.activation, c->stream),
+       "tensor-core launch");
+  } else {
+    CK(c, tps_launch(sh, c->net_host.data(), c->H, g.activation, c->stream), "batched launch");
+  }
   return ITMPC_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 itmpc_status itmpc_iterate(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
                            float *weights, float *costs) {

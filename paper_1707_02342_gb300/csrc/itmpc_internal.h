@@ -119,6 +119,9 @@ struct TpsShared {
   float *partials;
   unsigned int *unit_counter;
   int *status;
+  // debug: states x_0..x_T of samples 0..n_states-1 of instance 0 (n_states x (T+1) x 7), or null
+  float *states_out;
+  int n_states, pad2;
 };
 
 // Network values in kernel parameter space (constant bank): FMA operands read
@@ -130,6 +133,19 @@ struct TpsNet {
 
 // Launch the rollout (persistent over work units) and the per-instance merge.
 cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, cudaStream_t s);
+// The per-instance merge alone (after any kernel that wrote the units' records);
+// also resets the unit counter.
+cudaError_t tps_merge(const TpsShared &sh, cudaStream_t s);
+
+// ---- tensor-core (BF16 / FP8) rollout of H = 128 networks over the same work units ----
+constexpr int kTcHidden = 128;
+// Bytes of the packed operand image of one precision (1 = BF16, 2 = FP8 layer 2).
+size_t tc_image_bytes(int precision);
+// Build both operand images from the packed FP32 network (device).
+cudaError_t tc_pack(const float *net, unsigned char *img_bf16, unsigned char *img_fp8, cudaStream_t s);
+// Rollout + records (tensor cores), then tps_merge.
+cudaError_t tc_launch(const TpsShared &sh, const unsigned char *image, int precision, int activation,
+                      cudaStream_t s);
 size_t tps_merge_smem_bytes(int max_units_per_instance, int T_max);
 cudaError_t launch_noise(const IterParams &p, float *eps, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);

@@ -1,0 +1,51 @@
+// itmpc_units.cuh -- per-sample device steps shared by the kernels that work
+// on 128-sample units of possibly many instances (TpsShared parameters).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "itmpc_device.cuh"
+#include "itmpc_internal.h"
+
+namespace itmpc {
+
+__device__ __forceinline__ float2 tps_noise(const TpsShared &sh, uint32_t k, uint32_t t, uint32_t c2, uint32_t c3) {
+  const uint4 w = philox4x32_10(make_uint4(k, t, c2, c3), sh.key0, sh.key1);
+  const float2 z = box_muller(w.x, w.y);
+  return make_float2(sh.sigma0 * z.x, sh.sigma1 * z.y);
+}
+
+// h(p_x, p_y): bilinear, texel (i, j) centred at origin + (j + 1/2, i + 1/2) res, clamp-to-edge.
+__device__ __forceinline__ float tps_costmap(const TpsShared &sh, const float *map, float px, float py) {
+  const float fx = (px - sh.origin_x) * sh.inv_res - 0.5f;
+  const float fy = (py - sh.origin_y) * sh.inv_res - 0.5f;
+  const float jf = floorf(fx), if_ = floorf(fy);
+  const float a = fx - jf, b = fy - if_;
+  const float jc = fminf(fmaxf(jf, -1.0f), (float)sh.map_w);
+  const float ic = fminf(fmaxf(if_, -1.0f), (float)sh.map_h);
+  const int jj = (int)jc, ii = (int)ic;
+  const int j0 = min(max(jj, 0), sh.map_w - 1), j1 = min(max(jj + 1, 0), sh.map_w - 1);
+  const int i0 = min(max(ii, 0), sh.map_h - 1), i1 = min(max(ii + 1, 0), sh.map_h - 1);
+  const float *r0 = map + (size_t)i0 * sh.map_w;
+  const float *r1 = map + (size_t)i1 * sh.map_w;
+  const float m00 = __ldg(r0 + j0), m01 = __ldg(r0 + j1);
+  const float m10 = __ldg(r1 + j0), m11 = __ldg(r1 + j1);
+  return (1.0f - a) * (1.0f - b) * m00 + a * (1.0f - b) * m01 + (1.0f - a) * b * m10 + a * b * m11;
+}
+
+// State cost at loop index t (Sec. V-C).
+__device__ __forceinline__ float tps_state_cost(const TpsShared &sh, const float *map, float px, float py, float vx,
+                                                float vy, int t) {
+  float h = tps_costmap(sh, map, px, py);
+  h = h > sh.map_cap ? sh.map_cap : h;  // NaN stays NaN
+  const float zeta = -atan2f(vy, fabsf(vx));
+  const float sp = vx - sh.v_des;
+  float imp = 0.0f;
+  if (h > sh.track_thresh) imp += exp2f((float)t * sh.log2_decay) * sh.crash_cost;
+  if (fabsf(zeta) > sh.slip_thresh) imp += sh.crash_cost;
+  return sh.w_track * h + sh.w_speed * sp * sp + sh.w_stab * zeta * zeta + sh.w_crash * imp;
+}
+
+}  // namespace itmpc
