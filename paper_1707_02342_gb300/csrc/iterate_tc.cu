@@ -6,19 +6,30 @@
 // sample-step, so here every layer runs as a tcgen05 MMA over a tile of 128
 // samples (M = 128 rows = one work unit), accumulating in FP32 in tensor
 // memory:
-//   layer 1  D = [z_hi z_lo 1 1 0 0] x [W1 W1 b1_hi b1_lo 0 0]^T   (K = 16, N = 128)
+//   layer 1  D1 = [z_hi z_lo 1 1 0 0] x [W1 W1 b1_hi b1_lo 0 0]^T   (K = 16, N = 128)
 //            z = (x_d, g(v)) split into two BF16 parts, so the state enters
 //            with ~16 significant bits although the weights are BF16;
-//   layer 2  D = tanh(h1) x W2^T + bias                            (K = 128, N = 128)
+//   layer 2  D2 = tanh(D1) x W2^T + bias                            (K = 128, N = 128)
 //            BF16 operands, or E4M3 operands with per-layer scales (FP8 form);
-//   layer 3  D = tanh(h2) x W3^T + bias                            (K = 128, N = 16, 4 used)
+//   layer 3  D3 = tanh(D2) x W3^T + bias                            (K = 128, N = 16, 4 used)
 // Biases enter through the two constant-one columns of the layer-1 operand.
-// Between the MMAs the CTA's 16 warps read the accumulators from tensor
-// memory (warp w: TMEM lanes 32 (w % 4) .. +31 = samples, columns 32 (w / 4)
-// .. +31 = hidden units), apply the hardware tanh and write the next
-// operand to shared memory.  Warps 0-3 own the per-sample state (Euler step,
-// kinematics), warps 4-7 draw the next step's noise, warps 8-11 add the
-// running cost of Sec. V-C; those side tasks overlap the MMAs.
+// Every A operand lives in tensor memory (written with tcgen05.st), the
+// weights (B operands) in shared memory.
+//
+// Warp roles (one CTA per SM, persistent over 128-sample units):
+//   * 16 epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (its
+//     samples), columns 32 (w / 4) .. +31 of a layer's accumulator, applies
+//     the hardware tanh and stores the result as the next layer's A operand.
+//     Warps 0-3 also own the sample state (Euler step of Sec. V-B, next
+//     layer-1 operand first, kinematics after); warps 8-11 add the running
+//     cost of Sec. V-C, fetching the costmap texels one layer ahead.
+//   * one MMA warp issues each layer once its operand is complete and waits
+//     for the MMA itself: it is the only thread polling an mbarrier; the
+//     epilogue warps block on named barriers (no spinning, which would steal
+//     issue slots from the activations).
+// Layers do not overlap: an MMA accumulating in tensor memory while the
+// epilogue warps read and write it slows the epilogue by more than the MMA
+// takes alone.  Noise is drawn in blocks of steps into shared memory.
 // Each unit leaves one partial record (Alg. 2 shifted by the unit's minimum),
 // merged per instance by tps_merge -- the same records as the FP32
 // thread-per-sample kernels, so single and batched iterations share it.
@@ -41,10 +52,30 @@ namespace {
 
 constexpr int kH = kTcHidden;        // 128 hidden units
 constexpr int kRows = kTpsThreads;   // samples per unit = MMA rows
-constexpr int kTcThreads = 512;
-constexpr uint32_t kTmemCols = 128;  // one FP32 accumulator tile, reused by the three layers
+constexpr int kEpiThreads = 512;     // 16 epilogue warps
+constexpr int kTcThreads = kEpiThreads + 32;  // + the MMA warp
+constexpr int kMmaWarp = kEpiThreads / 32;
 constexpr float kActScale = 256.0f;  // E4M3 scale of tanh outputs (|h| < 1, exact power of two)
 static_assert(kRows == 128, "a unit is one M = 128 tile");
+
+// Tensor memory columns: accumulators D1 (layer 1, and D3 of layer 3 in its
+// first 16 columns) and D2; A operands: layer-1 input (8 columns = 16 BF16),
+// h1 (64 columns BF16 / 32 E4M3), h2 (64 columns BF16).
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColD2 = 128;
+constexpr uint32_t kColA1 = 256;
+constexpr uint32_t kColH1 = 320;
+constexpr uint32_t kColH2 = 384;
+
+// Named barriers (id 0 is __syncthreads).  Producers bar.arrive, consumers bar.sync.
+constexpr int kBarInput = 1;  // state warps -> MMA warp: layer-1 operand stored      (128 + 32)
+constexpr int kBarH1 = 2;     // epilogue -> MMA warp: h1 stored                       (512 + 32)
+constexpr int kBarH2 = 3;     // epilogue -> MMA warp: h2 stored                       (512 + 32)
+constexpr int kBarD1 = 4;     // MMA warp -> epilogue: layer 1 complete                (32 + 512)
+constexpr int kBarD2 = 5;     // MMA warp -> epilogue: layer 2 complete                (32 + 512)
+constexpr int kBarD3 = 6;     // MMA warp -> state warps: layer 3 complete             (32 + 128)
+constexpr int kBarState = 7;  // state warps -> cost warps: x(t) in shared memory      (128 + 128)
+constexpr int kBarNoise = 8;  // epilogue warps: a block of noise written              (512)
 
 // Operand image (bytes): every block K-major, no swizzle (itmpc_tcgen05.cuh).
 constexpr int kOffB1 = 0;       // 128 x 16 BF16: [W1 | W1 | b1_hi b1_lo 0 0]
@@ -58,12 +89,13 @@ constexpr int kImgFp8 = kOffB2 + 16384 + 16;
 template <bool FP8>
 constexpr int img_bytes() { return FP8 ? kImgFp8 : kImgBf16; }
 template <bool FP8>
-constexpr int a1_off() { return (img_bytes<FP8>() + 127) & ~127; }
+constexpr int u_off() { return (img_bytes<FP8>() + 127) & ~127; }
 
+// Shared memory before the noise block; the noise block holds Tc steps x kRows float2.
 template <bool FP8>
-size_t smem_bytes(int T_max) {
+size_t smem_fixed(int T_max) {
   const size_t U_len = (size_t)((2 * T_max + 3) & ~3);
-  return (size_t)a1_off<FP8>() + 4096 + 32768 + 4 * U_len + 8 * 2 * kRows + 16 * kRows + 3 * 4 * kRows;
+  return (size_t)u_off<FP8>() + 4 * U_len + 16 * kRows + 3 * 4 * kRows;
 }
 
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
@@ -77,8 +109,10 @@ __device__ __forceinline__ uint32_t e4m3x4_bits(float a, float b, float c, float
   return (p0 & 0xFFFFu) | (p1 << 16);
 }
 
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void bar_state_warps() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void nbar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void nbar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 
 template <int ACT>
 __device__ __forceinline__ float act_tc(float x) {
@@ -98,94 +132,139 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
   return false;
 }
 
-// Hidden columns [32 cg, 32 cg + 32) of sample row s -> activation -> BF16
-// operand row (128 x 128 BF16 tile, Kb = 256).  scale multiplies the
-// accumulator first (the FP8 form's de-scale).
-template <int ACT, bool SCALE>
-__device__ __forceinline__ void put_bf16(unsigned char *A, int s, int cg, const uint32_t (&r)[32], float scale) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint32_t w[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int c = 8 * j + 2 * i;
-      float a = __uint_as_float(r[c]), b = __uint_as_float(r[c + 1]);
-      if (SCALE) {
-        a *= scale;
-        b *= scale;
-      }
-      w[i] = bf16x2_bits(act_tc<ACT>(a), act_tc<ACT>(b));
-    }
-    *reinterpret_cast<uint4 *>(A + cm_offset(s, 64 * cg + 16 * j, 256)) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&w)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]),
+      "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15])
+      : "memory");
 }
 
-// Same columns -> activation -> times kActScale -> E4M3 operand row (Kb = 128).
-template <int ACT>
-__device__ __forceinline__ void put_e4m3(unsigned char *A, int s, int cg, const uint32_t (&r)[32]) {
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    uint32_t w[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int c = 16 * j + 4 * i;
-      w[i] = e4m3x4_bits(act_tc<ACT>(__uint_as_float(r[c])) * kActScale,
-                         act_tc<ACT>(__uint_as_float(r[c + 1])) * kActScale,
-                         act_tc<ACT>(__uint_as_float(r[c + 2])) * kActScale,
-                         act_tc<ACT>(__uint_as_float(r[c + 3])) * kActScale);
-    }
-    *reinterpret_cast<uint4 *>(A + cm_offset(s, 32 * cg + 16 * j, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
-// Network input row of sample s: (x_d, g) as BF16 hi and lo parts plus the two
-// constant-one columns that carry the biases.
-__device__ __forceinline__ void put_input(unsigned char *A1, int s, const float (&z)[6]) {
+// Network input row of this thread's sample (TMEM lane): (x_d, g) as BF16 hi and
+// lo parts plus the two constant-one columns that carry the biases.
+__device__ __forceinline__ void put_input(uint32_t t_lane, const float (&z)[6]) {
   float hi[6], lo[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(z[i]);
-    hi[i] = __bfloat162float(h);
+    hi[i] = __bfloat162float(__float2bfloat16_rn(z[i]));
     lo[i] = z[i] - hi[i];  // exact in FP32; rounded to BF16 when packed
   }
   const uint4 c0 = make_uint4(bf16x2_bits(hi[0], hi[1]), bf16x2_bits(hi[2], hi[3]), bf16x2_bits(hi[4], hi[5]),
                               bf16x2_bits(lo[0], lo[1]));
   const uint4 c1 = make_uint4(bf16x2_bits(lo[2], lo[3]), bf16x2_bits(lo[4], lo[5]), bf16x2_bits(1.0f, 1.0f), 0u);
-  *reinterpret_cast<uint4 *>(A1 + cm_offset(s, 0, 32)) = c0;
-  *reinterpret_cast<uint4 *>(A1 + cm_offset(s, 16, 32)) = c1;
+  tc_st8(t_lane + kColA1, c0, c1);
 }
 
-__device__ __forceinline__ void issue_layer1(uint32_t tmem, uint32_t a1, uint32_t img) {
-  tc_mma_bf16(tmem, tc_desc(a1, 128, 256), tc_desc(img + kOffB1, 128, 256), tc_idesc(true, 128, 128), 0);
-}
-
-template <bool FP8>
-__device__ __forceinline__ void issue_layer2(uint32_t tmem, uint32_t a1, uint32_t ah, uint32_t img) {
-  tc_mma_bf16(tmem, tc_desc(a1, 128, 256), tc_desc(img + kOffB2b, 128, 256), tc_idesc(true, 128, 128), 0);
-  if constexpr (FP8) {
+// One layer's epilogue for this thread: accumulator columns col0 + 32 sub .. +31
+// of its lane -> activation -> A operand (K elements 32 sub .. +31) from column
+// a_col: BF16, 2 per column, or (OUT_E4M3) E4M3(kActScale h), 4 per column.
+// SCALE multiplies the accumulator first (the FP8 form's de-scale).
+template <int ACT, bool OUT_E4M3, bool SCALE>
+__device__ __forceinline__ void epilogue(uint32_t t_lane, uint32_t col0, uint32_t a_col, int sub, float scale) {
+  uint32_t r[32];
+  tc_ld32(t_lane + col0 + 32 * sub, r);
+  tc_wait_ld();
+  float v[32];
 #pragma unroll
-    for (int ks = 0; ks < 4; ++ks)
-      tc_mma_e4m3(tmem, tc_desc(ah + 256 * ks, 128, 1024), tc_desc(img + kOffB2 + 256 * ks, 128, 1024),
-                  tc_idesc(false, 128, 128), 1);
+  for (int i = 0; i < 32; ++i) {
+    float a = __uint_as_float(r[i]);
+    if (SCALE) a *= scale;
+    v[i] = act_tc<ACT>(a);
+  }
+  if constexpr (OUT_E4M3) {
+    const uint4 lo = make_uint4(
+        e4m3x4_bits(v[0] * kActScale, v[1] * kActScale, v[2] * kActScale, v[3] * kActScale),
+        e4m3x4_bits(v[4] * kActScale, v[5] * kActScale, v[6] * kActScale, v[7] * kActScale),
+        e4m3x4_bits(v[8] * kActScale, v[9] * kActScale, v[10] * kActScale, v[11] * kActScale),
+        e4m3x4_bits(v[12] * kActScale, v[13] * kActScale, v[14] * kActScale, v[15] * kActScale));
+    const uint4 hi = make_uint4(
+        e4m3x4_bits(v[16] * kActScale, v[17] * kActScale, v[18] * kActScale, v[19] * kActScale),
+        e4m3x4_bits(v[20] * kActScale, v[21] * kActScale, v[22] * kActScale, v[23] * kActScale),
+        e4m3x4_bits(v[24] * kActScale, v[25] * kActScale, v[26] * kActScale, v[27] * kActScale),
+        e4m3x4_bits(v[28] * kActScale, v[29] * kActScale, v[30] * kActScale, v[31] * kActScale));
+    tc_st8(t_lane + a_col + 8 * sub, lo, hi);
   } else {
+    uint32_t w[16];
 #pragma unroll
-    for (int ks = 0; ks < 8; ++ks)
-      tc_mma_bf16(tmem, tc_desc(ah + 256 * ks, 128, 2048), tc_desc(img + kOffB2 + 256 * ks, 128, 2048),
-                  tc_idesc(true, 128, 128), 1);
+    for (int i = 0; i < 16; ++i) w[i] = bf16x2_bits(v[2 * i], v[2 * i + 1]);
+    tc_st16(t_lane + a_col + 16 * sub, w);
+  }
+  tc_wait_st();
+  tc_fence_before();  // the reads and stores precede the MMA the arrival releases
+}
+
+// Layer-2 MMAs: the bias (through the ones of the layer-1 operand) opens the accumulation.
+template <bool FP8>
+__device__ __forceinline__ void issue_layer2(uint32_t tmem, uint32_t img) {
+  const uint32_t d = tmem + kColD2;
+  tc_mma_bf16_ta(d, tmem + kColA1, tc_desc(img + kOffB2b, 128, 256), tc_idesc(true, 128, 128), 0);
+  if constexpr (FP8) {  // 32 E4M3 = 8 columns per MMA
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      tc_mma_e4m3_ta(d, tmem + kColH1 + 8 * k, tc_desc(img + kOffB2 + 256 * k, 128, 1024), tc_idesc(false, 128, 128),
+                     1);
+  } else {  // 16 BF16 = 8 columns per MMA
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      tc_mma_bf16_ta(d, tmem + kColH1 + 8 * k, tc_desc(img + kOffB2 + 256 * k, 128, 2048), tc_idesc(true, 128, 128),
+                     1);
   }
 }
 
-__device__ __forceinline__ void issue_layer3(uint32_t tmem, uint32_t a1, uint32_t ah, uint32_t img) {
-  tc_mma_bf16(tmem, tc_desc(a1, 128, 256), tc_desc(img + kOffB3b, 128, 256), tc_idesc(true, 128, 16), 0);
+__device__ __forceinline__ void issue_layer3(uint32_t tmem, uint32_t img) {
+  tc_mma_bf16_ta(tmem, tmem + kColA1, tc_desc(img + kOffB3b, 128, 256), tc_idesc(true, 128, 16), 0);
 #pragma unroll
-  for (int ks = 0; ks < 8; ++ks)
-    tc_mma_bf16(tmem, tc_desc(ah + 256 * ks, 128, 2048), tc_desc(img + kOffB3 + 256 * ks, 128, 2048),
-                tc_idesc(true, 128, 16), 1);
+  for (int k = 0; k < 8; ++k)
+    tc_mma_bf16_ta(tmem, tmem + kColH2 + 8 * k, tc_desc(img + kOffB3 + 256 * k, 128, 2048), tc_idesc(true, 128, 16),
+                   1);
+}
+
+// The costmap texels of h(p_x, p_y) (bilinear, clamp-to-edge, as tps_costmap),
+// fetched one layer before they are combined.
+struct CostFetch {
+  float m00, m01, m10, m11, a, b, vx, vy;
+};
+
+__device__ __forceinline__ CostFetch cost_fetch(const TpsShared &sh, const float *map, float4 x) {
+  CostFetch f;
+  const float fx = (x.x - sh.origin_x) * sh.inv_res - 0.5f;
+  const float fy = (x.y - sh.origin_y) * sh.inv_res - 0.5f;
+  const float jf = floorf(fx), if_ = floorf(fy);
+  f.a = fx - jf;
+  f.b = fy - if_;
+  const float jc = fminf(fmaxf(jf, -1.0f), (float)sh.map_w);
+  const float ic = fminf(fmaxf(if_, -1.0f), (float)sh.map_h);
+  const int jj = (int)jc, ii = (int)ic;
+  const int j0 = min(max(jj, 0), sh.map_w - 1), j1 = min(max(jj + 1, 0), sh.map_w - 1);
+  const int i0 = min(max(ii, 0), sh.map_h - 1), i1 = min(max(ii + 1, 0), sh.map_h - 1);
+  const float *r0 = map + (size_t)i0 * sh.map_w;
+  const float *r1 = map + (size_t)i1 * sh.map_w;
+  f.m00 = __ldg(r0 + j0);
+  f.m01 = __ldg(r0 + j1);
+  f.m10 = __ldg(r1 + j0);
+  f.m11 = __ldg(r1 + j1);
+  f.vx = x.z;
+  f.vy = x.w;
+  return f;
+}
+
+// State cost at loop index t (Sec. V-C) from fetched texels (as tps_state_cost).
+__device__ __forceinline__ float cost_finish(const TpsShared &sh, const CostFetch &f, int t) {
+  float h = (1.0f - f.a) * (1.0f - f.b) * f.m00 + f.a * (1.0f - f.b) * f.m01 + (1.0f - f.a) * f.b * f.m10 +
+            f.a * f.b * f.m11;
+  h = h > sh.map_cap ? sh.map_cap : h;  // NaN stays NaN
+  const float zeta = -atan2f(f.vy, fabsf(f.vx));
+  const float sp = f.vx - sh.v_des;
+  float imp = 0.0f;
+  if (h > sh.track_thresh) imp += exp2f((float)t * sh.log2_decay) * sh.crash_cost;
+  if (fabsf(zeta) > sh.slip_thresh) imp += sh.crash_cost;
+  return sh.w_track * h + sh.w_speed * sp * sp + sh.w_stab * zeta * zeta + sh.w_crash * imp;
 }
 
 template <bool FP8, int ACT>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    tc_rollout_kernel(const __grid_constant__ TpsShared sh, const unsigned char *__restrict__ image) {
+    tc_rollout_kernel(const __grid_constant__ TpsShared sh, const unsigned char *__restrict__ image, int Tc) {
   constexpr int IMG = img_bytes<FP8>();
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[4];  // operand image, layer 1, layer 2, layer 3
@@ -196,19 +275,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   volatile int *abort_v = &abort_s;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int quarter = warp & 3, cg = warp >> 2;
-  const int s = 32 * quarter + lane;  // sample row (TMEM lane) this thread serves
+  const int quarter = warp & 3, sub = (warp >> 2) & 3;
+  const int s = 32 * quarter + lane;  // sample row (TMEM lane) of an epilogue thread
 
   unsigned char *img = smem;
-  unsigned char *A1 = smem + a1_off<FP8>();
-  unsigned char *Ah = A1 + 4096;
-  float *U_s = reinterpret_cast<float *>(Ah + 32768);
+  float *U_s = reinterpret_cast<float *>(smem + u_off<FP8>());
   const int U_len = (2 * sh.T_max + 3) & ~3;
-  float2 *eps_s = reinterpret_cast<float2 *>(U_s + U_len);  // [2][kRows]: noise of steps t, t + 1
-  float4 *st_s = reinterpret_cast<float4 *>(eps_s + 2 * kRows);  // (p_x, p_y, v_x, v_y) for the cost warps
-  float *cc_s = reinterpret_cast<float *>(st_s + kRows);          // control-cost term of the previous step
+  float4 *st_s = reinterpret_cast<float4 *>(U_s + U_len);  // (p_x, p_y, v_x, v_y) of x(t) for the cost warps
+  float *cc_s = reinterpret_cast<float *>(st_s + kRows);   // control-cost term of step t - 1
   float *S_s = cc_s + kRows;
   float *e_s = S_s + kRows;
+  float2 *eps_s = reinterpret_cast<float2 *>(e_s + kRows);  // [Tc][kRows]
 
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
@@ -220,11 +297,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t t_lane = tmem + ((uint32_t)(32 * quarter) << 16);
-  const uint32_t a1_u = smem_u32(A1), ah_u = smem_u32(Ah), img_u = smem_u32(img);
+  const uint32_t img_u = smem_u32(img);
 
-  // thread 0 issues every asynchronous operation and tracks which have not been seen complete
-  int pend_img = 0, pend1 = 0, pend2 = 0, pend3 = 0;
-  uint32_t ph1 = 0, ph2 = 0, ph3 = 0;
+  int pend_img = 0;
   if (tid == 0) {
     mbar_expect_tx(&bars[0], (uint32_t)IMG);
     bulk_copy_g2s(img, image, (uint32_t)IMG, &bars[0]);
@@ -232,6 +307,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   if (tc_wait(&bars[0], 0, abort_v) && tid == 0) pend_img = 0;
   const float inv_scale = FP8 ? reinterpret_cast<const float *>(img + IMG - 16)[0] : 1.0f;
+  uint32_t ph = 0;  // MMA warp: phase of the layer barriers (one commit each per step)
+  // MMA warp: 1 + parity of a commit not seen complete, else 0
+  uint32_t pend1 = 0, pend2 = 0, pend3 = 0;
 
   if (!__syncthreads_or(*abort_v)) {
     for (;;) {
@@ -244,149 +322,140 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const TpsInstance &I = sh.inst[un.inst];
       const int K = I.K, T = I.T;
       for (int i = tid; i < 2 * T; i += kTcThreads) U_s[i] = __ldg(I.U + i);
-      const int k = un.k0 + s;
-      const bool imp = k < I.n_imp;
-      const float *map = sh.maps + (size_t)I.map * (size_t)sh.map_stride;
-      const bool dbg = cg == 0 && sh.states_out && un.inst == 0 && k < sh.n_states;
-      float px = 0.f, py = 0.f, th = 0.f, xd0 = 0.f, xd1 = 0.f, xd2 = 0.f, xd3 = 0.f, cc = 0.f, S = 0.f;
-      auto save_state = [&](int t) {
-        float *o = sh.states_out + ((size_t)k * (T + 1) + t) * 7;
-        o[0] = px; o[1] = py; o[2] = th; o[3] = xd0; o[4] = xd1; o[5] = xd2; o[6] = xd3;
-      };
-      // d = f(x_d, g(v)) of the last layer-3 MMA (TMEM columns 0-3) -> explicit Euler step (Sec. V-B)
-      auto euler = [&]() {
-        uint32_t r[4];
-        __syncwarp();
-        tc_ld4(t_lane, r);
-        tc_wait_ld();
-        float sn, cs;
-        sincosf(th, &sn, &cs);
-        px = fmaf(cs * xd1 - sn * xd2, sh.dt, px);
-        py = fmaf(sn * xd1 + cs * xd2, sh.dt, py);
-        th = fmaf(xd3, sh.dt, th);
-        xd0 = fmaf(__uint_as_float(r[0]), sh.dt, xd0);
-        xd1 = fmaf(__uint_as_float(r[1]), sh.dt, xd1);
-        xd2 = fmaf(__uint_as_float(r[2]), sh.dt, xd2);
-        xd3 = fmaf(__uint_as_float(r[3]), sh.dt, xd3);
-      };
-      if (cg == 0) {
-        px = __ldg(I.x0 + 0); py = __ldg(I.x0 + 1); th = __ldg(I.x0 + 2);
-        xd0 = __ldg(I.x0 + 3); xd1 = __ldg(I.x0 + 4); xd2 = __ldg(I.x0 + 5); xd3 = __ldg(I.x0 + 6);
-        if (dbg) save_state(0);
-      } else if (cg == 1) {
-        eps_s[s] = tps_noise(sh, (uint32_t)k, 0u, I.ctr2, I.ctr3);
-      }
       __syncthreads();
 
-      for (int t = 0; t < T; ++t) {
-        const int b = t & 1;
-        if (cg == 0) {
-          if (t > 0) {
-            if (tc_wait(&bars[3], ph3, abort_v)) {
-              ph3 ^= 1u;
-              if (tid == 0) pend3 = 0;
-            }
-            tc_fence_after();
-            euler();  // x(t)
-            st_s[s] = make_float4(px, py, xd1, xd2);
-            cc_s[s] = cc;
-            if (dbg) save_state(t);
-          }
-          const float2 e = eps_s[b * kRows + s];
-          const float u0 = U_s[2 * t], u1 = U_s[2 * t + 1];
-          const float v0 = imp ? u0 + e.x : e.x, v1 = imp ? u1 + e.y : e.y;
-          const float g0 = fminf(fmaxf(v0, sh.umin0), sh.umax0), g1 = fminf(fmaxf(v1, sh.umin1), sh.umax1);
-          cc = sh.gamma != 0.0f ? sh.gamma * (u0 * v0 * sh.inv_sig2_0 + u1 * v1 * sh.inv_sig2_1) : 0.0f;
-          const float z[6] = {xd0, xd1, xd2, xd3, g0, g1};
-          put_input(A1, s, z);
-          fence_async_smem();
-          tc_fence_before();
-          bar_state_warps();
-          if (tid == 0) {
+      if (warp == kMmaWarp) {
+        // ---------------- MMA warp: issue a layer, wait for it, release its readers ----------------
+        auto run = [&](int bar_in, int n_in, int which, int bar_out, int n_out, uint32_t &pend) {
+          nbar_sync(bar_in, n_in);
+          if (lane == 0) {
             tc_fence_after();
             if (!*abort_v) {
-              issue_layer1(tmem, a1_u, img_u);
-              tc_commit(&bars[1]);
-              pend1 = 1;
+              if (which == 1)
+                tc_mma_bf16_ta(tmem, tmem + kColA1, tc_desc(img_u + kOffB1, 128, 256), tc_idesc(true, 128, 128), 0);
+              else if (which == 2)
+                issue_layer2<FP8>(tmem, img_u);
+              else
+                issue_layer3(tmem, img_u);
+              tc_commit(&bars[which]);
+              pend = 1u + ph;
+              if (tc_wait(&bars[which], ph, abort_v)) pend = 0;
             }
+            tc_fence_before();
           }
-        } else if (cg == 1) {
-          if (t + 1 < T) eps_s[(b ^ 1) * kRows + s] = tps_noise(sh, (uint32_t)k, (uint32_t)(t + 1), I.ctr2, I.ctr3);
-        }
-        // layer-1 epilogue: h1 = tanh(W1 z + b1) -> layer-2 operand
-        {
-          if (tc_wait(&bars[1], ph1, abort_v)) {
-            ph1 ^= 1u;
-            if (tid == 0) pend1 = 0;
-          }
-          tc_fence_after();
-          uint32_t r[32];
           __syncwarp();
-          tc_ld32(t_lane + 32 * cg, r);
+          nbar_arrive(bar_out, n_out);
+        };
+        for (int t = 0; t < T; ++t) {
+          run(kBarInput, 128 + 32, 1, kBarD1, kTcThreads, pend1);
+          run(kBarH1, kTcThreads, 2, kBarD2, kTcThreads, pend2);
+          run(kBarH2, kTcThreads, 3, kBarD3, 128 + 32, pend3);
+          ph ^= 1u;
+        }
+      } else {
+        // ---------------- epilogue warps ----------------
+        const int k = un.k0 + s;
+        const bool imp = k < I.n_imp;
+        const float *map = sh.maps + (size_t)I.map * (size_t)sh.map_stride;
+        const bool state = sub == 0, coster = sub == 2;
+        const bool dbg = state && sh.states_out && un.inst == 0 && k < sh.n_states;
+        float px = 0.f, py = 0.f, th = 0.f, xd0 = 0.f, xd1 = 0.f, xd2 = 0.f, xd3 = 0.f, cc = 0.f, S = 0.f;
+        auto save_state = [&](int t) {
+          float *o = sh.states_out + ((size_t)k * (T + 1) + t) * 7;
+          o[0] = px; o[1] = py; o[2] = th; o[3] = xd0; o[4] = xd1; o[5] = xd2; o[6] = xd3;
+        };
+        // x(t) from x(t - 1) and f = D3 columns 0-3 (explicit Euler, Sec. V-B): the
+        // velocities first (they feed the network), the kinematics with the old
+        // velocities after the next operand is out
+        float ox1 = 0.f, ox2 = 0.f, ox3 = 0.f;
+        auto step_velocities = [&]() -> void {
+          nbar_sync(kBarD3, 128 + 32);
+          tc_fence_after();
+          uint32_t r[4];
+          tc_ld4(t_lane, r);
           tc_wait_ld();
-          if constexpr (FP8) put_e4m3<ACT>(Ah, s, cg, r);
-          else put_bf16<ACT, false>(Ah, s, cg, r, 1.0f);
-          fence_async_smem();
-          tc_fence_before();
+          ox1 = xd1; ox2 = xd2; ox3 = xd3;
+          xd0 = fmaf(__uint_as_float(r[0]), sh.dt, xd0);
+          xd1 = fmaf(__uint_as_float(r[1]), sh.dt, xd1);
+          xd2 = fmaf(__uint_as_float(r[2]), sh.dt, xd2);
+          xd3 = fmaf(__uint_as_float(r[3]), sh.dt, xd3);
+        };
+        auto kinematics = [&]() -> void {
+          float sn, cs;
+          sincosf(th, &sn, &cs);
+          px = fmaf(cs * ox1 - sn * ox2, sh.dt, px);
+          py = fmaf(sn * ox1 + cs * ox2, sh.dt, py);
+          th = fmaf(ox3, sh.dt, th);
+        };
+        if (state) {
+          px = __ldg(I.x0 + 0); py = __ldg(I.x0 + 1); th = __ldg(I.x0 + 2);
+          xd0 = __ldg(I.x0 + 3); xd1 = __ldg(I.x0 + 4); xd2 = __ldg(I.x0 + 5); xd3 = __ldg(I.x0 + 6);
+          if (dbg) save_state(0);
         }
-        if (__syncthreads_or(*abort_v)) break;
-        if (tid == 0) {
-          tc_fence_after();
-          if (!*abort_v) {
-            issue_layer2<FP8>(tmem, a1_u, ah_u, img_u);
-            tc_commit(&bars[2]);
-            pend2 = 1;
+        CostFetch cf{};
+        float cc_prev = 0.f;
+        for (int t = 0; t < T; ++t) {
+          if (t % Tc == 0) {  // noise eps_{k, t .. t + Tc - 1} of the unit's samples
+            const int nst = min(Tc, T - t);
+            for (int it = tid; it < nst * kRows; it += kEpiThreads) {
+              const int tt = it / kRows, s2 = it % kRows;
+              eps_s[it] = tps_noise(sh, (uint32_t)(un.k0 + s2), (uint32_t)(t + tt), I.ctr2, I.ctr3);
+            }
+            nbar_sync(kBarNoise, kEpiThreads);
           }
-        }
-        // running cost of x(t) (Alg. 1: after every step) while layer 2 runs
-        if (cg == 2 && t > 0) {
-          const float4 x = st_s[s];
-          S += tps_state_cost(sh, map, x.x, x.y, x.z, x.w, t) + cc_s[s];
-        }
-        // layer-2 epilogue: h2 = tanh(W2 h1 + b2) -> layer-3 operand
-        {
-          if (tc_wait(&bars[2], ph2, abort_v)) {
-            ph2 ^= 1u;
-            if (tid == 0) pend2 = 0;
+          if (state) {
+            if (t > 0) step_velocities();  // x_d(t)
+            const float2 e = eps_s[(t % Tc) * kRows + s];
+            const float u0 = U_s[2 * t], u1 = U_s[2 * t + 1];
+            const float v0 = imp ? u0 + e.x : e.x, v1 = imp ? u1 + e.y : e.y;
+            const float g0 = fminf(fmaxf(v0, sh.umin0), sh.umax0), g1 = fminf(fmaxf(v1, sh.umin1), sh.umax1);
+            const float z[6] = {xd0, xd1, xd2, xd3, g0, g1};
+            put_input(t_lane, z);
+            tc_wait_st();
+            tc_fence_before();  // the D3 read and the operand store precede the layer-1 MMA
+            nbar_arrive(kBarInput, 128 + 32);
+            if (t > 0) {
+              kinematics();  // (p_x, p_y, theta)(t)
+              if (dbg) save_state(t);
+            }
+            st_s[s] = make_float4(px, py, xd1, xd2);
+            cc_s[s] = cc;
+            nbar_arrive(kBarState, 256);
+            cc = sh.gamma != 0.0f ? sh.gamma * (u0 * v0 * sh.inv_sig2_0 + u1 * v1 * sh.inv_sig2_1) : 0.0f;
           }
-          tc_fence_after();
-          uint32_t r[32];
-          __syncwarp();
-          tc_ld32(t_lane + 32 * cg, r);
-          tc_wait_ld();
-          put_bf16<ACT, FP8>(Ah, s, cg, r, inv_scale);
-          fence_async_smem();
-          tc_fence_before();
-        }
-        if (__syncthreads_or(*abort_v)) break;
-        if (tid == 0) {
-          tc_fence_after();
-          if (!*abort_v) {
-            issue_layer3(tmem, a1_u, ah_u, img_u);
-            tc_commit(&bars[3]);
-            pend3 = 1;
+          if (coster) {  // texels of x(t), combined while layer 2 runs
+            nbar_sync(kBarState, 256);
+            cf = cost_fetch(sh, map, st_s[s]);
+            cc_prev = cc_s[s];
           }
+          // layer-1 epilogue: h1 = tanh(D1)
+          nbar_sync(kBarD1, kTcThreads);
+          tc_fence_after();
+          epilogue<ACT, FP8, false>(t_lane, 0, kColH1, sub, 1.0f);
+          nbar_arrive(kBarH1, kTcThreads);
+          if (coster && t > 0) S += cost_finish(sh, cf, t) + cc_prev;  // running cost of x(t) (Alg. 1)
+          // layer-2 epilogue: h2 = tanh(D2)
+          nbar_sync(kBarD2, kTcThreads);
+          tc_fence_after();
+          epilogue<ACT, false, FP8>(t_lane, kColD2, kColH2, sub, inv_scale);
+          nbar_arrive(kBarH2, kTcThreads);
+        }
+        if (state) {
+          step_velocities();  // x(T)
+          kinematics();
+          if (dbg) save_state(T);
+          st_s[s] = make_float4(px, py, xd1, xd2);
+          cc_s[s] = cc;
+          nbar_arrive(kBarState, 256);
+        }
+        if (coster) {
+          nbar_sync(kBarState, 256);
+          cf = cost_fetch(sh, map, st_s[s]);
+          S += cost_finish(sh, cf, T) + cc_s[s];
+          S_s[s] = S;
         }
       }
       if (__syncthreads_or(*abort_v)) break;
-      if (cg == 0) {
-        if (tc_wait(&bars[3], ph3, abort_v)) {
-          ph3 ^= 1u;
-          if (tid == 0) pend3 = 0;
-        }
-        tc_fence_after();
-        euler();  // x(T)
-        st_s[s] = make_float4(px, py, xd1, xd2);
-        cc_s[s] = cc;
-        if (dbg) save_state(T);
-      }
-      if (__syncthreads_or(*abort_v)) break;
-      if (cg == 2) {
-        const float4 x = st_s[s];
-        S += tps_state_cost(sh, map, x.x, x.y, x.z, x.w, T) + cc_s[s];
-        S_s[s] = S;
-      }
-      __syncthreads();
 
       // costs and this unit's partial record (Alg. 2 shifted by the unit's own minimum)
       float Sv = 0.f;
@@ -421,8 +490,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         rec[0] = rho; rec[1] = a; rec[2] = bb; rec[3] = c; rec[4] = d;
         rec[5] = 0.f; rec[6] = 0.f; rec[7] = 0.f;
       }
-      // E_c[t] = sum_s e_s eps_s(t): item (t, quarter) sums 32 samples, the noise drawn again
-      // from its counter (samples with e = 0 are skipped)
+      // E_c[t] = sum_s e_s eps_s(t): item (t, quarter) sums 32 samples -- from the noise block when
+      // it holds the whole horizon, else drawn again from the counter (samples with e = 0 skipped)
+      const bool resident = Tc >= T;
       const int rounds = (4 * T + kTcThreads - 1) / kTcThreads;
       for (int r = 0; r < rounds; ++r) {
         const int item = tid + r * kTcThreads;
@@ -433,7 +503,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int s2 = qq * 32; s2 < qq * 32 + 32; ++s2) {
             const float es = e_s[s2];
             if (es != 0.0f) {
-              const float2 ep = tps_noise(sh, (uint32_t)(un.k0 + s2), (uint32_t)t, I.ctr2, I.ctr3);
+              const float2 ep = resident ? eps_s[t * kRows + s2]
+                                         : tps_noise(sh, (uint32_t)(un.k0 + s2), (uint32_t)t, I.ctr2, I.ctr3);
               a0 = fmaf(es, ep.x, a0);
               a1 = fmaf(es, ep.y, a1);
             }
@@ -452,12 +523,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 
   // a wait ran out: report it, let every copy / MMA in flight land, then free the TMEM
-  if (tid == 0 && *abort_v) {
-    *sh.status = kDevErrTimeout;
-    if (pend_img) mbar_wait_bounded(&bars[0], 0, kWaitPolls);
-    if (pend1) mbar_wait_bounded(&bars[1], ph1, kWaitPolls);
-    if (pend2) mbar_wait_bounded(&bars[2], ph2, kWaitPolls);
-    if (pend3) mbar_wait_bounded(&bars[3], ph3, kWaitPolls);
+  if (*abort_v) {
+    if (tid == 0) {
+      *sh.status = kDevErrTimeout;
+      if (pend_img) mbar_wait_bounded(&bars[0], 0, kWaitPolls);
+    }
+    if (warp == kMmaWarp && lane == 0) {
+      if (pend1) mbar_wait_bounded(&bars[1], pend1 - 1u, kWaitPolls);
+      if (pend2) mbar_wait_bounded(&bars[2], pend2 - 1u, kWaitPolls);
+      if (pend3) mbar_wait_bounded(&bars[3], pend3 - 1u, kWaitPolls);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -541,13 +616,18 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(const float *__restrict__ 
 template <bool FP8, int ACT>
 cudaError_t tc_launch_t(const TpsShared &sh, const unsigned char *image, cudaStream_t s) {
   auto kern = tc_rollout_kernel<FP8, ACT>;
-  const size_t smem = smem_bytes<FP8>(sh.T_max);
   int dev = 0, sms = 0, optin = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-  if (smem > (size_t)optin) return cudaErrorInvalidValue;
+  // noise block: as many steps as fit (the whole horizon when possible)
+  // (the limit covers the kernel's static shared memory too: keep 1 KB for it)
+  const size_t fixed = smem_fixed<FP8>(sh.T_max) + 1024;
+  const size_t per_step = sizeof(float2) * kRows;
+  if (fixed + per_step > (size_t)optin) return cudaErrorInvalidValue;
+  const int Tc = (int)std::min<size_t>((size_t)sh.T_max, ((size_t)optin - fixed) / per_step);
+  const size_t smem = fixed - 1024 + per_step * (size_t)Tc;
   static size_t configured[64] = {};
   if (dev >= 0 && dev < 64 && configured[dev] < smem) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -555,7 +635,7 @@ cudaError_t tc_launch_t(const TpsShared &sh, const unsigned char *image, cudaStr
     configured[dev] = smem;
   }
   const int grid = std::min(sh.n_units, sms);  // one resident CTA per SM, persistent over units
-  kern<<<grid, kTcThreads, smem, s>>>(sh, image);
+  kern<<<grid, kTcThreads, smem, s>>>(sh, image, Tc);
   return cudaGetLastError();
 }
 

@@ -2,7 +2,7 @@
 // (tcgen05: MMA from shared-memory descriptors into tensor memory, TMEM
 // allocation, TMEM -> register loads) used by the reduced-precision rollout.
 //
-// Operand layout: every MMA operand is K-major without swizzle, built from
+// Shared-memory operand layout: K-major without swizzle, built from
 // "core matrices" of 8 rows x 16 bytes stored as 128 contiguous bytes.  For an
 // R x Kb-byte tile, byte kb of row r lives at
 //     (r / 8) * (Kb * 8) + (kb / 16) * 128 + (r % 8) * 16 + kb % 16,
@@ -51,6 +51,22 @@ __device__ __forceinline__ void tc_mma_e4m3(uint32_t tmem_d, uint64_t a, uint64_
       "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 
+// Same with the A operand in tensor memory: lane r = row r, each 32-bit column packs
+// consecutive K elements (2 BF16 or 4 E4M3, lowest first); one 32-byte K-step = 8 columns.
+__device__ __forceinline__ void tc_mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc, int accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void tc_mma_e4m3_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc, int accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
+}
+
 // The mbarrier receives one arrival once every MMA this thread issued so far has completed.
 __device__ __forceinline__ void tc_commit(uint64_t *mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -92,6 +108,26 @@ __device__ __forceinline__ void tc_ld4(uint32_t taddr, uint32_t (&r)[4]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 }
+
+// Warp stores 2 / 4 / 8 consecutive 32-bit columns of its 32 TMEM lanes (thread i -> lane i).
+__device__ __forceinline__ void tc_st2(uint32_t taddr, uint32_t a, uint32_t b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(a), "r"(b) : "memory");
+}
+
+__device__ __forceinline__ void tc_st4(uint32_t taddr, uint4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_st8(uint32_t taddr, uint4 lo, uint4 hi) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w)
+               : "memory");
+}
+
+// This thread's earlier tcgen05.st have completed.
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Hardware tanh (MUFU), ~2^-11 relative error: below the BF16/E4M3 rounding it feeds.
 __device__ __forceinline__ float tanh_mufu(float x) {
