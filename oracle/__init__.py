@@ -82,6 +82,11 @@ def lib():
             "oracle_rollout_many": (C.c_int, [P, d, d, C.c_uint64, C.c_int64, i64p, d, d, d]),
             "oracle_iterate": (C.c_int, [P, d, d, C.c_uint64, d, d, d]),
             "oracle_max_threads": (C.c_int, []),
+            "oracle_net_floats": (C.c_int, [C.c_int32]),
+            "oracle_mlp_vjp": (None, [P, d, d, d, d]),
+            "oracle_state_cost_grad": (None, [P, d, C.c_int32, d, d]),
+            "oracle_dynamics_step_vjp": (None, [P, d, d, d, d, d, d]),
+            "oracle_iterate_vjp": (C.c_int, [P, d, d, C.c_uint64, d, C.c_double, d, d, d, d, d, d, d, d]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -290,3 +295,90 @@ def iterate(P: Problem, x0, U, it: int):
 
 def max_threads() -> int:
     return int(lib().oracle_max_threads())
+
+
+def net_floats(H: int) -> int:
+    """Parameters of a 6 -> H -> H -> 4 network: W1, b1, W2, b2, W3, b3 packed in that order."""
+    return 12 * H + H * H + 4
+
+
+def pack_net(layers) -> np.ndarray:
+    """Flatten [(W1, b1), (W2, b2), (W3, b3)] in the packed order (row-major W)."""
+    return np.concatenate([np.ravel(a).astype(np.float64) for W, b in layers for a in (W, b)])
+
+
+def unpack_net(flat, H: int):
+    """Inverse of ``pack_net`` for a 6 -> H -> H -> 4 network."""
+    flat = np.asarray(flat, dtype=np.float64)
+    shapes = [(H, 6), (H,), (H, H), (H,), (4, H), (4,)]
+    out, o = [], 0
+    for sh in shapes:
+        n = int(np.prod(sh))
+        out.append(flat[o:o + n].reshape(sh))
+        o += n
+    return [(out[0], out[1]), (out[2], out[3]), (out[4], out[5])]
+
+
+def mlp_vjp(P: Problem, z, dbar):
+    """(zbar (6,), packed parameter gradient) of the network for cotangent dbar (4,)."""
+    s = P.struct()
+    z, dbar = _f64(z, (6,)), _f64(dbar, (4,))
+    zbar = np.empty(6)
+    g = np.zeros(net_floats(P.layers[0][0].shape[0]))
+    lib().oracle_mlp_vjp(C.byref(s), _ptr(z), _ptr(dbar), _ptr(zbar), _ptr(g))
+    return zbar, g
+
+
+def state_cost_grad(P: Problem, x, t: int):
+    """(dc/dx (7,), components (4,)) of the state cost at loop index t."""
+    s = P.struct()
+    x = _f64(x, (7,))
+    g = np.empty(7)
+    comp = np.empty(4)
+    lib().oracle_state_cost_grad(C.byref(s), _ptr(x), t, _ptr(g), _ptr(comp))
+    return g, comp
+
+
+def dynamics_step_vjp(P: Problem, x, gv, xbar_n):
+    """(xbar (7,), gvbar (2,), packed network gradient) of one Euler step."""
+    s = P.struct()
+    x, gv, xbar_n = _f64(x, (7,)), _f64(gv, (2,)), _f64(xbar_n, (7,))
+    xbar = np.empty(7)
+    gvbar = np.empty(2)
+    g = np.zeros(net_floats(P.layers[0][0].shape[0]))
+    lib().oracle_dynamics_step_vjp(C.byref(s), _ptr(x), _ptr(gv), _ptr(xbar_n), _ptr(xbar), _ptr(gvbar), _ptr(g))
+    return xbar, gvbar, g
+
+
+def iterate_vjp(P: Problem, x0, U, it: int, gJ: float = 1.0, gU=None, S_use=None) -> dict:
+    """Reverse-mode derivative of one iteration (FP64).
+
+    Returns the forward outputs (U', w, S, J = sum w S) and the gradient of
+    gJ * J + sum_t gU_t . U'_t with respect to the cost multipliers (4,), the
+    nominal sequence U (T, 2) and the packed network parameters.  ``S_use``
+    (K,) replaces the oracle's costs in the weights and cost cotangents.
+    """
+    s = P.struct()
+    x0, U = _f64(x0, (7,)), _f64(U, (P.T, 2))
+    gU = None if gU is None else _f64(gU, (P.T, 2))
+    S_use = None if S_use is None else _f64(S_use, (P.K,))
+    H = P.layers[0][0].shape[0]
+    out = dict(U_out=np.empty((P.T, 2)), w=np.empty(P.K), S=np.empty(P.K), J=np.empty(1), g_cost_w=np.empty(4),
+               g_U=np.empty((P.T, 2)), g_net=np.empty(net_floats(H)))
+    rc = lib().oracle_iterate_vjp(C.byref(s), _ptr(x0), _ptr(U), it, _ptr(S_use) if S_use is not None else None,
+                                  float(gJ), _ptr(gU) if gU is not None else None, _ptr(out["U_out"]),
+                                  _ptr(out["w"]), _ptr(out["S"]), _ptr(out["J"]), _ptr(out["g_cost_w"]),
+                                  _ptr(out["g_U"]), _ptr(out["g_net"]))
+    if rc:
+        raise ValueError(f"oracle_iterate_vjp: status {rc}")
+    out["J"] = float(out["J"][0])
+    return out
+
+
+def expected_cost(P: Problem, x0, U, it: int):
+    """(J = sum_k w_k S_k over finite S, U') from the forward oracle alone."""
+    rc, Uo, w, S = iterate(P, x0, U, it)
+    if rc:
+        raise ValueError(f"oracle_iterate: status {rc}")
+    fin = w != 0.0
+    return float(np.sum(w[fin] * S[fin])), Uo

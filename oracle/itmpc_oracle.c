@@ -371,3 +371,259 @@ int oracle_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ========================================================================= */
+/* Reverse-mode derivative of one iteration (the adjoint form).
+ *
+ * The paper derives no gradient of its controller; this is the chain rule
+ * applied by hand, in FP64, to the functions above, with the noise held fixed
+ * (eps does not depend on any parameter).  Outputs of the iteration:
+ *   J   = sum_k w_k S_k            (the expected weighted cost, finite S only)
+ *   U'  = sum_k w_k v_k            (Sec. III-D, as oracle_update)
+ * Given cotangents gJ (scalar) and gU (T x 2), the vector-Jacobian product
+ *   d/dtheta [ gJ J + sum_t gU_t . U'_t ]
+ * is returned for theta = the four cost multipliers, the nominal sequence U
+ * and the network parameters (packed W1 [H][6], b1 [H], W2 [H][H], b2 [H],
+ * W3 [4][H], b3 [4]).  Pieces of the chain:
+ *   - Alg. 2: dw_k/dS_j = -(1/lambda) w_k (delta_kj - w_j), so
+ *       dJ/dS_j    = w_j (1 - (S_j - J)/lambda),
+ *       dU'_t/dS_j = -(w_j/lambda) (v_{j,t} - U'_t);
+ *     rho cancels from w (shift invariance) and has no derivative.
+ *   - Sec. III-D: U'_t depends on u_t directly through v = u + eps for the
+ *     importance samples: dU'_t/du_t = sum_{k importance} w_k.
+ *   - Alg. 1 rollout: S_k = sum_{t=1..T} c(x_t, t) + gamma u_{t-1}' Sigma^-1 v_{t-1},
+ *     x_t = F(x_{t-1}, g(v_{t-1})) (Sec. V-B), reversed from t = T down to 1.
+ *   - Sec. V-C cost: the impulse terms are piecewise constant in x (zero
+ *     derivative); the capped track term passes the bilinear slope only when
+ *     h <= cap; d zeta/d(v_x, v_y) from zeta = -atan2(v_y, |v_x|) (0 at the
+ *     origin).  The clamp g passes the derivative only inside [u_min, u_max].
+ * Where S_use is given it replaces the FP64 costs in the weights, J and the
+ * cost cotangents (stage-wise checks of a GPU path against its own costs);
+ * the trajectories are always the oracle's own.                             */
+
+static double act_deriv(const oracle_problem *P, double h) { return P->activation == 1 ? 1.0 : 1.0 - h * h; }
+
+/* Network part of the step, reversed: given z and dbar = dL/df, accumulate
+ * the parameter gradient into gnet and return zbar = dL/dz. */
+void oracle_mlp_vjp(const oracle_problem *P, const double z[6], const double dbar[4], double zbar[6],
+                    double *gnet) {
+  const int H = P->H;
+  double h1[ORACLE_MAX_H], h2[ORACLE_MAX_H], h2bar[ORACLE_MAX_H], a2bar[ORACLE_MAX_H], a1bar[ORACLE_MAX_H];
+  double *gW1 = gnet, *gb1 = gW1 + 6 * H, *gW2 = gb1 + H, *gb2 = gW2 + (size_t)H * H, *gW3 = gb2 + H,
+         *gb3 = gW3 + 4 * H;
+  for (int j = 0; j < H; ++j) {
+    double a = P->b1[j];
+    for (int i = 0; i < 6; ++i) a += P->W1[j * 6 + i] * z[i];
+    h1[j] = act(P, a);
+  }
+  for (int j = 0; j < H; ++j) {
+    double a = P->b2[j];
+    for (int i = 0; i < H; ++i) a += P->W2[(size_t)j * H + i] * h1[i];
+    h2[j] = act(P, a);
+  }
+  /* output layer d = W3 h2 + b3 */
+  for (int o = 0; o < 4; ++o) {
+    gb3[o] += dbar[o];
+    for (int i = 0; i < H; ++i) gW3[o * H + i] += dbar[o] * h2[i];
+  }
+  for (int i = 0; i < H; ++i) {
+    double s = 0.0;
+    for (int o = 0; o < 4; ++o) s += P->W3[o * H + i] * dbar[o];
+    h2bar[i] = s;
+    a2bar[i] = s * act_deriv(P, h2[i]);
+  }
+  /* hidden layer 2: a2 = W2 h1 + b2 */
+  for (int j = 0; j < H; ++j) {
+    gb2[j] += a2bar[j];
+    for (int i = 0; i < H; ++i) gW2[(size_t)j * H + i] += a2bar[j] * h1[i];
+  }
+  for (int i = 0; i < H; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < H; ++j) s += P->W2[(size_t)j * H + i] * a2bar[j];
+    a1bar[i] = s * act_deriv(P, h1[i]);
+  }
+  /* hidden layer 1: a1 = W1 z + b1 */
+  for (int j = 0; j < H; ++j) {
+    gb1[j] += a1bar[j];
+    for (int m = 0; m < 6; ++m) gW1[j * 6 + m] += a1bar[j] * z[m];
+  }
+  for (int m = 0; m < 6; ++m) {
+    double s = 0.0;
+    for (int j = 0; j < H; ++j) s += P->W1[j * 6 + m] * a1bar[j];
+    zbar[m] = s;
+  }
+  (void)h2bar;
+}
+
+/* Gradient of the state cost c(x, t) with respect to x (7 entries; only
+ * p_x, p_y, v_x, v_y carry one).  comp receives the four unweighted terms as
+ * oracle_state_cost does. */
+void oracle_state_cost_grad(const oracle_problem *P, const double x[7], int32_t t, double gx[7], double comp[4]) {
+  (void)oracle_state_cost(P, x, t, comp, NULL);
+  for (int i = 0; i < 7; ++i) gx[i] = 0.0;
+  /* track: d h / d(p_x, p_y) of the bilinear lookup, zero where capped */
+  double h = oracle_costmap(P, x[0], x[1]);
+  if (!(h > P->map_cap)) {
+    double fx = (x[0] - P->origin_x) / P->res - 0.5;
+    double fy = (x[1] - P->origin_y) / P->res - 0.5;
+    double jf = floor(fx), if_ = floor(fy);
+    double a = fx - jf, b = fy - if_;
+    long W = P->map_w, Hh = P->map_h;
+    long j0 = clamp_index(jf, W), j1 = clamp_index(jf + 1.0, W);
+    long i0 = clamp_index(if_, Hh), i1 = clamp_index(if_ + 1.0, Hh);
+    double m00 = P->map[i0 * W + j0], m01 = P->map[i0 * W + j1];
+    double m10 = P->map[i1 * W + j0], m11 = P->map[i1 * W + j1];
+    double dh_dfx = (1.0 - b) * (m01 - m00) + b * (m11 - m10);
+    double dh_dfy = (1.0 - a) * (m10 - m00) + a * (m11 - m01);
+    gx[0] += P->cost_w[0] * dh_dfx / P->res;
+    gx[1] += P->cost_w[0] * dh_dfy / P->res;
+  }
+  /* speed: (v_x - v_des)^2 */
+  gx[4] += P->cost_w[1] * 2.0 * (x[4] - P->v_des);
+  /* stabilizing: zeta^2, zeta = -atan2(v_y, |v_x|) */
+  double vx = x[4], vy = x[5], r2 = vx * vx + vy * vy;
+  if (r2 > 0.0) {
+    double zeta = -atan2(vy, fabs(vx));
+    double sgn = vx > 0.0 ? 1.0 : (vx < 0.0 ? -1.0 : 0.0);
+    double dz_dvx = vy * sgn / r2, dz_dvy = -fabs(vx) / r2;
+    gx[4] += P->cost_w[2] * 2.0 * zeta * dz_dvx;
+    gx[5] += P->cost_w[2] * 2.0 * zeta * dz_dvy;
+  }
+}
+
+/* One Euler step of Sec. V-B reversed: given x = x_{t-1}, the clamped control
+ * gv and xbar_n = dL/dx_t, return xbar = dL/dx_{t-1} (through this step only),
+ * gvbar = dL/dg(v), and accumulate the network gradient. */
+void oracle_dynamics_step_vjp(const oracle_problem *P, const double x[7], const double gv[2],
+                              const double xbar_n[7], double xbar[7], double gvbar[2], double *gnet) {
+  const double dt = P->dt, th = x[2], vx = x[4], vy = x[5], c = cos(th), s = sin(th);
+  for (int i = 0; i < 7; ++i) xbar[i] = xbar_n[i];
+  xbar[2] += dt * (xbar_n[0] * (-s * vx - c * vy) + xbar_n[1] * (c * vx - s * vy));
+  xbar[4] += dt * (xbar_n[0] * c + xbar_n[1] * s);
+  xbar[5] += dt * (-xbar_n[0] * s + xbar_n[1] * c);
+  xbar[6] += dt * xbar_n[2];
+  double z[6] = {x[3], x[4], x[5], x[6], gv[0], gv[1]};
+  double dbar[4] = {dt * xbar_n[3], dt * xbar_n[4], dt * xbar_n[5], dt * xbar_n[6]};
+  double zbar[6];
+  oracle_mlp_vjp(P, z, dbar, zbar, gnet);
+  for (int i = 0; i < 4; ++i) xbar[3 + i] += zbar[i];
+  gvbar[0] = zbar[4];
+  gvbar[1] = zbar[5];
+}
+
+/* Reverse sweep of one sample (Alg. 1's inner loop backwards) with cost
+ * cotangent Sbar: accumulates into gU (T x 2), gnet and gcw (4). */
+static void rollout_sample_vjp(const oracle_problem *P, const double x0[7], const double *U, uint64_t iter,
+                               int64_t k, double Sbar, double *traj, double *vs, double *gU, double *gnet,
+                               double gcw[4]) {
+  const int32_t T = P->T;
+  int importance = (double)k < (1.0 - P->alpha_explore) * (double)P->K;
+  /* forward, keeping x_0..x_T and v_0..v_{T-1} */
+  memcpy(traj, x0, 7 * sizeof(double));
+  for (int32_t t = 1; t <= T; ++t) {
+    double eps[2], gv[2];
+    oracle_noise(P, iter, k, t - 1, eps);
+    for (int i = 0; i < 2; ++i) {
+      vs[2 * (t - 1) + i] = importance ? U[2 * (t - 1) + i] + eps[i] : eps[i];
+      gv[i] = clampd(vs[2 * (t - 1) + i], P->u_min[i], P->u_max[i]);
+    }
+    oracle_dynamics_step(P, traj + 7 * (size_t)(t - 1), gv, traj + 7 * (size_t)t);
+  }
+  /* backward */
+  double xbar[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int32_t t = T; t >= 1; --t) {
+    const double *xt = traj + 7 * (size_t)t, *xp = traj + 7 * (size_t)(t - 1), *v = vs + 2 * (t - 1);
+    const double *u = U + 2 * (t - 1);
+    double gx[7], comp[4];
+    oracle_state_cost_grad(P, xt, t, gx, comp);
+    for (int i = 0; i < 7; ++i) xbar[i] += Sbar * gx[i];
+    for (int i = 0; i < 4; ++i) gcw[i] += Sbar * comp[i];
+    double gv[2] = {clampd(v[0], P->u_min[0], P->u_max[0]), clampd(v[1], P->u_min[1], P->u_max[1])};
+    double xbar_p[7], gvbar[2];
+    oracle_dynamics_step_vjp(P, xp, gv, xbar, xbar_p, gvbar, gnet);
+    for (int i = 0; i < 2; ++i) {
+      double vbar = (v[i] >= P->u_min[i] && v[i] <= P->u_max[i]) ? gvbar[i] : 0.0;
+      double ubar = 0.0;
+      if (P->gamma != 0.0) {
+        double is2 = 1.0 / (P->sigma[i] * P->sigma[i]);
+        /* gamma u_i v_i / sigma_i^2: d/dv = gamma u_i/sigma_i^2, d/du (explicit) = gamma v_i/sigma_i^2 */
+        vbar += Sbar * P->gamma * u[i] * is2;
+        ubar += Sbar * P->gamma * v[i] * is2;
+      }
+      if (importance) ubar += vbar;
+      gU[2 * (t - 1) + i] += ubar;
+    }
+    memcpy(xbar, xbar_p, sizeof(xbar));
+  }
+}
+
+int oracle_net_floats(int32_t H) { return 12 * H + H * H + 4; }
+
+int oracle_iterate_vjp(const oracle_problem *P, const double x0[7], const double *U, uint64_t iter,
+                       const double *S_use, double gJ, const double *gUo, double *U_out, double *w, double *S,
+                       double *J_out, double *g_cost_w, double *g_U, double *g_net) {
+  int rc = check_problem(P);
+  if (rc) return rc;
+  const int64_t K = P->K;
+  const int32_t T = P->T, nf = oracle_net_floats(P->H);
+  int nt = P->n_threads > 0 ? P->n_threads : 1;
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
+  for (int64_t k = 0; k < K; ++k) S[k] = oracle_rollout_sample(P, x0, U, iter, k, NULL, NULL, NULL);
+  const double *Sw = S_use ? S_use : S;
+  rc = oracle_weights(K, Sw, P->lambda, w, NULL, NULL);
+  if (rc) return rc;
+  oracle_update(P, iter, w, U, U_out);
+  double J = 0.0, w_imp = 0.0, c0 = 0.0;
+  for (int64_t k = 0; k < K; ++k) {
+    if (w[k] != 0.0) J += w[k] * Sw[k];
+    if ((double)k < (1.0 - P->alpha_explore) * (double)K) w_imp += w[k];
+  }
+  *J_out = J;
+  if (gUo)
+    for (int32_t t = 0; t < 2 * T; ++t) c0 += gUo[t] * U_out[t];
+  for (int i = 0; i < 4; ++i) g_cost_w[i] = 0.0;
+  for (int32_t t = 0; t < 2 * T; ++t) g_U[t] = gUo ? gUo[t] * w_imp : 0.0;
+  for (int32_t i = 0; i < nf; ++i) g_net[i] = 0.0;
+  /* per-thread accumulators, summed in thread order afterwards */
+  double *acc = (double *)calloc((size_t)nt * (nf + 2 * T + 4), sizeof(double));
+  double *work = (double *)malloc((size_t)nt * (7 * (T + 1) + 2 * T) * sizeof(double));
+  if (!acc || !work) {
+    free(acc);
+    free(work);
+    return ORACLE_ERR_ARG;
+  }
+#pragma omp parallel num_threads(nt)
+  {
+#ifdef _OPENMP
+    int id = omp_get_thread_num();
+#else
+    int id = 0;
+#endif
+    double *gnet = acc + (size_t)id * (nf + 2 * T + 4), *gU = gnet + nf, *gcw = gU + 2 * T;
+    double *traj = work + (size_t)id * (7 * (T + 1) + 2 * T), *vs = traj + 7 * (T + 1);
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t k = 0; k < K; ++k) {
+      if (w[k] == 0.0) continue;
+      int importance = (double)k < (1.0 - P->alpha_explore) * (double)K;
+      double a = 0.0; /* sum_t gU_t . v_{k,t} */
+      if (gUo) {
+        for (int32_t t = 0; t < T; ++t) {
+          double eps[2];
+          oracle_noise(P, iter, k, t, eps);
+          for (int i = 0; i < 2; ++i) a += gUo[2 * t + i] * (importance ? U[2 * t + i] + eps[i] : eps[i]);
+        }
+      }
+      double Sbar = w[k] * (gJ * (1.0 - (Sw[k] - J) / P->lambda) - (a - c0) / P->lambda);
+      rollout_sample_vjp(P, x0, U, iter, k, Sbar, traj, vs, gU, gnet, gcw);
+    }
+  }
+  for (int id = 0; id < nt; ++id) {
+    const double *gnet = acc + (size_t)id * (nf + 2 * T + 4), *gU = gnet + nf, *gcw = gU + 2 * T;
+    for (int32_t i = 0; i < nf; ++i) g_net[i] += gnet[i];
+    for (int32_t t = 0; t < 2 * T; ++t) g_U[t] += gU[t];
+    for (int i = 0; i < 4; ++i) g_cost_w[i] += gcw[i];
+  }
+  free(acc);
+  free(work);
+  return ORACLE_OK;
+}
