@@ -76,7 +76,12 @@ typedef enum { ITMPC_ACT_TANH = 0, ITMPC_ACT_IDENTITY = 1 } itmpc_activation;
  *   crash_decay     the 0.9 of the time-decayed track impulse (power t = 1..T);
  *   track_thresh    0.99; slip_thresh 0.75; map_cap 2.5 (Sec. V-C)
  *   seed, instance  Philox key and instance tag
- *   precision       ITMPC_FP32 for itmpc_iterate
+ *   precision       ITMPC_FP32: every layer in FP32 on the FMA pipes (hidden 32, 64, 128);
+ *                   ITMPC_BF16 / ITMPC_FP8 (hidden == 128 only): the three network
+ *                   layers as tcgen05 tensor-core MMAs over 128-sample tiles with
+ *                   FP32 accumulation -- BF16 operands, or layer 2 in FP8 E4M3 with a
+ *                   power-of-two per-layer scale; noise, kinematics, costs, the
+ *                   normaliser and the weighted sums stay FP32
  *   activation      ITMPC_ACT_TANH (the paper's network) or ITMPC_ACT_IDENTITY
  *                   (an affine network, used by closed-form checks)
  *   stream          cudaStream_t all calls are ordered on (NULL: legacy default) */
@@ -260,6 +265,56 @@ itmpc_status itmpc_iterate_noalloc(const itmpc_config *cfg, const float *const *
                                    const float *map, int32_t width, int32_t height, float res, float origin_x,
                                    float origin_y, const float *x0, const float *U, uint64_t iter, float *U_out,
                                    float *weights, float *costs);
+
+/* ---- Adjoint form: reverse-mode derivative of one FP32 iteration ----
+ * The paper derives no gradient of its controller; these entry points apply
+ * the chain rule to Alg. 1 (rollout, running cost), Alg. 2 (weights) and the
+ * control law of Sec. III-D with the noise held fixed.  The iteration's
+ * outputs are J = sum_k w_k S_k (the expected weighted cost) and U' (T x 2);
+ * given cotangents gJ and gU the backward pass returns the gradient of
+ * gJ J + sum_t gU_t . U'_t with respect to the four cost multipliers, the
+ * nominal sequence U and the network parameters.  The impulse terms of the
+ * cost are piecewise constant (no slope), the clamp g passes the slope only
+ * inside [u_min, u_max], and a sample whose weight is 0 contributes nothing.
+ * The forward pass stores the rollout states every `every` steps; the
+ * backward pass re-runs each segment from its checkpoint, so memory is
+ * K x (T / every + 1) x 7 floats instead of the whole trajectory. */
+#define ITMPC_ADJ_MAX_EVERY 32
+
+/* Floats of the checkpoint buffer for K samples, horizon T and interval every
+ * (K x (T / every + 1) x 7: states x_t at t = 0, every, 2 every, ...), or -1
+ * for arguments out of range (every outside [1, ITMPC_ADJ_MAX_EVERY]). */
+int64_t itmpc_adjoint_ckpt_floats(int32_t K, int32_t T, int32_t every);
+
+/* Allocate the backward pass's device scratch for the context's K and T_max
+ * (per-CTA gradient records).  Requires hidden == 32 or 64 and FP32.
+ * Idempotent.  Errors: ITMPC_ERR_ARG, ITMPC_ERR_OOM. */
+itmpc_status itmpc_reserve_adjoint(itmpc_ctx *ctx);
+
+/* Forward pass: itmpc_iterate plus checkpoints and J.
+ *   x0, U, iter     as itmpc_iterate (device)
+ *   every           checkpoint interval (1..ITMPC_ADJ_MAX_EVERY; the shared memory
+ *                   of the backward pass must fit, else ITMPC_ERR_ARG)
+ *   ckpt            device, itmpc_adjoint_ckpt_floats(K, T, every) floats (written)
+ *   U_out           device T x 2 (may NOT alias U), weights and costs device K (written)
+ *   J               device, 1 float or NULL: sum_k w_k S_k
+ * Asynchronous on the context's stream.  ITMPC_ERR_STATE before itmpc_reserve_adjoint. */
+itmpc_status itmpc_iterate_fwd(itmpc_ctx *ctx, const float *x0, const float *U, uint64_t iter, int32_t every,
+                               float *ckpt, float *U_out, float *weights, float *costs, float *J);
+
+/* Backward pass for the outputs of an itmpc_iterate_fwd with the same U, iter,
+ * every and context parameters (ckpt, weights, costs, U_out are its outputs,
+ * unchanged; device).
+ *   gJ        device, 1 float, or NULL for 0: dL/dJ
+ *   gU_out    device T x 2, or NULL for 0: dL/dU'
+ *   g_cost_w  device, 4 floats (written): dL/d cost_w
+ *   g_U       device T x 2 (written): dL/dU
+ *   g_net     device, 12 H + H^2 + 4 floats (written): dL/d(W1, b1, W2, b2, W3, b3),
+ *             packed in that order, W row-major (fan_out x fan_in) as itmpc_set_dynamics
+ * The result is deterministic (fixed summation order).  Asynchronous. */
+itmpc_status itmpc_iterate_bwd(itmpc_ctx *ctx, const float *U, uint64_t iter, int32_t every, const float *ckpt,
+                               const float *weights, const float *costs, const float *U_out, const float *gJ,
+                               const float *gU_out, float *g_cost_w, float *g_U, float *g_net);
 
 /* Message for the last failing call on ctx (never NULL). */
 const char *itmpc_last_error(const itmpc_ctx *ctx);

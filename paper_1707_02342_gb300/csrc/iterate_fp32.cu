@@ -738,8 +738,8 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
             c += gamma * (u0 * v0 * p.inv_sig2_0 + u1 * v1 * p.inv_sig2_1);
           }
           Sacc[q] += c;
-          if (p.states_out != nullptr && k < p.n_states) {
-            float *o = p.states_out + ((size_t)k * (T + 1) + tau + 1) * 7;
+          if (p.states_out != nullptr && k < p.n_states && (tau + 1) % p.states_every == 0) {
+            float *o = p.states_out + ((size_t)k * (T / p.states_every + 1) + (tau + 1) / p.states_every) * 7;
             o[0] = ps.x; o[1] = ps.y; o[2] = ps.z; o[3] = xn.x; o[4] = xn.y; o[5] = xn.z; o[6] = xn.w;
           }
         }
@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
       const float S = warp_sum(Sacc[q]);
       if (k < p.K) {
         if (p.states_out != nullptr && k < p.n_states && lane < 7)
-          p.states_out[(size_t)k * (T + 1) * 7 + lane] = __ldg(p.x0 + lane);
+          p.states_out[(size_t)k * (T / p.states_every + 1) * 7 + lane] = __ldg(p.x0 + lane);
         if (lane == 0) {
           S_s[s] = S;
           p.costs[k] = S;

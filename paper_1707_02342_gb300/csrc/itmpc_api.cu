@@ -43,6 +43,8 @@ struct itmpc_ctx {
   cudaEvent_t staged = nullptr;  // the last H2D copy of the staging buffers
   // tensor-core operand images of the H = 128 network: [0] BF16, [1] FP8 layer 2
   unsigned char *tc_img[2] = {nullptr, nullptr};
+  // adjoint form (itmpc_reserve_adjoint): per-CTA gradient records and 4 scalars
+  float *adj_part = nullptr, *adj_scal = nullptr;
   std::string err;
 };
 
@@ -158,6 +160,7 @@ IterParams make_params(const itmpc_ctx *c) {
   p.grid_bar = c->counters + (c->n_counters - 2);
   p.stats = c->stats;
   p.status = c->status;
+  p.states_every = 1;
   return p;
 }
 
@@ -187,7 +190,8 @@ namespace {
 itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states);
 
 itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
-                           float *weights, float *costs, float *states, int n_states, float *eps_out) {
+                           float *weights, float *costs, float *states, int n_states, float *eps_out,
+                           int states_every = 1) {
   const bool tc = c->cfg.precision != ITMPC_FP32;
   if (tc || (!states && !eps_out && c->H == 32 && c->cfg.K >= kTpsMinK && c->inst_d)) {
     // the tensor-core kernels, or many samples: the thread-per-sample kernels, as a batch of one instance
@@ -215,6 +219,7 @@ itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64
   p.weights_inline = c->cfg.K <= 16384;
   p.states_out = states;
   p.n_states = n_states;
+  p.states_every = states_every;
   p.eps_out = eps_out;
   if (costs) p.costs = costs;  // write S_k straight into the caller's buffer
   const Fp32Tile tile = fp32_pick_tile(p.K, p.T, p.H, c->smem_optin);
@@ -238,6 +243,8 @@ void free_ctx(itmpc_ctx *c) {
   if (c->staged) cudaEventDestroy(c->staged);
   for (unsigned char *b : c->tc_img)
     if (b) cudaFree(b);
+  if (c->adj_part) cudaFree(c->adj_part);
+  if (c->adj_scal) cudaFree(c->adj_scal);
   delete c;
 }
 
@@ -665,6 +672,75 @@ itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *part
     }
     U_out[o] = (float)((double)U[o] * (eta_imp / eta) + E / eta);
   }
+  return ITMPC_OK;
+}
+
+int64_t itmpc_adjoint_ckpt_floats(int32_t K, int32_t T, int32_t every) {
+  if (K < 1 || T < 1 || every < 1 || every > ITMPC_ADJ_MAX_EVERY) return -1;
+  return (int64_t)K * (T / every + 1) * 7;
+}
+
+itmpc_status itmpc_reserve_adjoint(itmpc_ctx *c) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (c->H != 32 && c->H != 64) return fail(c, ITMPC_ERR_ARG, "the adjoint form needs hidden == 32 or 64 (got %d)", c->H);
+  if (c->adj_part) return ITMPC_OK;
+  CK(c, cudaMalloc((void **)&c->adj_part, sizeof(float) * adj_part_floats(c->K_cap, c->H, c->T_max)), "cudaMalloc");
+  CK(c, cudaMalloc((void **)&c->adj_scal, sizeof(float) * 4), "cudaMalloc");
+  return ITMPC_OK;
+}
+
+namespace {
+itmpc_status adj_check(itmpc_ctx *c, int32_t every) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (!c->adj_part) return fail(c, ITMPC_ERR_STATE, "itmpc_reserve_adjoint has not been called");
+  if (c->cfg.precision != ITMPC_FP32) return fail(c, ITMPC_ERR_ARG, "the adjoint form is FP32 only");
+  if (every < 1 || every > ITMPC_ADJ_MAX_EVERY)
+    return fail(c, ITMPC_ERR_ARG, "checkpoint interval %d outside [1, %d]", every, ITMPC_ADJ_MAX_EVERY);
+  if (adj_smem_bytes(c->H, every, c->cfg.T) > c->smem_optin)
+    return fail(c, ITMPC_ERR_ARG, "checkpoint interval %d with T=%d needs more shared memory than a CTA has", every,
+                c->cfg.T);
+  return ITMPC_OK;
+}
+}  // namespace
+
+itmpc_status itmpc_iterate_fwd(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, int32_t every,
+                               float *ckpt, float *U_out, float *weights, float *costs, float *J) {
+  itmpc_status st = adj_check(c, every);
+  if (st != ITMPC_OK) return st;
+  if (!x0 || !U || !ckpt || !U_out || !weights || !costs)
+    return fail(c, ITMPC_ERR_ARG, "x0, U, ckpt, U_out, weights and costs must be non-NULL");
+  if (U_out == U) return fail(c, ITMPC_ERR_ARG, "U_out may not alias U: the backward pass needs U");
+  st = run_iteration(c, x0, U, iter, U_out, weights, costs, ckpt, c->cfg.K, nullptr, every);
+  if (st != ITMPC_OK) return st;
+  const IterParams p = make_params(c);
+  CK(c, adj_launch_scalars(p.K, p.T, p.n_imp, weights, costs, U_out, nullptr, nullptr, c->adj_scal, J, c->stream),
+     "adjoint scalars launch");
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_iterate_bwd(itmpc_ctx *c, const float *U, uint64_t iter, int32_t every, const float *ckpt,
+                               const float *weights, const float *costs, const float *U_out, const float *gJ,
+                               const float *gU_out, float *g_cost_w, float *g_U, float *g_net) {
+  itmpc_status st = adj_check(c, every);
+  if (st != ITMPC_OK) return st;
+  if (!U || !ckpt || !weights || !costs || !U_out || !g_cost_w || !g_U || !g_net)
+    return fail(c, ITMPC_ERR_ARG, "U, ckpt, weights, costs, U_out and the three gradient outputs must be non-NULL");
+  AdjParams a{};
+  a.p = make_params(c);
+  set_iter(a.p, iter, c->cfg.instance);
+  a.p.U = U;
+  a.ckpt = ckpt;
+  a.every = every;
+  a.w = weights;
+  a.S = costs;
+  a.gUo = gU_out;
+  a.scal = c->adj_scal;
+  a.part = c->adj_part;
+  CK(c, adj_launch_scalars(a.p.K, a.p.T, a.p.n_imp, weights, costs, U_out, gU_out, gJ, c->adj_scal, nullptr,
+                           c->stream),
+     "adjoint scalars launch");
+  CK(c, adj_launch_backward(a, g_cost_w, g_U, g_net, c->stream), "adjoint backward launch");
   return ITMPC_OK;
 }
 

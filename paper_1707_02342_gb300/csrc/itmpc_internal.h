@@ -59,8 +59,9 @@ struct IterParams {
   int weights_inline;  // last CTA writes the weights itself
   // debug outputs (null in the hot path)
   float *eps_out;      // K x T x 2
-  float *states_out;   // n_states x (T+1) x 7
+  float *states_out;   // n_states x (T / states_every + 1) x 7: x_t at t = 0, every, 2 every, ...
   int n_states;
+  int states_every;    // 1: the whole trajectory; N: the adjoint form's checkpoints every N steps
 };
 
 // Launch shape of the FP32 fused kernel: nwarps warps per CTA, spw samples per
@@ -148,6 +149,23 @@ cudaError_t tc_launch(const TpsShared &sh, const unsigned char *image, int preci
                       cudaStream_t s);
 size_t tps_merge_smem_bytes(int max_units_per_instance, int T_max);
 cudaError_t launch_noise(const IterParams &p, float *eps, cudaStream_t s);
+
+// ---- adjoint form (iterate_adj.cu): reverse sweep over checkpointed FP32 rollouts ----
+struct AdjParams {
+  IterParams p;        // dynamics, costs, noise counters, map, network, U
+  const float *ckpt;   // K x (T / every + 1) x 7: x_t at t = 0, every, 2 every, ... (forward launch)
+  int every;           // checkpoint interval, 1..32
+  const float *w, *S;  // forward weights and costs (K)
+  const float *gUo;    // dL/dU' (T x 2) or null
+  const float *scal;   // [J, c0 = gU . U', sum of importance weights, gJ] (adj_launch_scalars)
+  float *part;         // per-CTA gradient records
+};
+int adj_num_ctas(int K);
+size_t adj_part_floats(int K, int H, int T_max);
+size_t adj_smem_bytes(int H, int every, int T);
+cudaError_t adj_launch_scalars(int K, int T, int n_imp, const float *w, const float *S, const float *Uo,
+                               const float *gUo, const float *gJ, float *scal, float *J_out, cudaStream_t s);
+cudaError_t adj_launch_backward(const AdjParams &a, float *g_cost_w, float *g_U, float *g_net, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);
 cudaError_t launch_tanh(const float *x, float *y, int64_t n, cudaStream_t s);
 

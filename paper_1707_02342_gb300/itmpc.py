@@ -66,6 +66,10 @@ SIGNATURES = {
     "itmpc_merge_partials": (C.c_int, [_i32, _i32, _vp, _vp, _f, _vp]),
     "itmpc_iterate_noalloc": (C.c_int, [C.POINTER(Config), _vp, _vp, _vp, _i32, _i32, _f, _f, _f, _vp, _vp, _u64,
                                         _vp, _vp, _vp]),
+    "itmpc_adjoint_ckpt_floats": (C.c_int64, [_i32, _i32, _i32]),
+    "itmpc_reserve_adjoint": (C.c_int, [_vp]),
+    "itmpc_iterate_fwd": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "itmpc_iterate_bwd": (C.c_int, [_vp, _vp, _u64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "itmpc_last_error": (C.c_char_p, [_vp]),
     "itmpc_status_string": (C.c_char_p, [_i32]),
     "itmpc_version": (C.c_int32, []),
@@ -257,6 +261,102 @@ class Controller:
     def rollout_states(self, x0, U, it: int, n: int, states, costs=None):
         self._check(self._L.itmpc_rollout_states(self._h, _dptr(x0), _dptr(U), it, n, _dptr(states),
                                                  _dptr(costs)))
+
+    # -- adjoint form -----------------------------------------------------------
+    def set_dynamics_packed(self, net):
+        """Network from one packed CUDA float32 tensor (W1, b1, W2, b2, W3, b3; net_floats(H) entries)."""
+        H = self.cfg.hidden
+        if net.numel() != net_floats(H) or not net.is_contiguous():
+            raise ValueError(f"packed network must be a contiguous tensor of {net_floats(H)} floats")
+        offs = [0, 6 * H, 7 * H, 7 * H + H * H, 8 * H + H * H, 12 * H + H * H, net_floats(H)]
+        parts = [net[offs[i]:offs[i + 1]] for i in range(6)]
+        self.set_dynamics([(parts[0], parts[1]), (parts[2], parts[3]), (parts[4], parts[5])])
+
+    def reserve_adjoint(self):
+        self._check(self._L.itmpc_reserve_adjoint(self._h))
+
+    def ckpt_floats(self, every: int) -> int:
+        n = int(self._L.itmpc_adjoint_ckpt_floats(self.cfg.K, self.cfg.T, every))
+        if n < 0:
+            raise ValueError(f"checkpoint interval {every} out of range")
+        return n
+
+    def iterate_fwd(self, x0, U, it: int, every: int, ckpt, U_out, weights, costs, J=None):
+        """Forward pass of the adjoint form: itmpc_iterate plus checkpoints and J (device tensors)."""
+        self._check(self._L.itmpc_iterate_fwd(self._h, _dptr(x0), _dptr(U), it, every, _dptr(ckpt), _dptr(U_out),
+                                              _dptr(weights), _dptr(costs), _dptr(J)))
+
+    def iterate_bwd(self, U, it: int, every: int, ckpt, weights, costs, U_out, gJ, gU_out, g_cost_w, g_U, g_net):
+        """Backward pass: gradients of gJ J + sum gU_out . U' (gJ, gU_out device tensors or None)."""
+        self._check(self._L.itmpc_iterate_bwd(self._h, _dptr(U), it, every, _dptr(ckpt), _dptr(weights),
+                                              _dptr(costs), _dptr(U_out), _dptr(gJ), _dptr(gU_out),
+                                              _dptr(g_cost_w), _dptr(g_U), _dptr(g_net)))
+
+
+def net_floats(H: int) -> int:
+    """Floats of a packed 6 -> H -> H -> 4 network (W1, b1, W2, b2, W3, b3)."""
+    return 12 * H + H * H + 4
+
+
+def _iteration_function():
+    import torch
+
+    class IterationFunction(torch.autograd.Function):
+        """One IT-MPC iteration as a differentiable function of (U, cost_w, packed network).
+
+        Forward: itmpc_iterate_fwd (the noise of iteration ``it`` is fixed);
+        outputs U' (T, 2) and J = sum_k w_k S_k (scalar).  Backward:
+        itmpc_iterate_bwd with the saved checkpoints.  Both passes set the
+        controller's cost multipliers and network from the inputs first.
+        """
+
+        @staticmethod
+        def forward(ctx, U, cost_w, net, ctl, x0, it, every):
+            ctl.set_config(cost_w=[float(v) for v in cost_w.detach().cpu()])
+            ctl.set_dynamics_packed(net.detach().contiguous())
+            dev = U.device
+            ckpt = torch.empty(ctl.ckpt_floats(every), device=dev)
+            U_out = torch.empty_like(U)
+            w = torch.empty(ctl.K, device=dev)
+            S = torch.empty(ctl.K, device=dev)
+            J = torch.empty((), device=dev)
+            Uc = U.detach().contiguous()
+            ctl.iterate_fwd(x0, Uc, it, every, ckpt, U_out, w, S, J)
+            ctx.save_for_backward(Uc, cost_w.detach(), net.detach(), ckpt, w, S, U_out)
+            ctx.ctl, ctx.it, ctx.every = ctl, it, every
+            ctx.mark_non_differentiable(w, S)
+            return U_out, J, w, S
+
+        @staticmethod
+        def backward(ctx, gU_out, gJ, gw, gS):
+            U, cost_w, net, ckpt, w, S, U_out = ctx.saved_tensors
+            ctl = ctx.ctl
+            ctl.set_config(cost_w=[float(v) for v in cost_w.cpu()])
+            ctl.set_dynamics_packed(net.contiguous())
+            g_cw = torch.empty(4, device=U.device)
+            g_U = torch.empty_like(U)
+            g_net = torch.empty_like(net)
+            gU_out = None if gU_out is None else gU_out.contiguous()
+            gJ = None if gJ is None else gJ.reshape(1).contiguous()
+            ctl.iterate_bwd(U, ctx.it, ctx.every, ckpt, w, S, U_out, gJ, gU_out, g_cw, g_U, g_net)
+            return g_U, g_cw.to(cost_w.dtype), g_net, None, None, None, None
+
+    return IterationFunction
+
+
+_ITER_FN = None
+
+
+def iterate_differentiable(ctl: Controller, x0, U, cost_w, net, it: int, every: int = 10):
+    """(U', J, weights, costs) of one iteration, differentiable in U, cost_w (4,) and the packed network.
+
+    ``ctl`` must have been given a costmap and ``reserve_adjoint()``; x0, U and
+    net are CUDA float32 tensors, cost_w a float32 tensor of 4 multipliers.
+    """
+    global _ITER_FN
+    if _ITER_FN is None:
+        _ITER_FN = _iteration_function()
+    return _ITER_FN.apply(U, cost_w, net, ctl, x0, it, every)
 
 
 def philox(ctr, key, out, stream=None):
