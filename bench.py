@@ -40,21 +40,25 @@ PROFILE = os.path.join(ROOT, "profiles", "iterate_fp32_K2048_T100.md")
 KERNEL_SOURCES = ["paper_1707_02342_gb300/csrc/iterate_fp32.cu", "paper_1707_02342_gb300/csrc/itmpc_device.cuh"]
 
 
-def kernel_source_hash() -> str:
+ADJ_PROFILE = os.path.join(ROOT, "profiles", "adj_backward_K4096_T100_H64.md")
+ADJ_SOURCES = ["paper_1707_02342_gb300/csrc/iterate_adj.cu"]
+
+
+def kernel_source_hash(sources=None) -> str:
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:12]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
-    if not os.path.exists(PROFILE):
+def profiled_traffic(profile=PROFILE, sources=None):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernel source."""
+    if not os.path.exists(profile):
         return None
-    text = open(PROFILE).read()
-    m_src = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
+    text = open(profile).read()
+    m_src = re.search(r"kernel_source_sha1[^:]*:\s*([0-9a-f]+)", text)
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_src or not m_b or m_src.group(1) != kernel_source_hash():
+    if not m_src or not m_b or m_src.group(1) != kernel_source_hash(sources):
         return None
     return float(m_b.group(1))
 
@@ -203,6 +207,141 @@ def measure_batched(params, layers, steps: int = 10, warmup: int = 3):
     return {"workload": "256 instances, K~U{512..8192}, T~U{40,60,100,150}, 8 spline maps 1024^2, H=32 FP32",
             "sample_steps_per_launch": sample_steps, "ms_per_step": ms_per, "value": sample_steps / (ms_per * 1e-3),
             "unit": UNIT, "gpu_launches_per_step": 2, "achieved_tflops": achieved}
+
+
+def _timed(fn, steps: int, warmup: int, flush):
+    """Median and mean CUDA-event time (ms) of fn() over ``steps`` calls, L2 flushed before each."""
+    import numpy as np
+    import torch
+
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts)), float(np.mean(ts))
+
+
+def _controller(K, T, H, tmap, layers, params, **kw):
+    import torch
+
+    from paper_1707_02342_gb300 import itmpc
+
+    ctl = itmpc.Controller(K, T, hidden=H, **dict(params, **kw))
+    ctl.set_dynamics([(torch.tensor(W, device="cuda"), torch.tensor(b, device="cuda")) for W, b in layers])
+    ctl.set_costmap(torch.tensor(tmap.data, device="cuda"), tmap.res, tmap.origin_x, tmap.origin_y)
+    return ctl
+
+
+def measure_precision(params, flush, cores, steps: int = 20, warmup: int = 3):
+    """The precision form: K = 16384, T = 100, 6->128->128->4 network, FP32 vs BF16 vs FP8 (tcgen05),
+    each timed through itmpc_iterate and compared with the FP64 oracle run on every sample."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1707_02342_gb300 import inputs, itmpc
+
+    K, T, H = 16384, 100, 128
+    tmap = inputs.track_costmap(inputs.spline_centerline(1), 1024, 0.1, 2.5)
+    layers = inputs.mlp_xavier((6, H, H, 4), seed=42)
+    x0 = inputs.start_state(tmap.centerline)
+    x0[4] = 4.0
+    U = inputs.nominal_controls(T, seed=9, scale=0.2)
+    it = 5
+    P = oracle.Problem(K=K, T=T, layers=layers, costmap=tmap.data, res=tmap.res, origin_x=tmap.origin_x,
+                       origin_y=tmap.origin_y, lam=params["lam"], sigma=params["sigma"], cost_w=params["cost_w"],
+                       n_threads=cores)
+    t0 = time.perf_counter()
+    rc, U64, w64, S64 = oracle.iterate(P, x0, U, it)
+    t_oracle = time.perf_counter() - t0
+    J64 = float(np.sum(w64[w64 > 0] * S64[w64 > 0]))
+    out = {"workload": f"it-mpc iteration K={K} T={T} 6->{H}->{H}->4 spline-1024 map",
+           "sample_steps_per_launch": K * T, "oracle_s": t_oracle}
+    flop = 2 * (6 * H + H * H + 4 * H) * K * T
+    x0_d, U_d = torch.tensor(x0, device="cuda"), torch.tensor(U, device="cuda")
+    base_ms = None
+    for name, prec in (("fp32", itmpc.FP32), ("bf16", itmpc.BF16), ("fp8", itmpc.FP8)):
+        ctl = _controller(K, T, H, tmap, layers, params, precision=prec)
+        Uo, w, S = torch.empty_like(U_d), torch.empty(K, device="cuda"), torch.empty(K, device="cuda")
+        med, mean = _timed(lambda: ctl.iterate(x0_d, U_d, it, Uo, w, S), steps, warmup, flush)
+        assert ctl.read_status() == itmpc.OK
+        Sg, wg, Ug = (t.double().cpu().numpy() for t in (S, w, Uo))
+        rel = np.abs(Sg - S64) / np.maximum(np.abs(S64), 1.0)
+        Jg = float(np.sum(wg[wg > 0] * Sg[wg > 0]))
+        base_ms = base_ms or mean
+        out[name] = {"ms_per_step": mean, "ms_median": med, "value": K * T / (mean * 1e-3), "unit": UNIT,
+                     "speedup_vs_fp32": base_ms / mean, "algorithmic_tflops": flop / (mean * 1e-3) / 1e12,
+                     "err_vs_fp64": {"cost_rel_median": float(np.median(rel)),
+                                     "cost_rel_p99": float(np.quantile(rel, 0.99)),
+                                     "cost_rel_max": float(rel.max()),
+                                     "expected_cost_rel": abs(Jg - J64) / abs(J64),
+                                     "U_out_err_over_update": float(np.abs(Ug - U64).max() / np.abs(U64 - U).max())}}
+        ctl.close()
+    return out
+
+
+def measure_adjoint(params, flush, cores, steps: int = 20, warmup: int = 3, every: int = 10):
+    """The adjoint form: K = 4096, T = 100, 6->64->64->4, checkpoints every 10 steps; forward + backward
+    time next to the plain iteration and to central differences, gradient error vs the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1707_02342_gb300 import inputs
+
+    K, T, H = 4096, 100, 64
+    tmap = inputs.track_costmap(inputs.spline_centerline(1), 1024, 0.1, 2.5)
+    layers = inputs.mlp_xavier((6, H, H, 4), seed=42)
+    x0 = inputs.start_state(tmap.centerline)
+    x0[4] = 4.0
+    U = inputs.nominal_controls(T, seed=9, scale=0.2)
+    it = 11
+    ctl = _controller(K, T, H, tmap, layers, params)
+    ctl.reserve_adjoint()
+    x0_d, U_d = torch.tensor(x0, device="cuda"), torch.tensor(U, device="cuda")
+    ck = torch.empty(ctl.ckpt_floats(every), device="cuda")
+    Uo, w, S, J = torch.empty_like(U_d), torch.empty(K, device="cuda"), torch.empty(K, device="cuda"), \
+        torch.empty(1, device="cuda")
+    gU_h = np.random.default_rng(3).standard_normal((T, 2)).astype(np.float32)
+    gJ, gU = torch.ones(1, device="cuda"), torch.tensor(gU_h, device="cuda")
+    nf = 12 * H + H * H + 4
+    g_cw, g_U, g_net = torch.empty(4, device="cuda"), torch.empty_like(U_d), torch.empty(nf, device="cuda")
+    plain = _timed(lambda: ctl.iterate(x0_d, U_d, it, Uo, w, S), steps, warmup, flush)[1]
+    fwd = _timed(lambda: ctl.iterate_fwd(x0_d, U_d, it, every, ck, Uo, w, S, J), steps, warmup, flush)[1]
+    bwd = _timed(lambda: ctl.iterate_bwd(U_d, it, every, ck, w, S, Uo, gJ, gU, g_cw, g_U, g_net), steps, warmup,
+                 flush)[1]
+    assert ctl.read_status() == 0
+    Sg = S.double().cpu().numpy()
+    active = int(np.count_nonzero(w.cpu().numpy()))
+    P = oracle.Problem(K=K, T=T, layers=layers, costmap=tmap.data, res=tmap.res, origin_x=tmap.origin_x,
+                       origin_y=tmap.origin_y, lam=params["lam"], sigma=params["sigma"], cost_w=params["cost_w"],
+                       n_threads=cores)
+    ref = oracle.iterate_vjp(P, x0, U, it, 1.0, gU_h.astype(np.float64), S_use=Sg)
+    got = {"cost_w": g_cw, "U": g_U, "net": g_net}
+    want = {"cost_w": ref["g_cost_w"], "U": ref["g_U"], "net": ref["g_net"]}
+    err = {k: float(np.linalg.norm(got[k].double().cpu().numpy().ravel() - want[k].ravel()) /
+                    np.linalg.norm(want[k])) for k in got}
+    ctl.close()
+    n_params = nf + 4 + 2 * T
+    bwd_flop = 2 * 2 * (6 * H + H * H + 4 * H) * active * T  # reverse network sweep: twice the forward MACs
+    return {"workload": f"adjoint of one iteration K={K} T={T} 6->{H}->{H}->4 spline-1024 map, "
+                        f"checkpoints every {every} steps", "active_samples": active,
+            "plain_ms": plain, "fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_over_plain": (fwd + bwd) / plain,
+            "n_params": n_params,
+            "speedup_vs_central_differences": 2 * n_params * plain / (fwd + bwd),
+            "grad_rel_err_vs_fp64": err,
+            "bwd_roofline": {"bound": "alu", "achieved": bwd_flop / (bwd * 1e-3) / 1e12, "unit": "TFLOP/s",
+                             "algorithmic_flop": bwd_flop,
+                             "traffic": profiled_traffic(ADJ_PROFILE, ADJ_SOURCES)}}
 
 
 def peaks():
@@ -371,11 +510,47 @@ def run_ours(args, rank, world, local_rank):
                           "unit": "TFLOP/s"}
         bt["roofline"]["frac"] = bt["roofline"]["achieved"] / peak_tflops
         line["forms"] = {"batched": bt}
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        pr = measure_precision(params, flush, cores)
+        bf_peak = pk.get("bf16_tflops", 1900.0)
+        for name, pkv in (("bf16", bf_peak), ("fp8", 2 * bf_peak)):
+            pr[name]["roofline"] = {"bound": "tensor", "achieved": pr[name]["algorithmic_tflops"], "peak": pkv,
+                                    "unit": "TFLOP/s", "frac": pr[name]["algorithmic_tflops"] / pkv,
+                                    "peak_note": "measured bf16 burst" + (" x 2 (nominal fp8/bf16 ratio)"
+                                                                           if name == "fp8" else "")}
+        pr["fp32"]["roofline"] = {"bound": "alu", "achieved": pr["fp32"]["algorithmic_tflops"], "peak": peak_tflops,
+                                  "unit": "TFLOP/s", "frac": pr["fp32"]["algorithmic_tflops"] / peak_tflops}
+        line["forms"]["precision"] = pr
+        ad = measure_adjoint(params, flush, cores)
+        ad["bwd_roofline"]["peak"] = peak_tflops
+        ad["bwd_roofline"]["frac"] = ad["bwd_roofline"]["achieved"] / peak_tflops
+        line["forms"]["adjoint"] = ad
     if world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_oracle_rate(seconds=args.cpu_seconds)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     ctl.close()
+
+
+def run_only(args):
+    """One form alone, a few steps (for ncu captures of its kernels)."""
+    import torch
+
+    from paper_1707_02342_gb300 import build as nbuild
+
+    torch.cuda.set_device(0)
+    nbuild.build()
+    _, layers, _, _, params = workload()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    steps, warm = max(1, args.steps), args.warmup
+    if args.only == "batched":
+        out = measure_batched(params, layers, steps=steps, warmup=warm)
+    elif args.only == "precision":
+        out = measure_precision(params, flush, cores, steps=steps, warmup=warm)
+    else:
+        out = measure_adjoint(params, flush, cores, steps=steps, warmup=warm)
+    print(json.dumps({"only": args.only, **out}), flush=True)
 
 
 def main():
@@ -387,6 +562,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / precision / adjoint forms")
+    ap.add_argument("--only", choices=["batched", "precision", "adjoint"], default=None,
+                    help="run one form alone and print its JSON (profiling runs); not a benchmark line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -394,6 +571,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.only:
+        run_only(args)
         return
     if world > 1:
         import torch
