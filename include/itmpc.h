@@ -198,10 +198,41 @@ itmpc_status itmpc_reserve_batch(itmpc_ctx *ctx, int32_t max_instances, int64_t 
 /* One control iteration of n independent instances in one launch (Alg. 1 and
  * Alg. 2 per instance; the thread-per-sample kernels of iterate_tps.cu): a
  * persistent kernel pulls (instance, 128-sample tile) work units, longest
- * horizon first, then one CTA per instance merges its partial sums.  inst is
+ * horizon first (work-unit size: itmpc_autotune_batch), then one CTA per
+ * instance merges its partial sums.  inst is
  * a host array of n descriptors.  Asynchronous; an instance whose costs are
  * all non-finite gets U_out = U and records ITMPC_ERR_NONFINITE. */
 itmpc_status itmpc_iterate_batch(itmpc_ctx *ctx, int32_t n, const itmpc_instance *inst);
+
+/* Choose the launch shape of batched FP32 iterations for this batch by timing
+ * it: samples per work unit (= threads per CTA) in {64, 128, 256} and the
+ * number of resident CTAs per SM (the occupancy limit or half of it); `reps`
+ * timed runs per candidate (0: 3).  The runs write to scratch outputs (the
+ * caller's U_out, weights, costs and stats are left untouched; x0 and U are
+ * only read); later itmpc_iterate_batch calls and graphs use the winner.
+ * The tensor-core (BF16 / FP8) kernels have a fixed shape (a unit is one
+ * 128-row MMA tile, one CTA per SM), reported without timing.  Synchronous.
+ * nt_out, ctas_out (may be NULL): the chosen shape (ctas 0 = occupancy limit). */
+itmpc_status itmpc_autotune_batch(itmpc_ctx *ctx, int32_t n, const itmpc_instance *inst, int32_t reps,
+                                  int32_t *nt_out, int32_t *ctas_out);
+
+/* Capture one batched iteration of the n instances into a CUDA graph owned by
+ * the context, for closed-loop use: each itmpc_batch_graph_launch replays the
+ * rollout and merge launches and then advances every instance's Philox
+ * iteration index by one on the device, so replay r (counting from 0 after
+ * create) draws the noise of iteration inst[i].iter + r.  With U_out == U each
+ * replay starts from the previous U'.  The graph keeps the descriptors, the
+ * parameters, the network and the costmaps as they are at create (pointers to
+ * x0, U and the outputs are read by every replay); create it again after
+ * changing any of them.  A new create replaces the previous graph.
+ * Errors: ITMPC_ERR_STATE before itmpc_reserve_batch, ITMPC_ERR_ARG, ITMPC_ERR_CUDA. */
+itmpc_status itmpc_batch_graph_create(itmpc_ctx *ctx, int32_t n, const itmpc_instance *inst);
+
+/* Replay the captured graph once on the context's stream (asynchronous). */
+itmpc_status itmpc_batch_graph_launch(itmpc_ctx *ctx);
+
+/* Release the captured graph (waits for the context's stream); no-op without one. */
+itmpc_status itmpc_batch_graph_destroy(itmpc_ctx *ctx);
 
 /* Diagnostics for stage-wise checks.
  * itmpc_noise: eps of iteration iter for every (k, t), device K x T x 2.

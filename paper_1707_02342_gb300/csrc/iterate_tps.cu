@@ -11,8 +11,8 @@
 // enough samples to keep every SM busy; at a few thousand samples the
 // warp-per-sample kernel of iterate_fp32.cu is faster.
 //
-// Kernel 1 (persistent): CTAs pull work units -- kTpsThreads consecutive
-// samples of one instance, longest horizon first -- from a global counter and
+// Kernel 1 (persistent): CTAs pull work units -- NT (64, 128 or 256, the
+// autotuned tile) consecutive samples of one instance, longest horizon first -- from a global counter and
 // write one partial record per unit (rho_c, eta_c, ..., E_c: Alg. 2 shifted by
 // the unit's own minimum).  Kernel 2: one CTA per instance merges that
 // instance's records into U', the weights and the diagnostics (log-sum-exp
@@ -89,13 +89,14 @@ __device__ __forceinline__ void tps_network(const TpsNet<H> &N, float x0, float 
   d0 = d[0]; d1 = d[1]; d2 = d[2]; d3 = d[3];
 }
 
-template <int H, int ACT>
-__global__ void __launch_bounds__(kTpsThreads, 5) tps_rollout_kernel(const __grid_constant__ TpsParams<H> P) {
-  constexpr int NWARP = kTpsThreads / 32;
+template <int H, int ACT, int NT>
+__global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsParams<H> P) {
+  constexpr int NWARP = NT / 32;
+  constexpr int G = NT / 32;  // 32-sample groups of a unit
   const TpsShared &sh = P.sh;
   const TpsNet<H> &N = P.net;
   __shared__ float U_s[2 * ITMPC_MAX_T_DEV];
-  __shared__ float e_s[kTpsThreads];
+  __shared__ float e_s[NT];
   __shared__ float red[NWARP][5];
   __shared__ int unit_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kTpsThreads, 5) tps_rollout_kernel(const __gri
     const TpsUnit un = sh.units[u];
     const TpsInstance &I = sh.inst[un.inst];
     const int K = I.K, T = I.T;
-    for (int i = tid; i < 2 * T; i += kTpsThreads) U_s[i] = __ldg(I.U + i);
+    for (int i = tid; i < 2 * T; i += NT) U_s[i] = __ldg(I.U + i);
     __syncthreads();
 
     const int k = un.k0 + tid;
@@ -172,13 +173,14 @@ __global__ void __launch_bounds__(kTpsThreads, 5) tps_rollout_kernel(const __gri
       rec[0] = rho; rec[1] = a; rec[2] = b; rec[3] = c; rec[4] = d;
       rec[5] = 0.f; rec[6] = 0.f; rec[7] = 0.f;
     }
-    // E_c[t] = sum_s e_s eps_s(t): item (t, quarter) sums 32 samples; the noise is
-    // drawn again from its counter (samples with e = 0 are skipped)
-    const int rounds = (4 * T + kTpsThreads - 1) / kTpsThreads;
+    // E_c[t] = sum_s e_s eps_s(t): item (t, group) sums 32 samples; the noise is
+    // drawn again from its counter (samples with e = 0 are skipped); the G items
+    // of one t sit on G consecutive lanes
+    const int rounds = (G * T + NT - 1) / NT;
     for (int r = 0; r < rounds; ++r) {
-      const int item = tid + r * kTpsThreads;
-      const bool valid = item < 4 * T;
-      const int t = item >> 2, q = item & 3;
+      const int item = tid + r * NT;
+      const bool valid = item < G * T;
+      const int t = item / G, q = item % G;
       float a0 = 0.f, a1 = 0.f;
       if (valid) {
         for (int s2 = q * 32; s2 < q * 32 + 32; ++s2) {
@@ -190,10 +192,11 @@ __global__ void __launch_bounds__(kTpsThreads, 5) tps_rollout_kernel(const __gri
           }
         }
       }
-      a0 += __shfl_xor_sync(FULL_MASK, a0, 1);
-      a1 += __shfl_xor_sync(FULL_MASK, a1, 1);
-      a0 += __shfl_xor_sync(FULL_MASK, a0, 2);
-      a1 += __shfl_xor_sync(FULL_MASK, a1, 2);
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        a0 += __shfl_xor_sync(FULL_MASK, a0, o);
+        a1 += __shfl_xor_sync(FULL_MASK, a1, o);
+      }
       if (valid && q == 0) {
         rec[8 + 2 * t] = a0;
         rec[8 + 2 * t + 1] = a1;
@@ -229,25 +232,42 @@ __global__ void __launch_bounds__(kMergeThreads) tps_merge_kernel(const __grid_c
                                stage_floats, &mbar, phase);
 }
 
-template <int H, int ACT>
-cudaError_t tps_launch_h(const TpsShared &sh, const float *net_host, cudaStream_t s) {
+template <int H, int ACT, int NT>
+cudaError_t tps_launch_h(const TpsShared &sh, const float *net_host, int ctas_per_sm, cudaStream_t s) {
   TpsParams<H> P;
   P.sh = sh;
   // packed layout W1 [H][6], b1 [H], W2 [H][H], b2 [H], W3 [4][H], b3 [4] (== TpsNet field order)
   static_assert(sizeof(TpsNet<H>) == sizeof(float) * (size_t)net_floats(H), "network layout");
   memcpy(&P.net, net_host, sizeof(TpsNet<H>));
-  auto kern = tps_rollout_kernel<H, ACT>;
+  auto kern = tps_rollout_kernel<H, ACT, NT>;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTpsThreads, 0)) != cudaSuccess) return e;
-  const int grid = std::min(sh.n_units, std::max(1, per_sm) * sms);
-  kern<<<grid, kTpsThreads, 0, s>>>(P);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0)) != cudaSuccess) return e;
+  per_sm = std::max(1, per_sm);
+  if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+  const int grid = std::min(sh.n_units, per_sm * sms);
+  kern<<<grid, NT, 0, s>>>(P);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+__global__ void tps_advance_kernel(TpsInstance *inst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t it = (uint64_t)inst[i].ctr2 | ((uint64_t)(inst[i].ctr3 & 0xFFFFu) << 32);
+  const uint64_t nx = (it + 1) & 0xFFFFFFFFFFFFull;
+  inst[i].ctr2 = (uint32_t)nx;
+  inst[i].ctr3 = (inst[i].ctr3 & 0xFFFF0000u) | (uint32_t)(nx >> 32);
+}
+
+cudaError_t tps_launch_advance(TpsInstance *inst, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  tps_advance_kernel<<<(n + 127) / 128, 128, 0, s>>>(inst, n);
+  return cudaGetLastError();
+}
 
 size_t tps_merge_smem_bytes(int max_units_per_instance, int T_max) {
   const size_t n = (size_t)max_units_per_instance;
@@ -273,11 +293,21 @@ cudaError_t tps_merge(const TpsShared &sh, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, cudaStream_t s) {
+cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, TpsTile tile,
+                       cudaStream_t s) {
   if (sh.n_units <= 0 || sh.n_inst <= 0) return cudaSuccess;
+  if (H != 32) return cudaErrorInvalidValue;  // the weights of wider networks do not fit the parameter space
   cudaError_t e;
-  if (H == 32) e = activation == 1 ? tps_launch_h<32, 1>(sh, net_host, s) : tps_launch_h<32, 0>(sh, net_host, s);
-  else return cudaErrorInvalidValue;  // the weights of wider networks do not fit the parameter space
+  const int c = tile.ctas_per_sm;
+  switch (tile.nt * 2 + (activation == 1)) {
+    case 128: e = tps_launch_h<32, 0, 64>(sh, net_host, c, s); break;
+    case 129: e = tps_launch_h<32, 1, 64>(sh, net_host, c, s); break;
+    case 256: e = tps_launch_h<32, 0, 128>(sh, net_host, c, s); break;
+    case 257: e = tps_launch_h<32, 1, 128>(sh, net_host, c, s); break;
+    case 512: e = tps_launch_h<32, 0, 256>(sh, net_host, c, s); break;
+    case 513: e = tps_launch_h<32, 1, 256>(sh, net_host, c, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   if (e != cudaSuccess) return e;
   return tps_merge(sh, s);
 }

@@ -45,6 +45,11 @@ struct itmpc_ctx {
   unsigned char *tc_img[2] = {nullptr, nullptr};
   // adjoint form (itmpc_reserve_adjoint): per-CTA gradient records and 4 scalars
   float *adj_part = nullptr, *adj_scal = nullptr;
+  // batched form: FP32 launch shape (itmpc_autotune_batch) and the captured closed-loop graph
+  TpsTile tps_tile{kTpsThreads, 0};
+  cudaGraphExec_t graph_exec = nullptr;
+  TpsInstance *ginst_d = nullptr;
+  TpsUnit *gunits_d = nullptr;
   std::string err;
 };
 
@@ -188,6 +193,14 @@ extern "C" itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances,
 namespace {
 
 itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states);
+itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
+                            TpsTile tile);
+itmpc_status build_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, int nt, TpsInstance *inst_h,
+                         TpsUnit *units_h, int *n_units);
+TpsShared batch_shared(const itmpc_ctx *c, const TpsInstance *inst_d, const TpsUnit *units_d, int n, int n_units);
+itmpc_status launch_batch(itmpc_ctx *c, const TpsShared &sh, TpsTile tile, cudaStream_t s);
+itmpc_status batch_ready(itmpc_ctx *c);
+int batch_nt(const itmpc_ctx *c);
 
 itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
                            float *weights, float *costs, float *states, int n_states, float *eps_out,
@@ -245,6 +258,9 @@ void free_ctx(itmpc_ctx *c) {
     if (b) cudaFree(b);
   if (c->adj_part) cudaFree(c->adj_part);
   if (c->adj_scal) cudaFree(c->adj_scal);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->ginst_d) cudaFree(c->ginst_d);
+  if (c->gunits_d) cudaFree(c->gunits_d);
   delete c;
 }
 
@@ -429,7 +445,7 @@ itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances, int64_t ma
   c->units_d = c->units_h = nullptr;
   c->batch_partials = c->batch_costs = c->batch_stats = nullptr;
   c->unit_counter = nullptr;
-  const int64_t max_units = max_total_samples / kTpsThreads + max_instances;
+  const int64_t max_units = max_total_samples / kTpsMinUnit + max_instances;
   if (max_units > ((int64_t)1 << 30)) return fail(c, ITMPC_ERR_ARG, "batch too large");
   CK(c, cudaMalloc((void **)&c->inst_d, sizeof(TpsInstance) * max_instances), "batch cudaMalloc");
   CK(c, cudaMalloc((void **)&c->units_d, sizeof(TpsUnit) * max_units), "batch cudaMalloc");
@@ -453,16 +469,134 @@ itmpc_status itmpc_iterate_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *
   return run_batch(c, n, inst, nullptr, 0);
 }
 
+itmpc_status itmpc_autotune_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, int32_t reps,
+                                  int32_t *nt_out, int32_t *ctas_out) {
+  itmpc_status st = batch_ready(c);
+  if (st != ITMPC_OK) return st;
+  if (n < 1 || !inst) return fail(c, ITMPC_ERR_ARG, "empty batch");
+  if (reps < 1) reps = 3;
+  if (c->cfg.precision != ITMPC_FP32) {  // one MMA tile per unit, one CTA per SM: nothing to choose
+    if (nt_out) *nt_out = kTpsThreads;
+    if (ctas_out) *ctas_out = 1;
+    return ITMPC_OK;
+  }
+  // run the caller's batch with its outputs redirected to scratch, so nothing the caller owns changes
+  int64_t uo_floats = 0;
+  for (int i = 0; i < n; ++i) uo_floats += 2 * (int64_t)std::max(inst[i].T, 0);
+  float *uo = nullptr;
+  CK(c, cudaMalloc((void **)&uo, sizeof(float) * std::max<int64_t>(uo_floats, 1)), "autotune cudaMalloc");
+  std::vector<itmpc_instance> q(inst, inst + n);
+  int64_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    q[i].U_out = uo + off;
+    off += 2 * (int64_t)std::max(inst[i].T, 0);
+    q[i].weights = nullptr;
+    q[i].costs = nullptr;
+    q[i].stats = nullptr;
+  }
+  const TpsTile cands[] = {{64, 0}, {64, 5}, {128, 0}, {128, 2}, {256, 0}, {256, 1}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TpsTile best = c->tps_tile;
+  float best_ms = INFINITY;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  for (const TpsTile &t : cands) {
+    if (ce != cudaSuccess) break;
+    st = run_batch_tile(c, n, q.data(), nullptr, 0, t);  // warm-up
+    if (st != ITMPC_OK) break;
+    float tot = 0.f;
+    for (int r = 0; r < reps && st == ITMPC_OK; ++r) {
+      ce = cudaEventRecord(e0, c->stream);
+      if (ce != cudaSuccess) break;
+      st = run_batch_tile(c, n, q.data(), nullptr, 0, t);
+      if (st != ITMPC_OK) break;
+      ce = cudaEventRecord(e1, c->stream);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess) break;
+      tot += ms;
+    }
+    if (st != ITMPC_OK || ce != cudaSuccess) break;
+    if (tot / reps < best_ms) {
+      best_ms = tot / reps;
+      best = t;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(uo);
+  if (st != ITMPC_OK) return st;
+  if (ce != cudaSuccess) return cuda_fail(c, ce, "autotune timing");
+  // the runs leave the status word of their own (scratch) outputs: clear it
+  CK(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "status reset");
+  c->tps_tile = best;
+  if (nt_out) *nt_out = best.nt;
+  if (ctas_out) *ctas_out = best.ctas_per_sm;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_batch_graph_destroy(itmpc_ctx *c) {
+  if (!c) return ITMPC_ERR_ARG;
+  CK(c, cudaStreamSynchronize(c->stream), "sync");
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->ginst_d) cudaFree(c->ginst_d);
+  if (c->gunits_d) cudaFree(c->gunits_d);
+  c->graph_exec = nullptr;
+  c->ginst_d = nullptr;
+  c->gunits_d = nullptr;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_batch_graph_create(itmpc_ctx *c, int32_t n, const itmpc_instance *inst) {
+  itmpc_status st = batch_ready(c);
+  if (st != ITMPC_OK) return st;
+  st = itmpc_batch_graph_destroy(c);
+  if (st != ITMPC_OK) return st;
+  const int nt = batch_nt(c);
+  std::vector<TpsInstance> ih((size_t)std::max(n, 1));
+  std::vector<TpsUnit> uh((size_t)std::max(c->batch_max_units, 1));
+  int u = 0;
+  st = build_batch(c, n, inst, nt, ih.data(), uh.data(), &u);
+  if (st != ITMPC_OK) return st;
+  CK(c, cudaMalloc((void **)&c->ginst_d, sizeof(TpsInstance) * n), "graph cudaMalloc");
+  CK(c, cudaMalloc((void **)&c->gunits_d, sizeof(TpsUnit) * u), "graph cudaMalloc");
+  CK(c, cudaMemcpy(c->ginst_d, ih.data(), sizeof(TpsInstance) * n, cudaMemcpyHostToDevice), "graph copy");
+  CK(c, cudaMemcpy(c->gunits_d, uh.data(), sizeof(TpsUnit) * u, cudaMemcpyHostToDevice), "graph copy");
+  const TpsShared sh = batch_shared(c, c->ginst_d, c->gunits_d, n, u);
+  cudaStream_t cap = nullptr;
+  CK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = launch_batch(c, sh, c->tps_tile, cap);
+    const cudaError_t ea = st == ITMPC_OK ? tps_launch_advance(c->ginst_d, n, cap) : cudaSuccess;
+    e = cudaStreamEndCapture(cap, &graph);
+    if (e == cudaSuccess) e = ea;
+  }
+  if (e == cudaSuccess && st == ITMPC_OK) e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (st != ITMPC_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_batch_graph_launch(itmpc_ctx *c) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (!c->graph_exec) return fail(c, ITMPC_ERR_STATE, "itmpc_batch_graph_create has not been called");
+  CK(c, cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
+  return ITMPC_OK;
+}
+
 }  // extern "C"
 
 namespace {
 
-itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states) {
-  itmpc_status st = ready(c);
-  if (st != ITMPC_OK) return st;
-  const bool tc = c->cfg.precision != ITMPC_FP32;
-  if (!tc && c->H != 32) return fail(c, ITMPC_ERR_ARG, "batched FP32 iterations need hidden == 32");
-  if (!c->inst_d) return fail(c, ITMPC_ERR_STATE, "itmpc_reserve_batch has not been called");
+// Validate a batch and write its host descriptors (nt-sample units, longest horizon first).
+itmpc_status build_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, int nt, TpsInstance *inst_h,
+                         TpsUnit *units_h, int *n_units) {
   if (n < 1 || n > c->batch_max_inst || !inst) return fail(c, ITMPC_ERR_ARG, "n=%d outside [1, %d]", n, c->batch_max_inst);
   int64_t total = 0;
   int units = 0;
@@ -472,12 +606,10 @@ itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, floa
     if (q.map_index < 0 || q.map_index >= c->n_maps) return fail(c, ITMPC_ERR_ARG, "instance %d: bad map", i);
     if (!q.x0 || !q.U || !q.U_out) return fail(c, ITMPC_ERR_ARG, "instance %d: NULL pointer", i);
     total += q.K;
-    units += (q.K + kTpsThreads - 1) / kTpsThreads;
+    units += (q.K + nt - 1) / nt;
   }
   if (total > c->batch_max_samples || units > c->batch_max_units)
     return fail(c, ITMPC_ERR_ARG, "batch exceeds the reserved capacity");
-  // the previous call's copies out of the staging buffers must have finished
-  CK(c, cudaEventSynchronize(c->staged), "event sync");
   const itmpc_config &g = c->cfg;
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -485,7 +617,7 @@ itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, floa
   int64_t rec_off = 0, cost_off = 0;
   for (int i = 0; i < n; ++i) {
     const itmpc_instance &q = inst[i];
-    TpsInstance &d = c->inst_h[i];
+    TpsInstance &d = inst_h[i];
     d.K = q.K;
     d.T = q.T;
     const double nimp = ceil((1.0 - (double)g.alpha_explore) * (double)q.K);
@@ -493,7 +625,7 @@ itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, floa
     d.map = q.map_index;
     d.ctr2 = (uint32_t)q.iter;
     d.ctr3 = (uint32_t)((q.iter >> 32) & 0xFFFFu) | (q.instance << 16);
-    d.n_units = (q.K + kTpsThreads - 1) / kTpsThreads;
+    d.n_units = (q.K + nt - 1) / nt;
     d.rec_off = (int)rec_off;
     rec_off += (int64_t)d.n_units * partial_len(q.T);
     d.x0 = q.x0;
@@ -507,11 +639,14 @@ itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, floa
   int u = 0;
   for (int oi = 0; oi < n; ++oi) {
     const int i = order[oi];
-    for (int j = 0; j < c->inst_h[i].n_units; ++j) c->units_h[u++] = TpsUnit{i, j * kTpsThreads, j, 0};
+    for (int j = 0; j < inst_h[i].n_units; ++j) units_h[u++] = TpsUnit{i, j * nt, j, 0};
   }
-  CK(c, cudaMemcpyAsync(c->inst_d, c->inst_h, sizeof(TpsInstance) * n, cudaMemcpyHostToDevice, c->stream), "copy");
-  CK(c, cudaMemcpyAsync(c->units_d, c->units_h, sizeof(TpsUnit) * u, cudaMemcpyHostToDevice, c->stream), "copy");
-  CK(c, cudaEventRecord(c->staged, c->stream), "event");
+  *n_units = u;
+  return ITMPC_OK;
+}
+
+TpsShared batch_shared(const itmpc_ctx *c, const TpsInstance *inst_d, const TpsUnit *units_d, int n, int n_units) {
+  const itmpc_config &g = c->cfg;
   TpsShared sh{};
   sh.key0 = (uint32_t)g.seed;
   sh.key1 = (uint32_t)(g.seed >> 32);
@@ -539,23 +674,60 @@ itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, floa
   sh.inv_res = (float)(1.0 / (double)c->res);
   sh.origin_x = c->origin_x;
   sh.origin_y = c->origin_y;
-  sh.inst = c->inst_d;
-  sh.units = c->units_d;
-  sh.n_units = u;
+  sh.inst = inst_d;
+  sh.units = units_d;
+  sh.n_units = n_units;
   sh.n_inst = n;
   sh.T_max = c->T_max;
   sh.partials = c->batch_partials;
   sh.unit_counter = c->unit_counter;
   sh.status = c->status;
-  sh.states_out = states;
-  sh.n_states = states ? n_states : 0;
-  if (tc) {
-    CK(c, tc_launch(sh, c->tc_img[g.precision == ITMPC_FP8 ? 1 : 0], g.precision, g.activation, c->stream),
+  return sh;
+}
+
+// Units of the tensor-core kernels are one 128-row MMA tile; FP32 units follow the tuned tile.
+int batch_nt(const itmpc_ctx *c) { return c->cfg.precision != ITMPC_FP32 ? kTpsThreads : c->tps_tile.nt; }
+
+itmpc_status launch_batch(itmpc_ctx *c, const TpsShared &sh, TpsTile tile, cudaStream_t s) {
+  const itmpc_config &g = c->cfg;
+  if (g.precision != ITMPC_FP32) {
+    CK(c, tc_launch(sh, c->tc_img[g.precision == ITMPC_FP8 ? 1 : 0], g.precision, g.activation, s),
        "tensor-core launch");
   } else {
-    CK(c, tps_launch(sh, c->net_host.data(), c->H, g.activation, c->stream), "batched launch");
+    CK(c, tps_launch(sh, c->net_host.data(), c->H, g.activation, tile, s), "batched launch");
   }
   return ITMPC_OK;
+}
+
+itmpc_status batch_ready(itmpc_ctx *c) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (c->cfg.precision == ITMPC_FP32 && c->H != 32) return fail(c, ITMPC_ERR_ARG, "batched FP32 iterations need hidden == 32");
+  if (!c->inst_d) return fail(c, ITMPC_ERR_STATE, "itmpc_reserve_batch has not been called");
+  return ITMPC_OK;
+}
+
+itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
+                            TpsTile tile) {
+  itmpc_status st = batch_ready(c);
+  if (st != ITMPC_OK) return st;
+  const int nt = c->cfg.precision != ITMPC_FP32 ? kTpsThreads : tile.nt;
+  // the previous call's copies out of the staging buffers must have finished
+  CK(c, cudaEventSynchronize(c->staged), "event sync");
+  int u = 0;
+  st = build_batch(c, n, inst, nt, c->inst_h, c->units_h, &u);
+  if (st != ITMPC_OK) return st;
+  CK(c, cudaMemcpyAsync(c->inst_d, c->inst_h, sizeof(TpsInstance) * n, cudaMemcpyHostToDevice, c->stream), "copy");
+  CK(c, cudaMemcpyAsync(c->units_d, c->units_h, sizeof(TpsUnit) * u, cudaMemcpyHostToDevice, c->stream), "copy");
+  CK(c, cudaEventRecord(c->staged, c->stream), "event");
+  TpsShared sh = batch_shared(c, c->inst_d, c->units_d, n, u);
+  sh.states_out = states;
+  sh.n_states = states ? n_states : 0;
+  return launch_batch(c, sh, tile, c->stream);
+}
+
+itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states) {
+  return run_batch_tile(c, n, inst, states, n_states, c->tps_tile);
 }
 
 }  // namespace

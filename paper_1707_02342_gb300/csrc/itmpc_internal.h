@@ -86,7 +86,15 @@ cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t
 cudaError_t launch_finalize_weights(const IterParams &p, cudaStream_t s);
 
 // ---- thread-per-sample path (many samples: large K, or many instances) ----
-constexpr int kTpsThreads = 128;  // samples per work unit (one thread each)
+constexpr int kTpsThreads = 128;  // samples per work unit of the tensor-core kernels (one MMA tile)
+constexpr int kTpsMinUnit = 64;   // smallest FP32 unit: batch buffers are sized for it
+
+// Launch shape of the thread-per-sample FP32 kernel (chosen by itmpc_autotune_batch):
+// nt samples (= threads) per unit and CTA; at most ctas_per_sm resident CTAs (0: occupancy limit).
+struct TpsTile {
+  int nt;
+  int ctas_per_sm;
+};
 
 // One MPC instance, as the device sees it.
 struct TpsInstance {
@@ -98,7 +106,7 @@ struct TpsInstance {
   float *U_out, *weights, *costs, *stats;
 };
 
-// A work unit: kTpsThreads consecutive samples of one instance.
+// A work unit: nt consecutive samples of one instance (128 for the tensor-core kernels).
 struct TpsUnit {
   int inst, k0, idx, pad;  // idx: the unit's index within its instance
 };
@@ -133,7 +141,11 @@ struct TpsNet {
 };
 
 // Launch the rollout (persistent over work units) and the per-instance merge.
-cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, cudaStream_t s);
+cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, TpsTile tile,
+                       cudaStream_t s);
+// Advance every instance's Philox iteration index (counter words 2-3, 48 bits) by one:
+// the last node of a captured closed-loop graph, so replay r draws iteration iter + r.
+cudaError_t tps_launch_advance(TpsInstance *inst, int n, cudaStream_t s);
 // The per-instance merge alone (after any kernel that wrote the units' records);
 // also resets the unit counter.
 cudaError_t tps_merge(const TpsShared &sh, cudaStream_t s);

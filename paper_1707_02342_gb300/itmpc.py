@@ -66,6 +66,10 @@ SIGNATURES = {
     "itmpc_merge_partials": (C.c_int, [_i32, _i32, _vp, _vp, _f, _vp]),
     "itmpc_iterate_noalloc": (C.c_int, [C.POINTER(Config), _vp, _vp, _vp, _i32, _i32, _f, _f, _f, _vp, _vp, _u64,
                                         _vp, _vp, _vp]),
+    "itmpc_autotune_batch": (C.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
+    "itmpc_batch_graph_create": (C.c_int, [_vp, _i32, _vp]),
+    "itmpc_batch_graph_launch": (C.c_int, [_vp]),
+    "itmpc_batch_graph_destroy": (C.c_int, [_vp]),
     "itmpc_adjoint_ckpt_floats": (C.c_int64, [_i32, _i32, _i32]),
     "itmpc_reserve_adjoint": (C.c_int, [_vp]),
     "itmpc_iterate_fwd": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _vp, _vp, _vp, _vp, _vp]),
@@ -222,16 +226,37 @@ class Controller:
     def reserve_batch(self, max_instances: int, max_total_samples: int):
         self._check(self._L.itmpc_reserve_batch(self._h, max_instances, max_total_samples))
 
-    def iterate_batch(self, instances):
-        """instances: list of dicts with K, T, map_index, instance, iter, x0, U, U_out and optional
-        weights, costs, stats (CUDA tensors).  Queued on the context's stream."""
+    @staticmethod
+    def _instances(instances):
         arr = (Instance * len(instances))()
         for a, d in zip(arr, instances):
             a.K, a.T, a.map_index = d["K"], d["T"], d.get("map_index", 0)
             a.instance, a.iter = d.get("instance", 0), d.get("iter", 0)
             a.x0, a.U, a.U_out = _dptr(d["x0"]), _dptr(d["U"]), _dptr(d["U_out"])
             a.weights, a.costs, a.stats = _dptr(d.get("weights")), _dptr(d.get("costs")), _dptr(d.get("stats"))
-        self._check(self._L.itmpc_iterate_batch(self._h, len(instances), arr))
+        return arr
+
+    def iterate_batch(self, instances):
+        """instances: list of dicts with K, T, map_index, instance, iter, x0, U, U_out and optional
+        weights, costs, stats (CUDA tensors).  Queued on the context's stream."""
+        self._check(self._L.itmpc_iterate_batch(self._h, len(instances), self._instances(instances)))
+
+    def autotune_batch(self, instances, reps: int = 3):
+        """Time the candidate launch shapes on this batch; returns (samples per unit, CTAs per SM)."""
+        nt, ctas = C.c_int32(), C.c_int32()
+        self._check(self._L.itmpc_autotune_batch(self._h, len(instances), self._instances(instances), reps,
+                                                 C.byref(nt), C.byref(ctas)))
+        return nt.value, ctas.value
+
+    def batch_graph_create(self, instances):
+        """Capture the batch as a closed-loop CUDA graph (replay r draws iteration iter + r)."""
+        self._check(self._L.itmpc_batch_graph_create(self._h, len(instances), self._instances(instances)))
+
+    def batch_graph_launch(self):
+        self._check(self._L.itmpc_batch_graph_launch(self._h))
+
+    def batch_graph_destroy(self):
+        self._check(self._L.itmpc_batch_graph_destroy(self._h))
 
     def iterate(self, x0, U, it: int, U_out, weights=None, costs=None):
         """Queue one iteration on the context's stream (device tensors)."""
