@@ -192,16 +192,19 @@ typedef struct {
 
 /* Reserve device memory for batched iterations of up to max_instances
  * instances with at most max_total_samples samples in all (no allocation
- * happens in itmpc_iterate_batch).  Requires hidden == 32. */
+ * happens in itmpc_iterate_batch).  Requires hidden == 32, 64 or 128 (BF16 /
+ * FP8: 128). */
 itmpc_status itmpc_reserve_batch(itmpc_ctx *ctx, int32_t max_instances, int64_t max_total_samples);
 
 /* One control iteration of n independent instances in one launch (Alg. 1 and
- * Alg. 2 per instance; the thread-per-sample kernels of iterate_tps.cu): a
- * persistent kernel pulls (instance, 128-sample tile) work units, longest
- * horizon first (work-unit size: itmpc_autotune_batch), then one CTA per
- * instance merges its partial sums.  inst is
- * a host array of n descriptors.  Asynchronous; an instance whose costs are
- * all non-finite gets U_out = U and records ITMPC_ERR_NONFINITE. */
+ * Alg. 2 per instance): a persistent kernel pulls (instance, sample tile) work
+ * units, longest horizon first, then one CTA per instance merges its partial
+ * sums.  The rollout kernel follows the network: one thread per sample with
+ * the weights in the constant bank (FP32, hidden 32; unit size from
+ * itmpc_autotune_batch), a register-tiled GEMM per step over 16 / 32 samples
+ * (FP32, hidden 64 / 128), or tcgen05 MMAs over 128 samples (BF16 / FP8).
+ * inst is a host array of n descriptors.  Asynchronous; an instance whose
+ * costs are all non-finite gets U_out = U and records ITMPC_ERR_NONFINITE. */
 itmpc_status itmpc_iterate_batch(itmpc_ctx *ctx, int32_t n, const itmpc_instance *inst);
 
 /* Choose the launch shape of batched FP32 iterations for this batch by timing
@@ -210,8 +213,9 @@ itmpc_status itmpc_iterate_batch(itmpc_ctx *ctx, int32_t n, const itmpc_instance
  * timed runs per candidate (0: 3).  The runs write to scratch outputs (the
  * caller's U_out, weights, costs and stats are left untouched; x0 and U are
  * only read); later itmpc_iterate_batch calls and graphs use the winner.
- * The tensor-core (BF16 / FP8) kernels have a fixed shape (a unit is one
- * 128-row MMA tile, one CTA per SM), reported without timing.  Synchronous.
+ * The tensor-core (BF16 / FP8) kernels and the FP32 kernels of the wider
+ * networks have fixed shapes (a unit is one 128-row MMA tile, or 16 / 32
+ * samples for H = 64 / 128), reported without timing.  Synchronous.
  * nt_out, ctas_out (may be NULL): the chosen shape (ctas 0 = occupancy limit). */
 itmpc_status itmpc_autotune_batch(itmpc_ctx *ctx, int32_t n, const itmpc_instance *inst, int32_t reps,
                                   int32_t *nt_out, int32_t *ctas_out);

@@ -181,10 +181,18 @@ itmpc_status ready(itmpc_ctx *c) {
   return ITMPC_OK;
 }
 
-constexpr int kTpsMinK = 4096;  // from here on one thread per sample beats a warp per sample
+constexpr int kTpsMinK = 4096;   // from here on one thread per sample beats a warp per sample (H = 32)
+constexpr int kWideMinK = 2048;  // from here on the tiled GEMM kernel beats a warp per sample (H = 64, 128)
 
-// Batched contexts: the thread-per-sample FP32 kernels (H = 32) and the tensor-core kernels (H = 128).
-bool batch_capable(int H) { return H == 32 || H == kTcHidden; }
+// Batched contexts: the thread-per-sample FP32 kernels (H = 32), the tiled FP32 kernels
+// (H = 64, 128) and the tensor-core kernels (H = 128).
+bool batch_capable(int H) { return H == 32 || H == 64 || H == kTcHidden; }
+
+// Smallest work unit any kernel of this width may use: batch buffers are sized for it.
+int min_unit(int H) { return H == 32 ? kTpsMinUnit : wide_unit_samples(H); }
+
+// Single iterations that run as a batch of one instance.
+bool single_as_batch(const itmpc_ctx *c, bool debug_out);
 
 }  // namespace
 
@@ -192,9 +200,10 @@ extern "C" itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances,
 
 namespace {
 
-itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states);
+itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
+                       int states_every = 1);
 itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
-                            TpsTile tile);
+                            TpsTile tile, int states_every = 1);
 itmpc_status build_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, int nt, TpsInstance *inst_h,
                          TpsUnit *units_h, int *n_units);
 TpsShared batch_shared(const itmpc_ctx *c, const TpsInstance *inst_d, const TpsUnit *units_d, int n, int n_units);
@@ -206,7 +215,7 @@ itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64
                            float *weights, float *costs, float *states, int n_states, float *eps_out,
                            int states_every = 1) {
   const bool tc = c->cfg.precision != ITMPC_FP32;
-  if (tc || (!states && !eps_out && c->H == 32 && c->cfg.K >= kTpsMinK && c->inst_d)) {
+  if (tc || (!eps_out && single_as_batch(c, states != nullptr))) {
     // the tensor-core kernels, or many samples: the thread-per-sample kernels, as a batch of one instance
     if (eps_out) return fail(c, ITMPC_ERR_ARG, "noise output is not available for this precision");
     itmpc_instance q{};
@@ -221,7 +230,7 @@ itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64
     q.weights = weights;
     q.costs = costs ? costs : c->costs;
     q.stats = c->stats;
-    return run_batch(c, 1, &q, states, n_states);
+    return run_batch(c, 1, &q, states, n_states, states_every);
   }
   IterParams p = make_params(c);
   set_iter(p, iter, c->cfg.instance);
@@ -319,7 +328,7 @@ itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
       if (e != cudaSuccess) return bail(e, "cudaMalloc");
     }
   }
-  if ((c->H == 32 && c->K_cap >= kTpsMinK) || c->H == kTcHidden) {
+  if ((c->H == 32 && c->K_cap >= kTpsMinK) || (c->H == 64 && c->K_cap >= kWideMinK) || c->H == kTcHidden) {
     itmpc_status bs = itmpc_reserve_batch(c, 1, c->K_cap);
     if (bs != ITMPC_OK) {
       free_ctx(c);
@@ -432,7 +441,7 @@ itmpc_status itmpc_set_costmap(itmpc_ctx *c, const float *map, int32_t width, in
 
 itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances, int64_t max_total_samples) {
   if (!c) return ITMPC_ERR_ARG;
-  if (!batch_capable(c->H)) return fail(c, ITMPC_ERR_ARG, "batched iterations need hidden == 32 or %d", kTcHidden);
+  if (!batch_capable(c->H)) return fail(c, ITMPC_ERR_ARG, "batched iterations need hidden == 32, 64 or 128");
   if (max_instances < 1 || max_total_samples < 1 || max_total_samples > ((int64_t)1 << 31))
     return fail(c, ITMPC_ERR_ARG, "bad batch capacity");
   CK(c, cudaStreamSynchronize(c->stream), "sync");
@@ -445,7 +454,7 @@ itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances, int64_t ma
   c->units_d = c->units_h = nullptr;
   c->batch_partials = c->batch_costs = c->batch_stats = nullptr;
   c->unit_counter = nullptr;
-  const int64_t max_units = max_total_samples / kTpsMinUnit + max_instances;
+  const int64_t max_units = max_total_samples / min_unit(c->H) + max_instances;
   if (max_units > ((int64_t)1 << 30)) return fail(c, ITMPC_ERR_ARG, "batch too large");
   CK(c, cudaMalloc((void **)&c->inst_d, sizeof(TpsInstance) * max_instances), "batch cudaMalloc");
   CK(c, cudaMalloc((void **)&c->units_d, sizeof(TpsUnit) * max_units), "batch cudaMalloc");
@@ -475,9 +484,10 @@ itmpc_status itmpc_autotune_batch(itmpc_ctx *c, int32_t n, const itmpc_instance 
   if (st != ITMPC_OK) return st;
   if (n < 1 || !inst) return fail(c, ITMPC_ERR_ARG, "empty batch");
   if (reps < 1) reps = 3;
-  if (c->cfg.precision != ITMPC_FP32) {  // one MMA tile per unit, one CTA per SM: nothing to choose
-    if (nt_out) *nt_out = kTpsThreads;
-    if (ctas_out) *ctas_out = 1;
+  if (c->cfg.precision != ITMPC_FP32 || c->H != 32) {
+    // fixed shapes: one 128-row MMA tile per unit (tensor cores), or the wide kernels' GEMM tile
+    if (nt_out) *nt_out = batch_nt(c);
+    if (ctas_out) *ctas_out = 0;
     return ITMPC_OK;
   }
   // run the caller's batch with its outputs redirected to scratch, so nothing the caller owns changes
@@ -686,15 +696,26 @@ TpsShared batch_shared(const itmpc_ctx *c, const TpsInstance *inst_d, const TpsU
 }
 
 // Units of the tensor-core kernels are one 128-row MMA tile; FP32 units follow the tuned tile.
-int batch_nt(const itmpc_ctx *c) { return c->cfg.precision != ITMPC_FP32 ? kTpsThreads : c->tps_tile.nt; }
+int batch_nt(const itmpc_ctx *c) {
+  if (c->cfg.precision != ITMPC_FP32) return kTpsThreads;
+  return c->H == 32 ? c->tps_tile.nt : wide_unit_samples(c->H);
+}
+
+bool single_as_batch(const itmpc_ctx *c, bool debug_out) {
+  if (!c->inst_d) return false;
+  if (c->H == 32) return !debug_out && c->cfg.K >= kTpsMinK;
+  return c->cfg.K >= kWideMinK;  // the wide kernel writes the states (checkpoints) itself
+}
 
 itmpc_status launch_batch(itmpc_ctx *c, const TpsShared &sh, TpsTile tile, cudaStream_t s) {
   const itmpc_config &g = c->cfg;
   if (g.precision != ITMPC_FP32) {
     CK(c, tc_launch(sh, c->tc_img[g.precision == ITMPC_FP8 ? 1 : 0], g.precision, g.activation, s),
        "tensor-core launch");
-  } else {
+  } else if (c->H == 32) {
     CK(c, tps_launch(sh, c->net_host.data(), c->H, g.activation, tile, s), "batched launch");
+  } else {
+    CK(c, wide_launch(sh, c->net, c->H, g.activation, s), "batched wide-network launch");
   }
   return ITMPC_OK;
 }
@@ -702,16 +723,17 @@ itmpc_status launch_batch(itmpc_ctx *c, const TpsShared &sh, TpsTile tile, cudaS
 itmpc_status batch_ready(itmpc_ctx *c) {
   itmpc_status st = ready(c);
   if (st != ITMPC_OK) return st;
-  if (c->cfg.precision == ITMPC_FP32 && c->H != 32) return fail(c, ITMPC_ERR_ARG, "batched FP32 iterations need hidden == 32");
+  if (c->cfg.precision != ITMPC_FP32 && c->H != kTcHidden)
+    return fail(c, ITMPC_ERR_ARG, "BF16 / FP8 iterations need hidden == %d", kTcHidden);
   if (!c->inst_d) return fail(c, ITMPC_ERR_STATE, "itmpc_reserve_batch has not been called");
   return ITMPC_OK;
 }
 
 itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
-                            TpsTile tile) {
+                            TpsTile tile, int states_every) {
   itmpc_status st = batch_ready(c);
   if (st != ITMPC_OK) return st;
-  const int nt = c->cfg.precision != ITMPC_FP32 ? kTpsThreads : tile.nt;
+  const int nt = (c->cfg.precision == ITMPC_FP32 && c->H == 32) ? tile.nt : batch_nt(c);
   // the previous call's copies out of the staging buffers must have finished
   CK(c, cudaEventSynchronize(c->staged), "event sync");
   int u = 0;
@@ -723,11 +745,13 @@ itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst,
   TpsShared sh = batch_shared(c, c->inst_d, c->units_d, n, u);
   sh.states_out = states;
   sh.n_states = states ? n_states : 0;
+  sh.states_every = states_every;
   return launch_batch(c, sh, tile, c->stream);
 }
 
-itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states) {
-  return run_batch_tile(c, n, inst, states, n_states, c->tps_tile);
+itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
+                       int states_every) {
+  return run_batch_tile(c, n, inst, states, n_states, c->tps_tile, states_every);
 }
 
 }  // namespace

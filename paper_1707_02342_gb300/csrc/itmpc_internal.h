@@ -128,9 +128,11 @@ struct TpsShared {
   float *partials;
   unsigned int *unit_counter;
   int *status;
-  // debug: states x_0..x_T of samples 0..n_states-1 of instance 0 (n_states x (T+1) x 7), or null
+  // states of samples 0..n_states-1 of instance 0, or null: x_0..x_T (n_states x (T+1) x 7) for the
+  // debug outputs; the FP32 wide-network kernel writes x_t at t = 0, e, 2e, ... with e = states_every
+  // (n_states x (T/e + 1) x 7: the adjoint form's checkpoints)
   float *states_out;
-  int n_states, pad2;
+  int n_states, states_every;
 };
 
 // Network values in kernel parameter space (constant bank): FMA operands read
@@ -160,6 +162,12 @@ cudaError_t tc_pack(const float *net, unsigned char *img_bf16, unsigned char *im
 cudaError_t tc_launch(const TpsShared &sh, const unsigned char *image, int precision, int activation,
                       cudaStream_t s);
 size_t tps_merge_smem_bytes(int max_units_per_instance, int T_max);
+
+// ---- FP32 rollout of the wide networks (H = 64, 128) as a per-step register-tiled GEMM ----
+int wide_unit_samples(int H);  // samples per work unit (16 for H = 64, 32 for H = 128)
+size_t wide_smem_bytes(int H, int T_max);
+// Rollout + records, then tps_merge.  net: the packed FP32 network on the device.
+cudaError_t wide_launch(const TpsShared &sh, const float *net, int H, int activation, cudaStream_t s);
 cudaError_t launch_noise(const IterParams &p, float *eps, cudaStream_t s);
 
 // ---- adjoint form (iterate_adj.cu): reverse sweep over checkpointed FP32 rollouts ----

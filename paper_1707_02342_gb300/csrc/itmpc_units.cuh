@@ -35,6 +35,40 @@ __device__ __forceinline__ float tps_costmap(const TpsShared &sh, const float *m
   return (1.0f - a) * (1.0f - b) * m00 + a * (1.0f - b) * m01 + (1.0f - a) * b * m10 + a * b * m11;
 }
 
+// The bilinear lookup split in two, so the texel loads can be issued a step before
+// they are used: fractional weights (a, b) and the four texels around (p_x, p_y).
+__device__ __forceinline__ void tps_costmap_fetch(const TpsShared &sh, const float *map, float px, float py,
+                                                  float &a, float &b, float &m00, float &m01, float &m10,
+                                                  float &m11) {
+  const float fx = (px - sh.origin_x) * sh.inv_res - 0.5f;
+  const float fy = (py - sh.origin_y) * sh.inv_res - 0.5f;
+  const float jf = floorf(fx), if_ = floorf(fy);
+  a = fx - jf;
+  b = fy - if_;
+  const float jc = fminf(fmaxf(jf, -1.0f), (float)sh.map_w);
+  const float ic = fminf(fmaxf(if_, -1.0f), (float)sh.map_h);
+  const int jj = (int)jc, ii = (int)ic;
+  const int j0 = min(max(jj, 0), sh.map_w - 1), j1 = min(max(jj + 1, 0), sh.map_w - 1);
+  const int i0 = min(max(ii, 0), sh.map_h - 1), i1 = min(max(ii + 1, 0), sh.map_h - 1);
+  const float *r0 = map + (size_t)i0 * sh.map_w;
+  const float *r1 = map + (size_t)i1 * sh.map_w;
+  m00 = __ldg(r0 + j0);
+  m01 = __ldg(r0 + j1);
+  m10 = __ldg(r1 + j0);
+  m11 = __ldg(r1 + j1);
+}
+
+// State cost at loop index t (Sec. V-C) given the interpolated map value h.
+__device__ __forceinline__ float tps_cost_from_h(const TpsShared &sh, float h, float vx, float vy, int t) {
+  h = h > sh.map_cap ? sh.map_cap : h;  // NaN stays NaN
+  const float zeta = -atan2f(vy, fabsf(vx));
+  const float sp = vx - sh.v_des;
+  float imp = 0.0f;
+  if (h > sh.track_thresh) imp += exp2f((float)t * sh.log2_decay) * sh.crash_cost;
+  if (fabsf(zeta) > sh.slip_thresh) imp += sh.crash_cost;
+  return sh.w_track * h + sh.w_speed * sp * sp + sh.w_stab * zeta * zeta + sh.w_crash * imp;
+}
+
 // State cost at loop index t (Sec. V-C).
 __device__ __forceinline__ float tps_state_cost(const TpsShared &sh, const float *map, float px, float py, float vx,
                                                 float vy, int t) {
