@@ -83,6 +83,8 @@ def lib():
             "oracle_iterate": (C.c_int, [P, d, d, C.c_uint64, d, d, d]),
             "oracle_max_threads": (C.c_int, []),
             "oracle_net_floats": (C.c_int, [C.c_int32]),
+            "oracle_savgol": (C.c_int, [C.c_int32, C.c_int32, d, C.c_int32, C.c_int32, d]),
+            "oracle_control_step": (C.c_int, [P, d, d, C.c_uint64, d, C.c_int32, C.c_int32, d, d, d, d]),
             "oracle_mlp_vjp": (None, [P, d, d, d, d]),
             "oracle_state_cost_grad": (None, [P, d, C.c_int32, d, d]),
             "oracle_dynamics_step_vjp": (None, [P, d, d, d, d, d, d]),
@@ -382,3 +384,32 @@ def expected_cost(P: Problem, x0, U, it: int):
         raise ValueError(f"oracle_iterate: status {rc}")
     fin = w != 0.0
     return float(np.sum(w[fin] * S[fin])), Uo
+
+
+def savgol(x, half: int = 2, deg: int = 2) -> np.ndarray:
+    """Savitzky-Golay smoothing of a 1-D or (n, c) sequence along axis 0 (edge values replicated)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    x2 = x.reshape(x.shape[0], -1)
+    y = np.empty_like(x2)
+    for c in range(x2.shape[1]):
+        col = np.ascontiguousarray(x2[:, c])
+        out = np.empty_like(col)
+        rc = lib().oracle_savgol(col.shape[0], 1, _ptr(col), half, deg, _ptr(out))
+        if rc:
+            raise ValueError("oracle_savgol: bad arguments")
+        y[:, c] = out
+    return y.reshape(x.shape)
+
+
+def control_step(P: Problem, x0, U, it: int, smoothing: int = 1, plant: int = 1, S_use=None) -> dict:
+    """One closed-loop step: iteration, smoothing, applied control, plant step, warm-start shift."""
+    s = P.struct()
+    x0, U = _f64(x0, (7,)), _f64(U, (P.T, 2))
+    S_use = None if S_use is None else _f64(S_use, (P.K,))
+    out = dict(x_next=np.empty(7), U_next=np.empty((P.T, 2)), u_applied=np.empty(2), U_prime=np.empty((P.T, 2)))
+    rc = lib().oracle_control_step(C.byref(s), _ptr(x0), _ptr(U), it, _ptr(S_use) if S_use is not None else None,
+                                   smoothing, plant, _ptr(out["x_next"]), _ptr(out["U_next"]),
+                                   _ptr(out["u_applied"]), _ptr(out["U_prime"]))
+    if rc:
+        raise ValueError(f"oracle_control_step: status {rc}")
+    return out

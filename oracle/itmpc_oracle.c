@@ -627,3 +627,131 @@ int oracle_iterate_vjp(const oracle_problem *P, const double x0[7], const double
   free(work);
   return ORACLE_OK;
 }
+
+/* ========================================================================= */
+/* Closed loop (the end of Alg. 1's outer loop).
+ *
+ * Control smoothing (Sec. III-E, "Control Smoothing"): fit, at every step j,
+ * a polynomial of degree `deg` to the 2 half + 1 values around j by least
+ * squares and keep its value at j -- the Savitzky-Golay filter (Savitzky &
+ * Golay, Anal. Chem. 36, 1964).  The paper does not give the window or the
+ * degree; half = 2 and deg = 2 are taken.  Edge steps replicate the first /
+ * last value of the sequence to fill the window.  The fit is computed here
+ * from its definition (normal equations of the local least-squares problem,
+ * solved by Gaussian elimination) for each window.                           */
+static int solve_small(int n, double *A, double *b) {
+  /* Gaussian elimination with partial pivoting on the n x n row-major A */
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r * n + c]) > fabs(A[p * n + c])) p = r;
+    if (A[p * n + c] == 0.0) return -1;
+    if (p != c) {
+      for (int k = 0; k < n; ++k) {
+        double t = A[c * n + k];
+        A[c * n + k] = A[p * n + k];
+        A[p * n + k] = t;
+      }
+      double t = b[c];
+      b[c] = b[p];
+      b[p] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      double f = A[r * n + c] / A[c * n + c];
+      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    double s = b[c];
+    for (int k = c + 1; k < n; ++k) s -= A[c * n + k] * b[k];
+    b[c] = s / A[c * n + c];
+  }
+  return 0;
+}
+
+/* y[j] = value at j of the least-squares polynomial of degree deg through
+ * x[j - half .. j + half] (indices clamped to [0, n-1]), one channel of a
+ * sequence with stride `stride`. */
+int oracle_savgol(int32_t n, int32_t stride, const double *x, int32_t half, int32_t deg, double *y) {
+  if (n < 1 || half < 0 || deg < 0 || deg > 2 * half || deg > 8) return ORACLE_ERR_ARG;
+  const int m = deg + 1;
+  for (int32_t j = 0; j < n; ++j) {
+    double A[81], b[9];
+    for (int r = 0; r < m; ++r) {
+      b[r] = 0.0;
+      for (int c = 0; c < m; ++c) A[r * m + c] = 0.0;
+    }
+    for (int32_t o = -half; o <= half; ++o) {
+      int32_t i = j + o;
+      i = i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
+      double pw[9];
+      pw[0] = 1.0;
+      for (int r = 1; r < m; ++r) pw[r] = pw[r - 1] * (double)o;  /* basis 1, o, o^2 ... */
+      for (int r = 0; r < m; ++r) {
+        b[r] += pw[r] * x[(size_t)i * stride];
+        for (int c = 0; c < m; ++c) A[r * m + c] += pw[r] * pw[c];
+      }
+    }
+    if (solve_small(m, A, b)) return ORACLE_ERR_ARG;
+    y[(size_t)j * stride] = b[0]; /* the polynomial's value at offset 0 */
+  }
+  return ORACLE_OK;
+}
+
+/* One closed-loop step: the iteration, then (Alg. 1, after ComputeWeights)
+ *   smoothing 0: U_s = U'                         (no filter)
+ *   smoothing 1: U_s = SGF(U')                    (Sec. III-E: filter the weighted mean)
+ *   smoothing 2: U_s = U + SGF(U' - U)            (Alg. 1: U <- U + SGF * sum_k w_k eps_k,
+ *                                                  the same when alpha = 0)
+ *   u_applied   = U_s[0]                          ("SendToActuators")
+ *   x_next      = F(x0, g(u_applied)) if plant    (noise-free model as the plant)
+ *   U_next[t-1] = U_s[t], U_next[T-1] = (0, 0)    (warm start; Initialize = (0, 0)
+ *                                                  in the paper's parameter table)
+ * S_use (optional, K) replaces the costs in the weights (stage-wise checks).  */
+int oracle_control_step(const oracle_problem *P, const double x0[7], const double *U, uint64_t iter,
+                        const double *S_use, int32_t smoothing, int32_t plant, double *x_next, double *U_next,
+                        double u_applied[2], double *U_prime) {
+  int rc = check_problem(P);
+  if (rc) return rc;
+  const int32_t T = P->T;
+  double *w = (double *)malloc(sizeof(double) * (size_t)P->K);
+  double *S = (double *)malloc(sizeof(double) * (size_t)P->K);
+  double *Us = (double *)malloc(sizeof(double) * 2 * (size_t)T);
+  double *D = (double *)malloc(sizeof(double) * 2 * (size_t)T);
+  if (!w || !S || !Us || !D) {
+    free(w); free(S); free(Us); free(D);
+    return ORACLE_ERR_ARG;
+  }
+  int nt = P->n_threads > 0 ? P->n_threads : 1;
+  (void)nt;
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
+  for (int64_t k = 0; k < P->K; ++k) S[k] = oracle_rollout_sample(P, x0, U, iter, k, NULL, NULL, NULL);
+  rc = oracle_weights(P->K, S_use ? S_use : S, P->lambda, w, NULL, NULL);
+  if (rc == ORACLE_OK) {
+    oracle_update(P, iter, w, U, U_prime);
+    if (smoothing == 1) {
+      for (int i = 0; i < 2 && rc == ORACLE_OK; ++i) rc = oracle_savgol(T, 2, U_prime + i, 2, 2, Us + i);
+    } else if (smoothing == 2) {
+      for (int32_t t = 0; t < 2 * T; ++t) D[t] = U_prime[t] - U[t];
+      for (int i = 0; i < 2 && rc == ORACLE_OK; ++i) rc = oracle_savgol(T, 2, D + i, 2, 2, Us + i);
+      for (int32_t t = 0; t < 2 * T; ++t) Us[t] += U[t];
+    } else {
+      memcpy(Us, U_prime, sizeof(double) * 2 * (size_t)T);
+    }
+  }
+  if (rc == ORACLE_OK) {
+    u_applied[0] = Us[0];
+    u_applied[1] = Us[1];
+    if (plant) oracle_plant_step(P, x0, u_applied, x_next);
+    else memcpy(x_next, x0, 7 * sizeof(double));
+    for (int32_t t = 1; t < T; ++t) {
+      U_next[2 * (t - 1)] = Us[2 * t];
+      U_next[2 * (t - 1) + 1] = Us[2 * t + 1];
+    }
+    U_next[2 * (T - 1)] = 0.0;
+    U_next[2 * (T - 1) + 1] = 0.0;
+  }
+  free(w); free(S); free(Us); free(D);
+  return rc;
+}
