@@ -363,6 +363,51 @@ def measure_adjoint(params, flush, cores, steps: int = 20, warmup: int = 3, ever
                              "traffic": profiled_traffic(ADJ_PROFILE, ADJ_SOURCES)}}
 
 
+def measure_closed_loop(tmap, layers, x0, U, params, flush, steps: int = 200, warmup: int = 10):
+    """The closed loop of Alg. 1 at the working size: iteration, Savitzky-Golay smoothing, the first
+    control through the noise-free model (the simulated plant) and the warm-start shift, as one CUDA
+    graph replayed per control step (and as direct itmpc_control_step calls)."""
+    import numpy as np
+    import torch
+
+    from paper_1707_02342_gb300 import itmpc
+
+    ctl = _controller(K_WORK, T_WORK, H_WORK, tmap, layers, params)
+    x = torch.tensor(x0, device="cuda")
+    Ud = torch.tensor(U, device="cuda")
+    ua = torch.empty(2, device="cuda")
+    stream = torch.cuda.current_stream()
+    it = [0]
+
+    def direct():
+        ctl.control_step(x, Ud, it[0], smoothing=itmpc.SMOOTH_SGF, plant=1, u_applied=ua)
+        it[0] += 1
+
+    ms_direct = _timed(direct, steps, warmup, flush)[1]
+    x.copy_(torch.tensor(x0, device="cuda"))
+    Ud.copy_(torch.tensor(U, device="cuda"))
+    ctl.control_graph_create(x, Ud, 0, smoothing=itmpc.SMOOTH_SGF, plant=1, u_applied=ua)
+    for _ in range(warmup):
+        ctl.control_graph_launch()
+    torch.cuda.synchronize()
+    # steps back to back (no flush between them: a closed loop runs them back to back)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        ctl.control_graph_launch()
+    b.record(stream)
+    b.synchronize()
+    ms_graph = a.elapsed_time(b) / steps
+    assert ctl.read_status() == itmpc.OK
+    xs = x.cpu().numpy()
+    ctl.close()
+    return {"workload": f"closed loop of Alg. 1, K={K_WORK} T={T_WORK} H={H_WORK} spline-1024 map: iteration, "
+                        "SGF(U'), plant step, warm start", "ms_per_control_step": ms_graph,
+            "control_updates_per_s": 1e3 / ms_graph, "rollout_steps_per_s": K_WORK * T_WORK / (ms_graph * 1e-3),
+            "mode": f"CUDA graph, {steps} replays back to back", "ms_per_control_step_direct_calls": ms_direct,
+            "gpu_launches_per_step": 3, "final_state_finite": bool(np.all(np.isfinite(xs)))}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     d = json.load(open(path)) if os.path.exists(path) else {}
@@ -540,6 +585,7 @@ def run_ours(args, rank, world, local_rank):
         pr["fp32"]["roofline"] = {"bound": "alu", "achieved": pr["fp32"]["algorithmic_tflops"], "peak": peak_tflops,
                                   "unit": "TFLOP/s", "frac": pr["fp32"]["algorithmic_tflops"] / peak_tflops}
         line["forms"]["precision"] = pr
+        line["forms"]["closed_loop"] = measure_closed_loop(tmap, layers, x0, U, params, flush)
         ad = measure_adjoint(params, flush, cores)
         ad["bwd_roofline"]["peak"] = peak_tflops
         ad["bwd_roofline"]["frac"] = ad["bwd_roofline"]["achieved"] / peak_tflops
@@ -559,7 +605,7 @@ def run_only(args):
 
     torch.cuda.set_device(0)
     nbuild.build()
-    _, layers, _, _, params = workload()
+    tmap, layers, x0, U, params = workload()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     steps, warm = max(1, args.steps), args.warmup
@@ -567,6 +613,8 @@ def run_only(args):
         out = measure_batched(params, layers, steps=steps, warmup=warm)
     elif args.only == "precision":
         out = measure_precision(params, flush, cores, steps=steps, warmup=warm)
+    elif args.only == "closed_loop":
+        out = measure_closed_loop(tmap, layers, x0, U, params, flush, steps=steps, warmup=warm)
     else:
         out = measure_adjoint(params, flush, cores, steps=steps, warmup=warm)
     print(json.dumps({"only": args.only, **out}), flush=True)
@@ -581,7 +629,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / precision / adjoint forms")
-    ap.add_argument("--only", choices=["batched", "precision", "adjoint"], default=None,
+    ap.add_argument("--only", choices=["batched", "precision", "adjoint", "closed_loop"], default=None,
                     help="run one form alone and print its JSON (profiling runs); not a benchmark line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -220,23 +220,64 @@ itmpc_status itmpc_iterate_batch(itmpc_ctx *ctx, int32_t n, const itmpc_instance
 itmpc_status itmpc_autotune_batch(itmpc_ctx *ctx, int32_t n, const itmpc_instance *inst, int32_t reps,
                                   int32_t *nt_out, int32_t *ctas_out);
 
+/* Control smoothing of Sec. III-E ("Control Smoothing") applied by the closed-loop
+ * step: the 5-point quadratic Savitzky-Golay filter (convolution weights
+ * (-3, 12, 17, 12, -3)/35, end values replicated at the edges).  The paper's text
+ * filters the weighted mean U'; its Alg. 1 adds the filtered weighted noise to U
+ * (U + SGF(U' - U)); both readings are offered. */
+typedef enum { ITMPC_SMOOTH_NONE = 0, ITMPC_SMOOTH_SGF = 1, ITMPC_SMOOTH_SGF_DELTA = 2 } itmpc_smoothing;
+
 /* Capture one batched iteration of the n instances into a CUDA graph owned by
- * the context, for closed-loop use: each itmpc_batch_graph_launch replays the
- * rollout and merge launches and then advances every instance's Philox
- * iteration index by one on the device, so replay r (counting from 0 after
- * create) draws the noise of iteration inst[i].iter + r.  With U_out == U each
- * replay starts from the previous U'.  The graph keeps the descriptors, the
- * parameters, the network and the costmaps as they are at create (pointers to
- * x0, U and the outputs are read by every replay); create it again after
- * changing any of them.  A new create replaces the previous graph.
+ * the context: each itmpc_batch_graph_launch replays the rollout and merge
+ * launches and then advances every instance's Philox iteration index by one on
+ * the device, so replay r (counting from 0 after create) draws the noise of
+ * iteration inst[i].iter + r.
+ *   closed_loop 0: the replay is an iteration (U_out == U makes each replay start
+ *                  from the previous U').
+ *   closed_loop 1: after the merge, every instance runs the end of Alg. 1 (as
+ *                  itmpc_control_step): U_s = smoothing(U_out, U); the first control
+ *                  U_s[0] goes to stats[5..6] (when stats is given) and, when plant
+ *                  != 0, through the noise-free model x0 <- F(x0, g(U_s[0])) (x0 is
+ *                  then written: it must be writable device memory); then
+ *                  U <- (U_s[1..T-1], (0, 0)).  U (also written) must not alias U_out.
+ * The graph keeps the descriptors, the parameters, the network and the costmaps
+ * as they are at create (the buffers behind the pointers are read and written by
+ * every replay); create it again after changing any of them.  A new create
+ * replaces the previous graph.
  * Errors: ITMPC_ERR_STATE before itmpc_reserve_batch, ITMPC_ERR_ARG, ITMPC_ERR_CUDA. */
-itmpc_status itmpc_batch_graph_create(itmpc_ctx *ctx, int32_t n, const itmpc_instance *inst);
+itmpc_status itmpc_batch_graph_create(itmpc_ctx *ctx, int32_t n, const itmpc_instance *inst, int32_t closed_loop,
+                                      int32_t smoothing, int32_t plant);
 
 /* Replay the captured graph once on the context's stream (asynchronous). */
 itmpc_status itmpc_batch_graph_launch(itmpc_ctx *ctx);
 
 /* Release the captured graph (waits for the context's stream); no-op without one. */
 itmpc_status itmpc_batch_graph_destroy(itmpc_ctx *ctx);
+
+/* One closed-loop step of Alg. 1 for the context's instance: the iteration from
+ * state x and nominal sequence U (iteration index iter), then
+ *   U_s = U' (smoothing 0), SGF(U') (1) or U + SGF(U' - U) (2),
+ *   u_applied = U_s[0] ("SendToActuators"; device, 2 floats, or NULL),
+ *   x <- F(x, g(U_s[0])) with the context's network, noise-free, when plant != 0
+ *        (a simulated plant; with a real vehicle pass plant = 0 and write the next
+ *        state estimate into x),
+ *   U <- (U_s[1], ..., U_s[T-1], (0, 0))  (warm start; Initialize = (0, 0)).
+ * x (7) and U (T x 2) are device buffers, read and written.  Asynchronous. */
+itmpc_status itmpc_control_step(itmpc_ctx *ctx, float *x, float *U, uint64_t iter, int32_t smoothing, int32_t plant,
+                                float *u_applied);
+
+/* Capture itmpc_control_step (x, U, u_applied as given; iteration index iter0)
+ * into a CUDA graph owned by the context; each itmpc_control_graph_launch replays
+ * it and advances a device counter, so replay r uses iteration iter0 + r.  For
+ * single iterations that run on the fused FP32 kernel (hidden 32 with K < 4096,
+ * hidden 64 / 128 with K < 2048); other configurations return ITMPC_ERR_ARG and
+ * use itmpc_batch_graph_create with closed_loop = 1.  The graph keeps the
+ * parameters, network and costmap as they are at create; a new create replaces
+ * the previous graph (and restarts the counter at 0). */
+itmpc_status itmpc_control_graph_create(itmpc_ctx *ctx, float *x, float *U, uint64_t iter0, int32_t smoothing,
+                                        int32_t plant, float *u_applied);
+itmpc_status itmpc_control_graph_launch(itmpc_ctx *ctx);
+itmpc_status itmpc_control_graph_destroy(itmpc_ctx *ctx);
 
 /* Diagnostics for stage-wise checks.
  * itmpc_noise: eps of iteration iter for every (k, t), device K x T x 2.

@@ -518,12 +518,22 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
       W2T_s[kk * H + j] = __ldg(net + net_off_W2(H) + i);
     }
   }
+  // counter words 2-3 of this iteration (plus the device-side offset of a replayed graph)
+  uint32_t c2 = p.ctr2, c3 = p.ctr3;
+  if (p.iter_add != nullptr) {
+    const unsigned long long it =
+        (((unsigned long long)(c3 & 0xFFFFu) << 32) | c2) + *p.iter_add;
+    c2 = (uint32_t)it;
+    c3 = (c3 & 0xFFFF0000u) | (uint32_t)((it >> 32) & 0xFFFFu);
+  }
   for (int i = tid; i < SCTA * T; i += NT) {
     const int s = i / T, t = i - s * T;
     const int k = k0 + s;
     float2 e = make_float2(0.0f, 0.0f);
     if (k < p.K) {
-      e = noise_at(p, (uint32_t)k, (uint32_t)t);
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)t, c2, c3), p.key0, p.key1);
+      const float2 z = box_muller(w.x, w.y);
+      e = make_float2(p.sigma0 * z.x, p.sigma1 * z.y);
       if (p.eps_out) reinterpret_cast<float2 *>(p.eps_out)[(size_t)k * T + t] = e;
     }
     const bool imp = k < p.n_imp;

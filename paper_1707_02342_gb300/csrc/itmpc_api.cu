@@ -50,6 +50,10 @@ struct itmpc_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   TpsInstance *ginst_d = nullptr;
   TpsUnit *gunits_d = nullptr;
+  LoopItem *gloop_d = nullptr;  // the batched graph's closed-loop items
+  // single-instance closed-loop graph (itmpc_control_graph_create) and its iteration counter
+  cudaGraphExec_t loop_exec = nullptr;
+  unsigned long long *loop_ctr = nullptr;
   std::string err;
 };
 
@@ -270,6 +274,9 @@ void free_ctx(itmpc_ctx *c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->ginst_d) cudaFree(c->ginst_d);
   if (c->gunits_d) cudaFree(c->gunits_d);
+  if (c->gloop_d) cudaFree(c->gloop_d);
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  if (c->loop_ctr) cudaFree(c->loop_ctr);
   delete c;
 }
 
@@ -553,15 +560,23 @@ itmpc_status itmpc_batch_graph_destroy(itmpc_ctx *c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->ginst_d) cudaFree(c->ginst_d);
   if (c->gunits_d) cudaFree(c->gunits_d);
+  if (c->gloop_d) cudaFree(c->gloop_d);
   c->graph_exec = nullptr;
   c->ginst_d = nullptr;
   c->gunits_d = nullptr;
+  c->gloop_d = nullptr;
   return ITMPC_OK;
 }
 
-itmpc_status itmpc_batch_graph_create(itmpc_ctx *c, int32_t n, const itmpc_instance *inst) {
+itmpc_status itmpc_batch_graph_create(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, int32_t closed_loop,
+                                      int32_t smoothing, int32_t plant) {
   itmpc_status st = batch_ready(c);
   if (st != ITMPC_OK) return st;
+  if (closed_loop && (smoothing < 0 || smoothing > 2))
+    return fail(c, ITMPC_ERR_ARG, "smoothing %d not one of 0, 1, 2", smoothing);
+  if (closed_loop && inst)
+    for (int i = 0; i < n; ++i)
+      if (inst[i].U_out == inst[i].U) return fail(c, ITMPC_ERR_ARG, "closed loop: instance %d has U_out == U", i);
   st = itmpc_batch_graph_destroy(c);
   if (st != ITMPC_OK) return st;
   const int nt = batch_nt(c);
@@ -575,13 +590,32 @@ itmpc_status itmpc_batch_graph_create(itmpc_ctx *c, int32_t n, const itmpc_insta
   CK(c, cudaMemcpy(c->ginst_d, ih.data(), sizeof(TpsInstance) * n, cudaMemcpyHostToDevice), "graph copy");
   CK(c, cudaMemcpy(c->gunits_d, uh.data(), sizeof(TpsUnit) * u, cudaMemcpyHostToDevice), "graph copy");
   const TpsShared sh = batch_shared(c, c->ginst_d, c->gunits_d, n, u);
+  int T_hi = 1;
+  if (closed_loop) {
+    std::vector<LoopItem> li((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      li[i].T = inst[i].T;
+      li[i].U_prime = inst[i].U_out;
+      li[i].U = const_cast<float *>(inst[i].U);
+      li[i].x = plant ? const_cast<float *>(inst[i].x0) : nullptr;
+      li[i].u_applied = inst[i].stats ? inst[i].stats + 5 : nullptr;
+      T_hi = std::max(T_hi, inst[i].T);
+    }
+    CK(c, cudaMalloc((void **)&c->gloop_d, sizeof(LoopItem) * n), "graph cudaMalloc");
+    CK(c, cudaMemcpy(c->gloop_d, li.data(), sizeof(LoopItem) * n, cudaMemcpyHostToDevice), "graph copy");
+  }
+  IterParams lp = make_params(c);
+  lp.T = T_hi;
   cudaStream_t cap = nullptr;
   CK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
     st = launch_batch(c, sh, c->tps_tile, cap);
-    const cudaError_t ea = st == ITMPC_OK ? tps_launch_advance(c->ginst_d, n, cap) : cudaSuccess;
+    cudaError_t ea = cudaSuccess;
+    if (st == ITMPC_OK && closed_loop)
+      ea = loop_launch(c->gloop_d, nullptr, n, c->H, c->net, lp, smoothing, plant, nullptr, cap);
+    if (st == ITMPC_OK && ea == cudaSuccess) ea = tps_launch_advance(c->ginst_d, n, cap);
     e = cudaStreamEndCapture(cap, &graph);
     if (e == cudaSuccess) e = ea;
   }
@@ -868,6 +902,75 @@ itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *part
     }
     U_out[o] = (float)((double)U[o] * (eta_imp / eta) + E / eta);
   }
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_control_step(itmpc_ctx *c, float *x, float *U, uint64_t iter, int32_t smoothing, int32_t plant,
+                                float *u_applied) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (!x || !U) return fail(c, ITMPC_ERR_ARG, "x and U must be non-NULL");
+  if (smoothing < 0 || smoothing > 2) return fail(c, ITMPC_ERR_ARG, "smoothing %d not one of 0, 1, 2", smoothing);
+  st = run_iteration(c, x, U, iter, c->Uout_d, nullptr, nullptr, nullptr, 0, nullptr);
+  if (st != ITMPC_OK) return st;
+  const LoopItem it{c->cfg.T, c->Uout_d, U, plant ? x : nullptr, u_applied};
+  CK(c, loop_launch(nullptr, &it, 1, c->H, c->net, make_params(c), smoothing, plant, nullptr, c->stream),
+     "closed-loop launch");
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_control_graph_destroy(itmpc_ctx *c) {
+  if (!c) return ITMPC_ERR_ARG;
+  CK(c, cudaStreamSynchronize(c->stream), "sync");
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  c->loop_exec = nullptr;
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_control_graph_create(itmpc_ctx *c, float *x, float *U, uint64_t iter0, int32_t smoothing,
+                                        int32_t plant, float *u_applied) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (!x || !U) return fail(c, ITMPC_ERR_ARG, "x and U must be non-NULL");
+  if (smoothing < 0 || smoothing > 2) return fail(c, ITMPC_ERR_ARG, "smoothing %d not one of 0, 1, 2", smoothing);
+  if (c->cfg.precision != ITMPC_FP32 || single_as_batch(c, false))
+    return fail(c, ITMPC_ERR_ARG, "this configuration runs as a batch of one: use itmpc_batch_graph_create");
+  st = itmpc_control_graph_destroy(c);
+  if (st != ITMPC_OK) return st;
+  if (!c->loop_ctr) CK(c, cudaMalloc((void **)&c->loop_ctr, sizeof(unsigned long long)), "cudaMalloc");
+  CK(c, cudaMemset(c->loop_ctr, 0, sizeof(unsigned long long)), "memset");
+  IterParams p = make_params(c);
+  set_iter(p, iter0, c->cfg.instance);
+  p.x0 = x;
+  p.U = U;
+  p.U_out = c->Uout_d;
+  p.weights = nullptr;
+  p.weights_inline = c->cfg.K <= 16384;
+  p.iter_add = c->loop_ctr;
+  p.grid_bar = nullptr;  // the ordinary launch (merge tree): no cooperative launch inside the graph
+  const Fp32Tile tile = fp32_pick_tile(p.K, p.T, p.H, c->smem_optin);
+  const LoopItem it{c->cfg.T, c->Uout_d, U, plant ? x : nullptr, u_applied};
+  cudaStream_t cap = nullptr;
+  CK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t ek = fp32_launch_iterate(p, tile, cap);
+    if (ek == cudaSuccess) ek = loop_launch(nullptr, &it, 1, c->H, c->net, p, smoothing, plant, c->loop_ctr, cap);
+    e = cudaStreamEndCapture(cap, &graph);
+    if (e == cudaSuccess) e = ek;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->loop_exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return cuda_fail(c, e, "closed-loop graph capture");
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_control_graph_launch(itmpc_ctx *c) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (!c->loop_exec) return fail(c, ITMPC_ERR_STATE, "itmpc_control_graph_create has not been called");
+  CK(c, cudaGraphLaunch(c->loop_exec, c->stream), "graph launch");
   return ITMPC_OK;
 }
 

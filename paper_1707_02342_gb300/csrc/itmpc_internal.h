@@ -62,6 +62,8 @@ struct IterParams {
   float *states_out;   // n_states x (T / states_every + 1) x 7: x_t at t = 0, every, 2 every, ...
   int n_states;
   int states_every;    // 1: the whole trajectory; N: the adjoint form's checkpoints every N steps
+  // device counter added to the iteration index (a replayed closed-loop graph advances it), or null
+  const unsigned long long *iter_add;
 };
 
 // Launch shape of the FP32 fused kernel: nwarps warps per CTA, spw samples per
@@ -169,6 +171,20 @@ size_t wide_smem_bytes(int H, int T_max);
 // Rollout + records, then tps_merge.  net: the packed FP32 network on the device.
 cudaError_t wide_launch(const TpsShared &sh, const float *net, int H, int activation, cudaStream_t s);
 cudaError_t launch_noise(const IterParams &p, float *eps, cudaStream_t s);
+
+// ---- closed loop (closed_loop.cu): smoothing, applied control, plant step, warm start ----
+struct LoopItem {
+  int T;
+  const float *U_prime;  // T x 2, the iteration's weighted mean U'
+  float *U;              // T x 2 in/out: read as the nominal sequence, written shifted
+  float *x;              // 7 in/out (the plant's state), or null
+  float *u_applied;      // 2, or null
+};
+// One CTA per item: U_s = smoothing(U', U) (0 none, 1 SGF(U'), 2 U + SGF(U' - U)), u_applied = U_s[0],
+// x <- F(x, g(u_applied)) when plant and x != null (the FP32 network of the context), U <- shift(U_s)
+// with U[T-1] = (0, 0); then *counter += 1 when counter != null (one thread, after the items).
+cudaError_t loop_launch(const LoopItem *items_dev, const LoopItem *item_host, int n, int H, const float *net,
+                        const IterParams &p, int smoothing, int plant, unsigned long long *counter, cudaStream_t s);
 
 // ---- adjoint form (iterate_adj.cu): reverse sweep over checkpointed FP32 rollouts ----
 struct AdjParams {

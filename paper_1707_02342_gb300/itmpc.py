@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libitmpc.so")
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_OOM = 0, -1, -2, -3, -4, -5, -6
 FP32, BF16, FP8 = 0, 1, 2
 ACT_TANH, ACT_IDENTITY = 0, 1
+SMOOTH_NONE, SMOOTH_SGF, SMOOTH_SGF_DELTA = 0, 1, 2
 MAX_K, MAX_T, STATS_LEN = 1 << 24, 512, 8
 NOALLOC_MAX_K, NOALLOC_MAX_T, NOALLOC_SCRATCH_BYTES = 8192, 256, 4 << 20
 
@@ -67,7 +68,11 @@ SIGNATURES = {
     "itmpc_iterate_noalloc": (C.c_int, [C.POINTER(Config), _vp, _vp, _vp, _i32, _i32, _f, _f, _f, _vp, _vp, _u64,
                                         _vp, _vp, _vp]),
     "itmpc_autotune_batch": (C.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
-    "itmpc_batch_graph_create": (C.c_int, [_vp, _i32, _vp]),
+    "itmpc_batch_graph_create": (C.c_int, [_vp, _i32, _vp, _i32, _i32, _i32]),
+    "itmpc_control_step": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _i32, _vp]),
+    "itmpc_control_graph_create": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _i32, _vp]),
+    "itmpc_control_graph_launch": (C.c_int, [_vp]),
+    "itmpc_control_graph_destroy": (C.c_int, [_vp]),
     "itmpc_batch_graph_launch": (C.c_int, [_vp]),
     "itmpc_batch_graph_destroy": (C.c_int, [_vp]),
     "itmpc_adjoint_ckpt_floats": (C.c_int64, [_i32, _i32, _i32]),
@@ -248,9 +253,25 @@ class Controller:
                                                  C.byref(nt), C.byref(ctas)))
         return nt.value, ctas.value
 
-    def batch_graph_create(self, instances):
-        """Capture the batch as a closed-loop CUDA graph (replay r draws iteration iter + r)."""
-        self._check(self._L.itmpc_batch_graph_create(self._h, len(instances), self._instances(instances)))
+    def batch_graph_create(self, instances, closed_loop: int = 0, smoothing: int = SMOOTH_SGF, plant: int = 1):
+        """Capture the batch as a CUDA graph (replay r draws iteration iter + r); closed_loop=1 adds the
+        end of Alg. 1 per instance (smoothing, applied control into stats[5:7], plant step, warm start)."""
+        self._check(self._L.itmpc_batch_graph_create(self._h, len(instances), self._instances(instances),
+                                                     closed_loop, smoothing, plant))
+
+    def control_step(self, x, U, it: int, smoothing: int = SMOOTH_SGF, plant: int = 1, u_applied=None):
+        """One closed-loop step of Alg. 1 on device tensors x (7) and U (T, 2), both updated in place."""
+        self._check(self._L.itmpc_control_step(self._h, _dptr(x), _dptr(U), it, smoothing, plant, _dptr(u_applied)))
+
+    def control_graph_create(self, x, U, it0: int, smoothing: int = SMOOTH_SGF, plant: int = 1, u_applied=None):
+        self._check(self._L.itmpc_control_graph_create(self._h, _dptr(x), _dptr(U), it0, smoothing, plant,
+                                                       _dptr(u_applied)))
+
+    def control_graph_launch(self):
+        self._check(self._L.itmpc_control_graph_launch(self._h))
+
+    def control_graph_destroy(self):
+        self._check(self._L.itmpc_control_graph_destroy(self._h))
 
     def batch_graph_launch(self):
         self._check(self._L.itmpc_batch_graph_launch(self._h))
