@@ -84,6 +84,8 @@ def lib():
             "oracle_max_threads": (C.c_int, []),
             "oracle_net_floats": (C.c_int, [C.c_int32]),
             "oracle_savgol": (C.c_int, [C.c_int32, C.c_int32, d, C.c_int32, C.c_int32, d]),
+            "oracle_cem_weights": (C.c_int, [C.c_int64, d, C.c_double, d, d, d]),
+            "oracle_iterate_cem": (C.c_int, [P, d, d, C.c_uint64, C.c_double, d, d, d, d]),
             "oracle_control_step": (C.c_int, [P, d, d, C.c_uint64, d, C.c_int32, C.c_int32, d, d, d, d]),
             "oracle_mlp_vjp": (None, [P, d, d, d, d]),
             "oracle_state_cost_grad": (None, [P, d, C.c_int32, d, d]),
@@ -413,3 +415,24 @@ def control_step(P: Problem, x0, U, it: int, smoothing: int = 1, plant: int = 1,
     if rc:
         raise ValueError(f"oracle_control_step: status {rc}")
     return out
+
+
+def cem_weights(S, delta: float):
+    """(status, w, Z, elite count) of the cross-entropy weights (Alg. 3)."""
+    S = _f64(S)
+    w = np.empty_like(S)
+    Z = np.empty(1)
+    m = np.zeros(1, dtype=np.int64)
+    rc = lib().oracle_cem_weights(S.shape[0], _ptr(S), float(delta), _ptr(w), _ptr(Z), _ptr(m))
+    return rc, w, float(Z[0]), int(m[0])
+
+
+def iterate_cem(P: Problem, x0, U, it: int, delta: float = 0.8, S_use=None):
+    """(status, U', w, S) of one cross-entropy MPC iteration."""
+    s = P.struct()
+    x0, U = _f64(x0, (7,)), _f64(U, (P.T, 2))
+    S_use = None if S_use is None else _f64(S_use, (P.K,))
+    Uo, w, S = np.empty((P.T, 2)), np.empty(P.K), np.empty(P.K)
+    rc = lib().oracle_iterate_cem(C.byref(s), _ptr(x0), _ptr(U), it, float(delta),
+                                  _ptr(S_use) if S_use is not None else None, _ptr(Uo), _ptr(w), _ptr(S))
+    return rc, Uo, w, S

@@ -755,3 +755,64 @@ int oracle_control_step(const oracle_problem *P, const double x0[7], const doubl
   free(w); free(S); free(Us); free(D);
   return rc;
 }
+
+/* ========================================================================= */
+/* Cross-entropy weights (Alg. 3, "Compute Weights (Cross Entropy)"), the
+ * paper's comparison controller on the same rollouts:
+ *   zeta = round(K (1 - delta)),  Z = the zeta-th smallest cost,
+ *   w_k  = 1/|E| for k in the elite set E = {k : S_k <= Z}, else 0.
+ * Readings: the printed indicator I{S_k < Z} would keep zeta - 1 samples and
+ * weights summing to (zeta - 1)/zeta; the elite set of the method's own
+ * definition ({C <= gamma}, Sec. VI-A, step 3) is taken, normalised by its size
+ * (= zeta without ties) so that the weights sum to one.  round() is
+ * floor(x + 1/2); zeta is clamped to [1, number of finite costs]; non-finite
+ * costs are never elite.  The ranks come from a plain insertion sort of the
+ * finite costs.                                                              */
+int oracle_cem_weights(int64_t K, const double *S, double delta, double *w, double *Z_out, int64_t *n_elite) {
+  if (K <= 0 || !(delta >= 0.0 && delta <= 1.0)) return ORACLE_ERR_ARG;
+  double *f = (double *)malloc(sizeof(double) * (size_t)K);
+  if (!f) return ORACLE_ERR_ARG;
+  int64_t n = 0;
+  for (int64_t k = 0; k < K; ++k) {
+    if (!isfinite(S[k])) continue;
+    int64_t i = n++;
+    while (i > 0 && f[i - 1] > S[k]) {
+      f[i] = f[i - 1];
+      --i;
+    }
+    f[i] = S[k];
+  }
+  if (n == 0) {
+    free(f);
+    for (int64_t k = 0; k < K; ++k) w[k] = 0.0;
+    return ORACLE_ERR_NONFINITE;
+  }
+  int64_t zeta = (int64_t)floor((double)K * (1.0 - delta) + 0.5);
+  if (zeta < 1) zeta = 1;
+  if (zeta > n) zeta = n;
+  const double Z = f[zeta - 1];
+  free(f);
+  int64_t m = 0;
+  for (int64_t k = 0; k < K; ++k) m += (isfinite(S[k]) && S[k] <= Z) ? 1 : 0;
+  for (int64_t k = 0; k < K; ++k) w[k] = (isfinite(S[k]) && S[k] <= Z) ? 1.0 / (double)m : 0.0;
+  if (Z_out) *Z_out = Z;
+  if (n_elite) *n_elite = m;
+  return ORACLE_OK;
+}
+
+/* One cross-entropy MPC iteration: the rollouts of Alg. 1, the weights of
+ * Alg. 3 and the same control law (U' = sum_k w_k v_k, the un-weighted mean of
+ * the elite controls).  S_use replaces the costs in the weights (stage-wise). */
+int oracle_iterate_cem(const oracle_problem *P, const double x0[7], const double *U, uint64_t iter, double delta,
+                       const double *S_use, double *U_out, double *w, double *S) {
+  int rc = check_problem(P);
+  if (rc) return rc;
+  int nt = P->n_threads > 0 ? P->n_threads : 1;
+  (void)nt;
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
+  for (int64_t k = 0; k < P->K; ++k) S[k] = oracle_rollout_sample(P, x0, U, iter, k, NULL, NULL, NULL);
+  rc = oracle_cem_weights(P->K, S_use ? S_use : S, delta, w, NULL, NULL);
+  if (rc) return rc;
+  oracle_update(P, iter, w, U, U_out);
+  return ORACLE_OK;
+}
