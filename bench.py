@@ -405,7 +405,25 @@ def measure_closed_loop(tmap, layers, x0, U, params, flush, steps: int = 200, wa
                         "SGF(U'), plant step, warm start", "ms_per_control_step": ms_graph,
             "control_updates_per_s": 1e3 / ms_graph, "rollout_steps_per_s": K_WORK * T_WORK / (ms_graph * 1e-3),
             "mode": f"CUDA graph, {steps} replays back to back", "ms_per_control_step_direct_calls": ms_direct,
-            "gpu_launches_per_step": 3, "final_state_finite": bool(np.all(np.isfinite(xs)))}
+            "gpu_launches_per_step": 2, "final_state_finite": bool(np.all(np.isfinite(xs)))}
+
+
+def measure_cem(tmap, layers, x0, U, params, flush, steps: int = 200, warmup: int = 10, delta: float = 0.8):
+    """Cross-entropy MPC (Alg. 3 weights, delta = 0.8 as in the paper's experiments) on the working
+    workload, next to the information-theoretic iteration on the same rollouts."""
+    import torch
+
+    ctl = _controller(K_WORK, T_WORK, H_WORK, tmap, layers, params)
+    x = torch.tensor(x0, device="cuda")
+    Ud = torch.tensor(U, device="cuda")
+    Uo, w, S = torch.empty_like(Ud), torch.empty(K_WORK, device="cuda"), torch.empty(K_WORK, device="cuda")
+    ms_cem = _timed(lambda: ctl.iterate_cem(x, Ud, 3, delta, Uo, w, S), steps, warmup, flush)[1]
+    ms_it = _timed(lambda: ctl.iterate(x, Ud, 3, Uo, w, S), steps, warmup, flush)[1]
+    assert ctl.read_status() == 0
+    ctl.close()
+    return {"workload": f"cross-entropy MPC iteration K={K_WORK} T={T_WORK} H={H_WORK} spline-1024 map, "
+                        f"delta={delta}", "ms_per_step": ms_cem, "ms_per_step_it_mpc": ms_it,
+            "value": K_WORK * T_WORK / (ms_cem * 1e-3), "unit": UNIT, "gpu_launches_per_step": 3}
 
 
 def peaks():
@@ -586,6 +604,7 @@ def run_ours(args, rank, world, local_rank):
                                   "unit": "TFLOP/s", "frac": pr["fp32"]["algorithmic_tflops"] / peak_tflops}
         line["forms"]["precision"] = pr
         line["forms"]["closed_loop"] = measure_closed_loop(tmap, layers, x0, U, params, flush)
+        line["forms"]["cem"] = measure_cem(tmap, layers, x0, U, params, flush)
         ad = measure_adjoint(params, flush, cores)
         ad["bwd_roofline"]["peak"] = peak_tflops
         ad["bwd_roofline"]["frac"] = ad["bwd_roofline"]["achieved"] / peak_tflops
@@ -613,6 +632,8 @@ def run_only(args):
         out = measure_batched(params, layers, steps=steps, warmup=warm)
     elif args.only == "precision":
         out = measure_precision(params, flush, cores, steps=steps, warmup=warm)
+    elif args.only == "cem":
+        out = measure_cem(tmap, layers, x0, U, params, flush, steps=steps, warmup=warm)
     elif args.only == "closed_loop":
         out = measure_closed_loop(tmap, layers, x0, U, params, flush, steps=steps, warmup=warm)
     else:
@@ -629,7 +650,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / precision / adjoint forms")
-    ap.add_argument("--only", choices=["batched", "precision", "adjoint", "closed_loop"], default=None,
+    ap.add_argument("--only", choices=["batched", "precision", "adjoint", "closed_loop", "cem"], default=None,
                     help="run one form alone and print its JSON (profiling runs); not a benchmark line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

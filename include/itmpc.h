@@ -254,6 +254,19 @@ itmpc_status itmpc_batch_graph_launch(itmpc_ctx *ctx);
 /* Release the captured graph (waits for the context's stream); no-op without one. */
 itmpc_status itmpc_batch_graph_destroy(itmpc_ctx *ctx);
 
+/* One iteration of the paper's comparison controller, cross-entropy MPC: the
+ * same rollouts and costs, the weights of Alg. 3 -- zeta = round(K (1 - delta)),
+ * Z = the zeta-th smallest finite cost, w_k = 1/|E| on the elite set
+ * E = {k : S_k <= Z} (|E| = zeta without ties; the paper prints S_k < Z, which
+ * would leave weights summing to (zeta - 1)/zeta) -- and the same control law,
+ * U'_t = sum_k w_k v_{k,t}: the mean of the elite controls.  delta in [0, 1]
+ * (0.8 in the paper's experiments); x0, U, U_out (may alias U), weights (K or
+ * NULL), costs (K or NULL) as itmpc_iterate.  Every cost non-finite: U_out = U,
+ * weights 0, device status ITMPC_ERR_NONFINITE.  itmpc_get_stats reports the
+ * information-theoretic diagnostics of the same rollouts.  Asynchronous. */
+itmpc_status itmpc_iterate_cem(itmpc_ctx *ctx, const float *x0, const float *U, uint64_t iter, float delta,
+                               float *U_out, float *weights, float *costs);
+
 /* One closed-loop step of Alg. 1 for the context's instance: the iteration from
  * state x and nominal sequence U (iteration index iter), then
  *   U_s = U' (smoothing 0), SGF(U') (1) or U + SGF(U' - U) (2),

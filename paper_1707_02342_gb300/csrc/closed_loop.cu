@@ -32,7 +32,8 @@ __device__ __forceinline__ float sgf5(const float *x, int n, int j) {
 template <int ACT>
 __global__ void __launch_bounds__(kLoopThreads) loop_kernel(const LoopItem *items, const LoopItem one, int H,
                                                             const float *__restrict__ net, const IterParams p,
-                                                            int smoothing, int plant) {
+                                                            int smoothing, int plant,
+                                                            unsigned long long *counter) {
   extern __shared__ __align__(16) float sm[];
   const LoopItem it = items ? items[blockIdx.x] : one;
   const int T = it.T, tid = threadIdx.x;
@@ -100,9 +101,9 @@ __global__ void __launch_bounds__(kLoopThreads) loop_kernel(const LoopItem *item
       }
     }
   }
+  // the next replay of a captured loop draws the next iteration's noise
+  if (counter && blockIdx.x == 0 && tid == 0) *counter += 1ull;
 }
-
-__global__ void counter_kernel(unsigned long long *counter) { *counter += 1ull; }
 
 }  // namespace
 
@@ -122,15 +123,10 @@ cudaError_t loop_launch(const LoopItem *items_dev, const LoopItem *item_host, in
   }
   const LoopItem one = item_host ? *item_host : LoopItem{};
   if (p.activation == 1)
-    loop_kernel<1><<<n, kLoopThreads, smem, s>>>(items_dev, one, H, net, p, smoothing, plant);
+    loop_kernel<1><<<n, kLoopThreads, smem, s>>>(items_dev, one, H, net, p, smoothing, plant, counter);
   else
-    loop_kernel<0><<<n, kLoopThreads, smem, s>>>(items_dev, one, H, net, p, smoothing, plant);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (counter) {
-    counter_kernel<<<1, 1, 0, s>>>(counter);
-    e = cudaGetLastError();
-  }
-  return e;
+    loop_kernel<0><<<n, kLoopThreads, smem, s>>>(items_dev, one, H, net, p, smoothing, plant, counter);
+  return cudaGetLastError();
 }
 
 }  // namespace itmpc

@@ -45,6 +45,7 @@ struct itmpc_ctx {
   unsigned char *tc_img[2] = {nullptr, nullptr};
   // adjoint form (itmpc_reserve_adjoint): per-CTA gradient records and 4 scalars
   float *adj_part = nullptr, *adj_scal = nullptr;
+  float *cem_scal = nullptr;  // cross-entropy threshold and elite count of the last CEM iteration
   // batched form: FP32 launch shape (itmpc_autotune_batch) and the captured closed-loop graph
   TpsTile tps_tile{kTpsThreads, 0};
   cudaGraphExec_t graph_exec = nullptr;
@@ -271,6 +272,7 @@ void free_ctx(itmpc_ctx *c) {
     if (b) cudaFree(b);
   if (c->adj_part) cudaFree(c->adj_part);
   if (c->adj_scal) cudaFree(c->adj_scal);
+  if (c->cem_scal) cudaFree(c->cem_scal);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->ginst_d) cudaFree(c->ginst_d);
   if (c->gunits_d) cudaFree(c->gunits_d);
@@ -328,6 +330,8 @@ itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
   e = cudaMalloc((void **)&c->counters, sizeof(unsigned int) * c->n_counters);
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
   e = cudaMalloc((void **)&c->status, sizeof(int));
+  if (e != cudaSuccess) return bail(e, "cudaMalloc");
+  e = cudaMalloc((void **)&c->cem_scal, sizeof(float) * 4);
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
   if (c->H == kTcHidden) {
     for (int i = 0; i < 2; ++i) {
@@ -905,6 +909,24 @@ itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *part
   return ITMPC_OK;
 }
 
+itmpc_status itmpc_iterate_cem(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float delta,
+                               float *U_out, float *weights, float *costs) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (!x0 || !U || !U_out) return fail(c, ITMPC_ERR_ARG, "x0, U and U_out must be non-NULL");
+  if (!(delta >= 0.0f && delta <= 1.0f)) return fail(c, ITMPC_ERR_ARG, "eliteness threshold %g outside [0, 1]", delta);
+  float *S = costs ? costs : c->costs;
+  st = run_iteration(c, x0, U, iter, c->Uout_d, nullptr, S, nullptr, 0, nullptr);
+  if (st != ITMPC_OK) return st;
+  IterParams p = make_params(c);
+  set_iter(p, iter, c->cfg.instance);
+  p.U = U;
+  p.U_out = U_out;
+  const int zeta0 = (int)floor((double)c->cfg.K * (1.0 - (double)delta) + 0.5);
+  CK(c, cem_launch(p, zeta0, S, weights ? weights : c->w_d, c->cem_scal, c->stream), "cross-entropy launch");
+  return ITMPC_OK;
+}
+
 itmpc_status itmpc_control_step(itmpc_ctx *c, float *x, float *U, uint64_t iter, int32_t smoothing, int32_t plant,
                                 float *u_applied) {
   itmpc_status st = ready(c);
@@ -947,21 +969,33 @@ itmpc_status itmpc_control_graph_create(itmpc_ctx *c, float *x, float *U, uint64
   p.weights = nullptr;
   p.weights_inline = c->cfg.K <= 16384;
   p.iter_add = c->loop_ctr;
-  p.grid_bar = nullptr;  // the ordinary launch (merge tree): no cooperative launch inside the graph
   const Fp32Tile tile = fp32_pick_tile(p.K, p.T, p.H, c->smem_optin);
   const LoopItem it{c->cfg.T, c->Uout_d, U, plant ? x : nullptr, u_applied};
   cudaStream_t cap = nullptr;
   CK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
-  if (e == cudaSuccess) {
-    cudaError_t ek = fp32_launch_iterate(p, tile, cap);
-    if (ek == cudaSuccess) ek = loop_launch(nullptr, &it, 1, c->H, c->net, p, smoothing, plant, c->loop_ctr, cap);
-    e = cudaStreamEndCapture(cap, &graph);
-    if (e == cudaSuccess) e = ek;
+  // first with the cooperative launch (grid barrier, distributed merge) when the device
+  // captures it; else the ordinary launch and its merge tree (no grid barrier)
+  cudaError_t e = cudaSuccess;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    IterParams q = p;
+    if (attempt == 1) q.grid_bar = nullptr;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t ek = fp32_launch_iterate(q, tile, cap);
+      if (ek == cudaSuccess) ek = loop_launch(nullptr, &it, 1, c->H, c->net, q, smoothing, plant, c->loop_ctr, cap);
+      e = cudaStreamEndCapture(cap, &graph);
+      if (e == cudaSuccess) e = ek;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->loop_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e == cudaSuccess) break;
+    cudaGetLastError();
+    if (c->loop_exec) {
+      cudaGraphExecDestroy(c->loop_exec);
+      c->loop_exec = nullptr;
+    }
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->loop_exec, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
   cudaStreamDestroy(cap);
   if (e != cudaSuccess) return cuda_fail(c, e, "closed-loop graph capture");
   return ITMPC_OK;

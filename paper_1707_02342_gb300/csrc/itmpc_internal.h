@@ -186,6 +186,11 @@ struct LoopItem {
 cudaError_t loop_launch(const LoopItem *items_dev, const LoopItem *item_host, int n, int H, const float *net,
                         const IterParams &p, int smoothing, int plant, unsigned long long *counter, cudaStream_t s);
 
+// ---- cross-entropy weights (cem.cu): Alg. 3 and the elite-mean update ----
+// w (K) and scal[0] = Z, scal[1] = elite count from the costs S; then U_out = the mean of the
+// elite samples' v (p.U, p.U_out, noise counters of p).  zeta0 = round(K (1 - delta)).
+cudaError_t cem_launch(const IterParams &p, int zeta0, const float *S, float *w, float *scal, cudaStream_t s);
+
 // ---- adjoint form (iterate_adj.cu): reverse sweep over checkpointed FP32 rollouts ----
 struct AdjParams {
   IterParams p;        // dynamics, costs, noise counters, map, network, U

@@ -70,6 +70,7 @@ SIGNATURES = {
     "itmpc_autotune_batch": (C.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
     "itmpc_batch_graph_create": (C.c_int, [_vp, _i32, _vp, _i32, _i32, _i32]),
     "itmpc_control_step": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _i32, _vp]),
+    "itmpc_iterate_cem": (C.c_int, [_vp, _vp, _vp, _u64, _f, _vp, _vp, _vp]),
     "itmpc_control_graph_create": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _i32, _vp]),
     "itmpc_control_graph_launch": (C.c_int, [_vp]),
     "itmpc_control_graph_destroy": (C.c_int, [_vp]),
@@ -258,6 +259,11 @@ class Controller:
         end of Alg. 1 per instance (smoothing, applied control into stats[5:7], plant step, warm start)."""
         self._check(self._L.itmpc_batch_graph_create(self._h, len(instances), self._instances(instances),
                                                      closed_loop, smoothing, plant))
+
+    def iterate_cem(self, x0, U, it: int, delta: float, U_out, weights=None, costs=None):
+        """One cross-entropy MPC iteration (Alg. 3 weights) on device tensors."""
+        self._check(self._L.itmpc_iterate_cem(self._h, _dptr(x0), _dptr(U), it, delta, _dptr(U_out),
+                                              _dptr(weights), _dptr(costs)))
 
     def control_step(self, x, U, it: int, smoothing: int = SMOOTH_SGF, plant: int = 1, u_applied=None):
         """One closed-loop step of Alg. 1 on device tensors x (7) and U (T, 2), both updated in place."""
