@@ -53,6 +53,7 @@ class _Problem(C.Structure):
         ("W3", C.c_void_p), ("b3", C.c_void_p),
         ("map", C.c_void_p), ("map_w", C.c_int32), ("map_h", C.c_int32),
         ("res", C.c_double), ("origin_x", C.c_double), ("origin_y", C.c_double),
+        ("model", C.c_int32), ("theta", C.c_void_p),
     ]
 
 
@@ -85,6 +86,8 @@ def lib():
             "oracle_net_floats": (C.c_int, [C.c_int32]),
             "oracle_savgol": (C.c_int, [C.c_int32, C.c_int32, d, C.c_int32, C.c_int32, d]),
             "oracle_cem_weights": (C.c_int, [C.c_int64, d, C.c_double, d, d, d]),
+            "oracle_basis_phi": (None, [d, d, d]),
+            "oracle_basis_f": (None, [P, d, d]),
             "oracle_iterate_cem": (C.c_int, [P, d, d, C.c_uint64, C.c_double, d, d, d, d]),
             "oracle_control_step": (C.c_int, [P, d, d, C.c_uint64, d, C.c_int32, C.c_int32, d, d, d, d]),
             "oracle_mlp_vjp": (None, [P, d, d, d, d]),
@@ -136,6 +139,8 @@ class Problem:
     instance: int = 0
     activation: int = 0
     n_threads: int = 1
+    model: int = 0        # 0: the network; 1: the basis-function model with coefficients ``theta`` (25, 4)
+    theta: object = None
     _keep: list = field(default_factory=list, repr=False)
 
     def struct(self) -> _Problem:
@@ -144,7 +149,9 @@ class Problem:
         assert W1.shape == (H, 6) and W2.shape == (H, H) and W3.shape == (4, H)
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (W1, b1, W2, b2, W3, b3)]
         m = np.ascontiguousarray(self.costmap, dtype=np.float32)
-        self._keep = arrs + [m]
+        th = np.ascontiguousarray(self.theta if self.theta is not None else np.zeros((25, 4)), dtype=np.float64)
+        assert th.shape == (25, 4)
+        self._keep = arrs + [m, th]
         s = _Problem()
         s.K, s.T, s.H, s.activation = self.K, self.T, H, self.activation
         s.dt, s.lam, s.gamma, s.alpha_explore = self.dt, self.lam, self.gamma, self.alpha_explore
@@ -158,6 +165,7 @@ class Problem:
         s.W1, s.b1, s.W2, s.b2, s.W3, s.b3 = (_ptr(a) for a in arrs)
         s.map, s.map_h, s.map_w = _ptr(m), m.shape[0], m.shape[1]
         s.res, s.origin_x, s.origin_y = self.res, self.origin_x, self.origin_y
+        s.model, s.theta = self.model, _ptr(th)
         return s
 
     def replace(self, **kw) -> "Problem":
@@ -436,3 +444,11 @@ def iterate_cem(P: Problem, x0, U, it: int, delta: float = 0.8, S_use=None):
     rc = lib().oracle_iterate_cem(C.byref(s), _ptr(x0), _ptr(U), it, float(delta),
                                   _ptr(S_use) if S_use is not None else None, _ptr(Uo), _ptr(w), _ptr(S))
     return rc, Uo, w, S
+
+
+def basis_phi(xd, g) -> np.ndarray:
+    """The 25 basis functions of the basis-function model at x_d = (roll, v_x, v_y, r), g = (steer, throttle)."""
+    xd, g = _f64(xd, (4,)), _f64(g, (2,))
+    phi = np.empty(25)
+    lib().oracle_basis_phi(_ptr(xd), _ptr(g), _ptr(phi))
+    return phi

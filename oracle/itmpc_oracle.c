@@ -58,6 +58,8 @@ typedef struct {
   const float *map;
   int32_t map_w, map_h;
   double res, origin_x, origin_y;
+  int32_t model;        /* 0: the network of Sec. V-B; 1: the basis-function model (Sec. V-B, appendix) */
+  const double *theta;  /* model 1: Theta, 25 x 4 row-major (basis i, output o) */
 } oracle_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -154,6 +156,58 @@ void oracle_mlp(const oracle_problem *P, const double z[6], double d[4]) {
   }
 }
 
+/* Sec. V-B, "Basis Function Model", and the paper's appendix: f(x_d, u) =
+ * Theta^T phi(x_d, u) with the 25 basis functions listed there, for
+ * x_d = (roll, v_x, v_y, r) (r the yaw rate) and u = (u_delta, u_F) =
+ * (steer, throttle).  The slip angles are
+ *   alpha_f = arctan(v_y/v_x + 0.45 r/v_x - u_delta) if v_x > 0.1, else -u_delta,
+ *   alpha_r = arctan(v_y/v_x - 0.35 r/v_x)           if v_x > 0.1, else 0,
+ * and "||.||" in the list is read as the absolute value.                    */
+void oracle_basis_phi(const double xd[4], const double g[2], double phi[25]) {
+  const double th = xd[0], vx = xd[1], vy = xd[2], r = xd[3];
+  const double ud = g[0], uF = g[1];
+  const int fast = vx > 0.1;
+  const double af = fast ? atan(vy / vx + 0.45 * r / vx - ud) : -ud;
+  const double ar = fast ? atan(vy / vx - 0.35 * r / vx) : 0.0;
+  const double tf = tan(af), tr = tan(ar), sd = sin(ud);
+  phi[0] = uF;
+  phi[1] = vx / 10.0;
+  phi[2] = sd * tf / 1200.0;
+  phi[3] = sd * tf * fabs(tf) / (1200.0 * 1200.0);
+  phi[4] = sd * tf * tf * tf / (1200.0 * 1200.0 * 1200.0);
+  phi[5] = r * vy / 25.0;
+  phi[6] = r / 10.0;
+  phi[7] = vy / 10.0;
+  phi[8] = sd;
+  phi[9] = fast ? (vy / vx) / 40.0 : 0.0;
+  phi[10] = tf / 1400.0;
+  phi[11] = tf * fabs(tf) / (1400.0 * 1400.0);
+  phi[12] = tf * tf * tf / (1400.0 * 1400.0 * 1400.0);
+  phi[13] = tr / 40.0;
+  phi[14] = tr * fabs(tr) / (40.0 * 40.0);
+  phi[15] = tr * tr * tr / (40.0 * 40.0 * 40.0);
+  phi[16] = r * vx / 50.0;
+  phi[17] = th;
+  phi[18] = th * r;
+  phi[19] = th * vx / 3.0;
+  phi[20] = th * vx * r / 5.0;
+  phi[21] = vx * vx / 100.0;
+  phi[22] = vx * vx * vx / 1000.0;
+  phi[23] = uF * uF;
+  phi[24] = uF * uF * uF;
+}
+
+/* f = Theta^T phi for the input z = (x_d, g(v)). */
+void oracle_basis_f(const oracle_problem *P, const double z[6], double d[4]) {
+  double phi[25];
+  oracle_basis_phi(z, z + 4, phi);
+  for (int o = 0; o < 4; ++o) {
+    double a = 0.0;
+    for (int i = 0; i < 25; ++i) a += P->theta[i * 4 + o] * phi[i];
+    d[o] = a;
+  }
+}
+
 /* g(v): clamp each control into [u_min, u_max] (Sec. III-E, "Handling Control
  * Constraints").  The paper gives no limits; callers pass them. */
 static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -167,7 +221,8 @@ void oracle_dynamics_step(const oracle_problem *P, const double x[7], const doub
   double th = x[2], vx = x[4], vy = x[5], thd = x[6];
   double z[6] = {x[3], x[4], x[5], x[6], gv[0], gv[1]};
   double f[4];
-  oracle_mlp(P, z, f);
+  if (P->model == 1) oracle_basis_f(P, z, f);
+  else oracle_mlp(P, z, f);
   xn[0] = x[0] + (cos(th) * vx - sin(th) * vy) * P->dt;
   xn[1] = x[1] + (sin(th) * vx + cos(th) * vy) * P->dt;
   xn[2] = x[2] + thd * P->dt;
@@ -325,8 +380,13 @@ void oracle_update(const oracle_problem *P, uint64_t iter, const double *w, cons
 }
 
 static int check_problem(const oracle_problem *P) {
-  if (!P || P->K <= 0 || P->T <= 0 || P->H <= 0 || P->H > ORACLE_MAX_H) return ORACLE_ERR_ARG;
-  if (!P->W1 || !P->b1 || !P->W2 || !P->b2 || !P->W3 || !P->b3) return ORACLE_ERR_ARG;
+  if (!P || P->K <= 0 || P->T <= 0) return ORACLE_ERR_ARG;
+  if (P->model == 1) {
+    if (!P->theta) return ORACLE_ERR_ARG;
+  } else {
+    if (P->H <= 0 || P->H > ORACLE_MAX_H) return ORACLE_ERR_ARG;
+    if (!P->W1 || !P->b1 || !P->W2 || !P->b2 || !P->W3 || !P->b3) return ORACLE_ERR_ARG;
+  }
   if (!P->map || P->map_w <= 0 || P->map_h <= 0 || !(P->res > 0.0)) return ORACLE_ERR_ARG;
   if (!(P->lambda > 0.0)) return ORACLE_ERR_ARG;
   return ORACLE_OK;
