@@ -426,6 +426,31 @@ def measure_cem(tmap, layers, x0, U, params, flush, steps: int = 200, warmup: in
             "value": K_WORK * T_WORK / (ms_cem * 1e-3), "unit": UNIT, "gpu_launches_per_step": 3}
 
 
+def measure_basis(tmap, params, flush, steps: int = 50, warmup: int = 5):
+    """The basis-function dynamics model (25 basis functions, synthetic Theta, seed 5) on the working
+    map, T = 100: one iteration at K = 2048 and at K = 65536 (thread-per-sample kernels)."""
+    import torch
+
+    from paper_1707_02342_gb300 import inputs, itmpc
+
+    theta = torch.tensor(inputs.basis_theta(5), device="cuda")
+    x0 = inputs.start_state(tmap.centerline)
+    x0[4] = 4.0
+    x = torch.tensor(x0, device="cuda")
+    out = {"workload": "basis-function dynamics model, T=100, spline-1024 map, synthetic Theta (seed 5)"}
+    for K in (K_WORK, 65536):
+        ctl = itmpc.Controller(K, T_WORK, hidden=H_WORK, dynamics=itmpc.DYN_BASIS, **params)
+        ctl.set_basis(theta)
+        ctl.set_costmap(torch.tensor(tmap.data, device="cuda"), tmap.res, tmap.origin_x, tmap.origin_y)
+        U = torch.tensor(inputs.nominal_controls(T_WORK, seed=9, scale=0.2), device="cuda")
+        Uo, w, S = torch.empty_like(U), torch.empty(K, device="cuda"), torch.empty(K, device="cuda")
+        ms = _timed(lambda: ctl.iterate(x, U, 2, Uo, w, S), steps, warmup, flush)[1]
+        assert ctl.read_status() == 0
+        ctl.close()
+        out[f"K{K}"] = {"ms_per_step": ms, "value": K * T_WORK / (ms * 1e-3), "unit": UNIT}
+    return out
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     d = json.load(open(path)) if os.path.exists(path) else {}
@@ -605,6 +630,7 @@ def run_ours(args, rank, world, local_rank):
         line["forms"]["precision"] = pr
         line["forms"]["closed_loop"] = measure_closed_loop(tmap, layers, x0, U, params, flush)
         line["forms"]["cem"] = measure_cem(tmap, layers, x0, U, params, flush)
+        line["forms"]["basis"] = measure_basis(tmap, params, flush)
         ad = measure_adjoint(params, flush, cores)
         ad["bwd_roofline"]["peak"] = peak_tflops
         ad["bwd_roofline"]["frac"] = ad["bwd_roofline"]["achieved"] / peak_tflops
@@ -632,6 +658,8 @@ def run_only(args):
         out = measure_batched(params, layers, steps=steps, warmup=warm)
     elif args.only == "precision":
         out = measure_precision(params, flush, cores, steps=steps, warmup=warm)
+    elif args.only == "basis":
+        out = measure_basis(tmap, params, flush, steps=steps, warmup=warm)
     elif args.only == "cem":
         out = measure_cem(tmap, layers, x0, U, params, flush, steps=steps, warmup=warm)
     elif args.only == "closed_loop":
@@ -650,7 +678,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / precision / adjoint forms")
-    ap.add_argument("--only", choices=["batched", "precision", "adjoint", "closed_loop", "cem"], default=None,
+    ap.add_argument("--only", choices=["batched", "precision", "adjoint", "closed_loop", "cem", "basis"], default=None,
                     help="run one form alone and print its JSON (profiling runs); not a benchmark line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

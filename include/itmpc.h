@@ -55,6 +55,7 @@ typedef enum {
 
 typedef enum { ITMPC_FP32 = 0, ITMPC_BF16 = 1, ITMPC_FP8 = 2 } itmpc_precision;
 typedef enum { ITMPC_ACT_TANH = 0, ITMPC_ACT_IDENTITY = 1 } itmpc_activation;
+typedef enum { ITMPC_DYN_NETWORK = 0, ITMPC_DYN_BASIS = 1 } itmpc_dynamics;
 
 #define ITMPC_MAX_K (1 << 24)
 #define ITMPC_MAX_T 512
@@ -84,6 +85,9 @@ typedef enum { ITMPC_ACT_TANH = 0, ITMPC_ACT_IDENTITY = 1 } itmpc_activation;
  *                   normaliser and the weighted sums stay FP32
  *   activation      ITMPC_ACT_TANH (the paper's network) or ITMPC_ACT_IDENTITY
  *                   (an affine network, used by closed-form checks)
+ *   dynamics        ITMPC_DYN_NETWORK (the network of Sec. V-B, itmpc_set_dynamics) or
+ *                   ITMPC_DYN_BASIS (the basis-function model, itmpc_set_basis; FP32,
+ *                   thread-per-sample kernels; fixed at create)
  *   stream          cudaStream_t all calls are ordered on (NULL: legacy default) */
 typedef struct {
   int32_t K, T, T_max, hidden;
@@ -96,7 +100,7 @@ typedef struct {
   uint32_t instance;
   int32_t precision;
   int32_t activation;
-  int32_t reserved;
+  int32_t dynamics;
   void *stream;
 } itmpc_config;
 
@@ -125,6 +129,15 @@ itmpc_status itmpc_set_stream(itmpc_ctx *ctx, void *stream);
  * The weights are copied into the context (synchronously for host input). */
 itmpc_status itmpc_set_dynamics(itmpc_ctx *ctx, int32_t n_layers, const int32_t *widths, const float *const *W,
                                 const float *const *b, int32_t on_device);
+
+/* Basis-function dynamics model of Sec. V-B ("Basis Function Model") and the
+ * paper's appendix: f(x_d, u) = Theta^T phi(x_d, u) with the 25 basis functions
+ * listed there (x_d = (roll, v_x, v_y, r), r the yaw rate; u = (steer, throttle);
+ * slip angles alpha_f = arctan(v_y/v_x + 0.45 r/v_x - u_delta),
+ * alpha_r = arctan(v_y/v_x - 0.35 r/v_x) for v_x > 0.1, else -u_delta and 0).
+ *   theta  25 x 4 row-major (basis i, output o); on_device selects device or host input.
+ * Requires cfg.dynamics == ITMPC_DYN_BASIS.  Copied into the context. */
+itmpc_status itmpc_set_basis(itmpc_ctx *ctx, const float *theta, int32_t on_device);
 
 /* Track costmap h of Sec. V-C: height x width FP32 texels, row-major (row i,
  * column j), texel (i, j) centred at (origin_x + (j + 0.5) res,

@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include "itmpc_device.cuh"
+#include "itmpc_units.cuh"
 
 namespace itmpc {
 
@@ -33,7 +34,8 @@ template <int ACT>
 __global__ void __launch_bounds__(kLoopThreads) loop_kernel(const LoopItem *items, const LoopItem one, int H,
                                                             const float *__restrict__ net, const IterParams p,
                                                             int smoothing, int plant,
-                                                            unsigned long long *counter) {
+                                                            unsigned long long *counter,
+                                                            const float *__restrict__ theta) {
   extern __shared__ __align__(16) float sm[];
   const LoopItem it = items ? items[blockIdx.x] : one;
   const int T = it.T, tid = threadIdx.x;
@@ -69,6 +71,21 @@ __global__ void __launch_bounds__(kLoopThreads) loop_kernel(const LoopItem *item
     for (int q = 0; q < 7; ++q) x[q] = it.x[q];
     const float z[6] = {x[3], x[4], x[5], x[6], fminf(fmaxf(u0, p.umin0), p.umax0),
                         fminf(fmaxf(u1, p.umin1), p.umax1)};
+    if (theta) {  // the basis-function model
+      if (tid == 0) {
+        BasisDyn B;
+        for (int i = 0; i < 100; ++i) B.theta[i] = theta[i];
+        float d[4];
+        B.eval(z[0], z[1], z[2], z[3], z[4], z[5], d[0], d[1], d[2], d[3]);
+        float sn, cs;
+        sincosf(x[2], &sn, &cs);
+        it.x[0] = x[0] + (cs * x[4] - sn * x[5]) * p.dt;
+        it.x[1] = x[1] + (sn * x[4] + cs * x[5]) * p.dt;
+        it.x[2] = x[2] + x[6] * p.dt;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) it.x[3 + q] = x[3 + q] + d[q] * p.dt;
+      }
+    } else {
     for (int j = tid; j < H; j += kLoopThreads) {
       float a = __ldg(net + net_off_b1(H) + j);
 #pragma unroll
@@ -100,6 +117,7 @@ __global__ void __launch_bounds__(kLoopThreads) loop_kernel(const LoopItem *item
         for (int q = 0; q < 4; ++q) it.x[3 + q] = x[3 + q] + d[q] * p.dt;
       }
     }
+    }
   }
   // the next replay of a captured loop draws the next iteration's noise
   if (counter && blockIdx.x == 0 && tid == 0) *counter += 1ull;
@@ -108,7 +126,8 @@ __global__ void __launch_bounds__(kLoopThreads) loop_kernel(const LoopItem *item
 }  // namespace
 
 cudaError_t loop_launch(const LoopItem *items_dev, const LoopItem *item_host, int n, int H, const float *net,
-                        const IterParams &p, int smoothing, int plant, unsigned long long *counter, cudaStream_t s) {
+                        const IterParams &p, int smoothing, int plant, unsigned long long *counter, cudaStream_t s,
+                        const float *theta) {
   if (n <= 0) return cudaSuccess;
   int T_max = 0;
   if (items_dev) T_max = p.T;  // callers pass the largest horizon in p.T for a batch
@@ -123,9 +142,9 @@ cudaError_t loop_launch(const LoopItem *items_dev, const LoopItem *item_host, in
   }
   const LoopItem one = item_host ? *item_host : LoopItem{};
   if (p.activation == 1)
-    loop_kernel<1><<<n, kLoopThreads, smem, s>>>(items_dev, one, H, net, p, smoothing, plant, counter);
+    loop_kernel<1><<<n, kLoopThreads, smem, s>>>(items_dev, one, H, net, p, smoothing, plant, counter, theta);
   else
-    loop_kernel<0><<<n, kLoopThreads, smem, s>>>(items_dev, one, H, net, p, smoothing, plant, counter);
+    loop_kernel<0><<<n, kLoopThreads, smem, s>>>(items_dev, one, H, net, p, smoothing, plant, counter, theta);
   return cudaGetLastError();
 }
 

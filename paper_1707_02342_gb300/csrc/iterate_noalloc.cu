@@ -69,6 +69,7 @@ itmpc_status check(const itmpc_config *c) {
     if (!fin(c->cost_w[i])) return ITMPC_ERR_ARG;
   if (!(c->crash_decay > 0.f) || !fin(c->crash_decay)) return ITMPC_ERR_ARG;
   if (c->precision != ITMPC_FP32) return ITMPC_ERR_ARG;
+  if (c->dynamics != ITMPC_DYN_NETWORK) return ITMPC_ERR_ARG;  // the fused kernel runs the network
   if (c->activation != ITMPC_ACT_TANH && c->activation != ITMPC_ACT_IDENTITY) return ITMPC_ERR_ARG;
   return ITMPC_OK;
 }

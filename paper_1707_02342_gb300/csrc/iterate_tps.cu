@@ -32,10 +32,10 @@ namespace itmpc {
 
 namespace {
 
-template <int H>
+template <class DYN>
 struct TpsParams {
   TpsShared sh;
-  TpsNet<H> net;
+  DYN dyn;
 };
 
 // Weight pair (w[i], w[i + 1]) from the parameter space; i even, the array 8-byte aligned.
@@ -89,12 +89,22 @@ __device__ __forceinline__ void tps_network(const TpsNet<H> &N, float x0, float 
   d0 = d[0]; d1 = d[1]; d2 = d[2]; d3 = d[3];
 }
 
-template <int H, int ACT, int NT>
-__global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsParams<H> P) {
+// The network of Sec. V-B, its weights in the kernel parameter space.
+template <int H, int ACT>
+struct MlpDyn {
+  TpsNet<H> net;
+  __device__ __forceinline__ void eval(float x0, float x1, float x2, float x3, float g0, float g1, float &d0,
+                                       float &d1, float &d2, float &d3) const {
+    tps_network<H, ACT>(net, x0, x1, x2, x3, g0, g1, d0, d1, d2, d3);
+  }
+};
+
+template <class DYN, int NT>
+__global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsParams<DYN> P) {
   constexpr int NWARP = NT / 32;
   constexpr int G = NT / 32;  // 32-sample groups of a unit
   const TpsShared &sh = P.sh;
-  const TpsNet<H> &N = P.net;
+  const DYN &dyn = P.dyn;
   __shared__ float U_s[2 * ITMPC_MAX_T_DEV];
   __shared__ float e_s[NT];
   __shared__ float red[NWARP][5];
@@ -121,6 +131,13 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
     if (live) {
       float px = __ldg(I.x0 + 0), py = __ldg(I.x0 + 1), th = __ldg(I.x0 + 2);
       float xd0 = __ldg(I.x0 + 3), xd1 = __ldg(I.x0 + 4), xd2 = __ldg(I.x0 + 5), xd3 = __ldg(I.x0 + 6);
+      // states of instance 0 (x_t at t = 0, every, 2 every, ...), when asked for
+      const bool dbg = sh.states_out != nullptr && un.inst == 0 && k < sh.n_states;
+      const int every = sh.states_every > 0 ? sh.states_every : 1;
+      float *st_o = dbg ? sh.states_out + (size_t)k * (T / every + 1) * 7 : nullptr;
+      if (dbg) {
+        st_o[0] = px; st_o[1] = py; st_o[2] = th; st_o[3] = xd0; st_o[4] = xd1; st_o[5] = xd2; st_o[6] = xd3;
+      }
       for (int t = 0; t < T; ++t) {
         const float2 e = tps_noise(sh, (uint32_t)k, (uint32_t)t, I.ctr2, I.ctr3);
         const float u0 = U_s[2 * t], u1 = U_s[2 * t + 1];
@@ -129,7 +146,7 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
         // f(x_d, g(v)): 6 -> H -> H -> 4 with weights from the constant bank, two
         // products per instruction (packed FP32 pairs, even/odd partial sums)
         float d0, d1, d2, d3;
-        tps_network<H, ACT>(N, xd0, xd1, xd2, xd3, g0, g1, d0, d1, d2, d3);
+        dyn.eval(xd0, xd1, xd2, xd3, g0, g1, d0, d1, d2, d3);
         // explicit Euler from the old state (Sec. V-B)
         float sn, cs;
         sincosf(th, &sn, &cs);
@@ -140,6 +157,10 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
         xd1 = fmaf(d1, sh.dt, xd1);
         xd2 = fmaf(d2, sh.dt, xd2);
         xd3 = fmaf(d3, sh.dt, xd3);
+        if (dbg && (t + 1) % every == 0) {
+          float *o = st_o + (size_t)((t + 1) / every) * 7;
+          o[0] = px; o[1] = py; o[2] = th; o[3] = xd0; o[4] = xd1; o[5] = xd2; o[6] = xd3;
+        }
         // running cost at x(t + 1) (Alg. 1) and the control-cost term (Sec. III-E)
         float c = tps_state_cost(sh, map, px, py, xd1, xd2, t + 1);
         if (sh.gamma != 0.0f) c += sh.gamma * (u0 * v0 * sh.inv_sig2_0 + u1 * v1 * sh.inv_sig2_1);
@@ -232,14 +253,10 @@ __global__ void __launch_bounds__(kMergeThreads) tps_merge_kernel(const __grid_c
                                stage_floats, &mbar, phase);
 }
 
-template <int H, int ACT, int NT>
-cudaError_t tps_launch_h(const TpsShared &sh, const float *net_host, int ctas_per_sm, cudaStream_t s) {
-  TpsParams<H> P;
-  P.sh = sh;
-  // packed layout W1 [H][6], b1 [H], W2 [H][H], b2 [H], W3 [4][H], b3 [4] (== TpsNet field order)
-  static_assert(sizeof(TpsNet<H>) == sizeof(float) * (size_t)net_floats(H), "network layout");
-  memcpy(&P.net, net_host, sizeof(TpsNet<H>));
-  auto kern = tps_rollout_kernel<H, ACT, NT>;
+template <class DYN, int NT>
+cudaError_t tps_launch_d(const TpsParams<DYN> &P, int ctas_per_sm, cudaStream_t s) {
+  const TpsShared &sh = P.sh;
+  auto kern = tps_rollout_kernel<DYN, NT>;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -293,20 +310,38 @@ cudaError_t tps_merge(const TpsShared &sh, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, TpsTile tile,
-                       cudaStream_t s) {
-  if (sh.n_units <= 0 || sh.n_inst <= 0) return cudaSuccess;
-  if (H != 32) return cudaErrorInvalidValue;  // the weights of wider networks do not fit the parameter space
-  cudaError_t e;
-  const int c = tile.ctas_per_sm;
-  switch (tile.nt * 2 + (activation == 1)) {
-    case 128: e = tps_launch_h<32, 0, 64>(sh, net_host, c, s); break;
-    case 129: e = tps_launch_h<32, 1, 64>(sh, net_host, c, s); break;
-    case 256: e = tps_launch_h<32, 0, 128>(sh, net_host, c, s); break;
-    case 257: e = tps_launch_h<32, 1, 128>(sh, net_host, c, s); break;
-    case 512: e = tps_launch_h<32, 0, 256>(sh, net_host, c, s); break;
-    case 513: e = tps_launch_h<32, 1, 256>(sh, net_host, c, s); break;
+template <class DYN>
+cudaError_t tps_launch_nt(const TpsParams<DYN> &P, TpsTile tile, cudaStream_t s) {
+  switch (tile.nt) {
+    case 64: return tps_launch_d<DYN, 64>(P, tile.ctas_per_sm, s);
+    case 128: return tps_launch_d<DYN, 128>(P, tile.ctas_per_sm, s);
+    case 256: return tps_launch_d<DYN, 256>(P, tile.ctas_per_sm, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int H, int ACT>
+cudaError_t tps_launch_mlp(const TpsShared &sh, const float *net_host, TpsTile tile, cudaStream_t s) {
+  TpsParams<MlpDyn<H, ACT>> P;
+  P.sh = sh;
+  // packed layout W1 [H][6], b1 [H], W2 [H][H], b2 [H], W3 [4][H], b3 [4] (== TpsNet field order)
+  static_assert(sizeof(TpsNet<H>) == sizeof(float) * (size_t)net_floats(H), "network layout");
+  memcpy(&P.dyn.net, net_host, sizeof(TpsNet<H>));
+  return tps_launch_nt(P, tile, s);
+}
+
+cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, TpsTile tile,
+                       cudaStream_t s, const float *theta_host) {
+  if (sh.n_units <= 0 || sh.n_inst <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (theta_host) {
+    TpsParams<BasisDyn> P;
+    P.sh = sh;
+    memcpy(P.dyn.theta, theta_host, sizeof(P.dyn.theta));
+    e = tps_launch_nt(P, tile, s);
+  } else {
+    if (H != 32) return cudaErrorInvalidValue;  // the weights of wider networks do not fit the parameter space
+    e = activation == 1 ? tps_launch_mlp<32, 1>(sh, net_host, tile, s) : tps_launch_mlp<32, 0>(sh, net_host, tile, s);
   }
   if (e != cudaSuccess) return e;
   return tps_merge(sh, s);

@@ -46,6 +46,10 @@ struct itmpc_ctx {
   // adjoint form (itmpc_reserve_adjoint): per-CTA gradient records and 4 scalars
   float *adj_part = nullptr, *adj_scal = nullptr;
   float *cem_scal = nullptr;  // cross-entropy threshold and elite count of the last CEM iteration
+  // basis-function dynamics model: coefficients (host copy for the kernel parameters, device copy)
+  std::vector<float> theta_host;
+  float *theta_d = nullptr;
+  bool have_theta = false;
   // batched form: FP32 launch shape (itmpc_autotune_batch) and the captured closed-loop graph
   TpsTile tps_tile{kTpsThreads, 0};
   cudaGraphExec_t graph_exec = nullptr;
@@ -119,6 +123,14 @@ itmpc_status check_config(const itmpc_config *cfg, char *msg, size_t n) {
     snprintf(msg, n, "unknown precision %d", cfg->precision);
     return ITMPC_ERR_ARG;
   }
+  if (cfg->dynamics != ITMPC_DYN_NETWORK && cfg->dynamics != ITMPC_DYN_BASIS) {
+    snprintf(msg, n, "unknown dynamics model %d", cfg->dynamics);
+    return ITMPC_ERR_ARG;
+  }
+  if (cfg->dynamics == ITMPC_DYN_BASIS && cfg->precision != ITMPC_FP32) {
+    snprintf(msg, n, "the basis-function model runs in FP32 only");
+    return ITMPC_ERR_ARG;
+  }
   if (cfg->precision != ITMPC_FP32 && cfg->hidden != kTcHidden) {
     snprintf(msg, n, "BF16 / FP8 iterations need hidden == %d", kTcHidden);
     return ITMPC_ERR_ARG;
@@ -181,7 +193,11 @@ void set_iter(IterParams &p, uint64_t iter, uint32_t instance) {
 
 itmpc_status ready(itmpc_ctx *c) {
   if (!c) return ITMPC_ERR_ARG;
-  if (!c->have_net) return fail(c, ITMPC_ERR_STATE, "itmpc_set_dynamics has not been called");
+  if (c->cfg.dynamics == ITMPC_DYN_BASIS) {
+    if (!c->have_theta) return fail(c, ITMPC_ERR_STATE, "itmpc_set_basis has not been called");
+  } else if (!c->have_net) {
+    return fail(c, ITMPC_ERR_STATE, "itmpc_set_dynamics has not been called");
+  }
   if (!c->have_map) return fail(c, ITMPC_ERR_STATE, "itmpc_set_costmap has not been called");
   return ITMPC_OK;
 }
@@ -273,6 +289,7 @@ void free_ctx(itmpc_ctx *c) {
   if (c->adj_part) cudaFree(c->adj_part);
   if (c->adj_scal) cudaFree(c->adj_scal);
   if (c->cem_scal) cudaFree(c->cem_scal);
+  if (c->theta_d) cudaFree(c->theta_d);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->ginst_d) cudaFree(c->ginst_d);
   if (c->gunits_d) cudaFree(c->gunits_d);
@@ -339,7 +356,8 @@ itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
       if (e != cudaSuccess) return bail(e, "cudaMalloc");
     }
   }
-  if ((c->H == 32 && c->K_cap >= kTpsMinK) || (c->H == 64 && c->K_cap >= kWideMinK) || c->H == kTcHidden) {
+  if ((c->H == 32 && c->K_cap >= kTpsMinK) || (c->H == 64 && c->K_cap >= kWideMinK) || c->H == kTcHidden ||
+      cfg->dynamics == ITMPC_DYN_BASIS) {
     itmpc_status bs = itmpc_reserve_batch(c, 1, c->K_cap);
     if (bs != ITMPC_OK) {
       free_ctx(c);
@@ -363,6 +381,7 @@ itmpc_status itmpc_set_config(itmpc_ctx *c, const itmpc_config *cfg) {
   if (cfg->K > c->K_cap) return fail(c, ITMPC_ERR_ARG, "K=%d exceeds the K=%d the context was created for", cfg->K, c->K_cap);
   if (cfg->T > c->T_max) return fail(c, ITMPC_ERR_ARG, "T=%d exceeds T_max=%d", cfg->T, c->T_max);
   if (cfg->hidden != c->H) return fail(c, ITMPC_ERR_ARG, "hidden width cannot change (%d -> %d)", c->H, cfg->hidden);
+  if (cfg->dynamics != c->cfg.dynamics) return fail(c, ITMPC_ERR_ARG, "the dynamics model cannot change");
   const int T_max = c->T_max;
   c->cfg = *cfg;
   c->cfg.T_max = T_max;
@@ -442,6 +461,27 @@ itmpc_status itmpc_set_costmaps(itmpc_ctx *c, int32_t n_maps, const float *const
   return ITMPC_OK;
 }
 
+itmpc_status itmpc_set_basis(itmpc_ctx *c, const float *theta, int32_t on_device) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (!theta) return fail(c, ITMPC_ERR_ARG, "theta is NULL");
+  if (c->cfg.dynamics != ITMPC_DYN_BASIS) return fail(c, ITMPC_ERR_ARG, "the context was created for the network model");
+  std::vector<float> h(100);
+  if (on_device) {
+    CK(c, cudaMemcpyAsync(h.data(), theta, sizeof(float) * 100, cudaMemcpyDeviceToHost, c->stream), "theta copy");
+    CK(c, cudaStreamSynchronize(c->stream), "sync");
+  } else {
+    memcpy(h.data(), theta, sizeof(float) * 100);
+  }
+  for (int i = 0; i < 100; ++i)
+    if (!finite(h[i])) return fail(c, ITMPC_ERR_ARG, "theta[%d] is not finite", i);
+  if (!c->theta_d) CK(c, cudaMalloc((void **)&c->theta_d, sizeof(float) * 100), "cudaMalloc");
+  CK(c, cudaMemcpyAsync(c->theta_d, h.data(), sizeof(float) * 100, cudaMemcpyHostToDevice, c->stream), "theta copy");
+  CK(c, cudaStreamSynchronize(c->stream), "sync");
+  c->theta_host = h;
+  c->have_theta = true;
+  return ITMPC_OK;
+}
+
 itmpc_status itmpc_set_costmap(itmpc_ctx *c, const float *map, int32_t width, int32_t height, float res,
                                float origin_x, float origin_y, int32_t on_device) {
   if (!c) return ITMPC_ERR_ARG;
@@ -495,7 +535,7 @@ itmpc_status itmpc_autotune_batch(itmpc_ctx *c, int32_t n, const itmpc_instance 
   if (st != ITMPC_OK) return st;
   if (n < 1 || !inst) return fail(c, ITMPC_ERR_ARG, "empty batch");
   if (reps < 1) reps = 3;
-  if (c->cfg.precision != ITMPC_FP32 || c->H != 32) {
+  if (c->cfg.precision != ITMPC_FP32 || (c->H != 32 && c->cfg.dynamics != ITMPC_DYN_BASIS)) {
     // fixed shapes: one 128-row MMA tile per unit (tensor cores), or the wide kernels' GEMM tile
     if (nt_out) *nt_out = batch_nt(c);
     if (ctas_out) *ctas_out = 0;
@@ -618,7 +658,8 @@ itmpc_status itmpc_batch_graph_create(itmpc_ctx *c, int32_t n, const itmpc_insta
     st = launch_batch(c, sh, c->tps_tile, cap);
     cudaError_t ea = cudaSuccess;
     if (st == ITMPC_OK && closed_loop)
-      ea = loop_launch(c->gloop_d, nullptr, n, c->H, c->net, lp, smoothing, plant, nullptr, cap);
+      ea = loop_launch(c->gloop_d, nullptr, n, c->H, c->net, lp, smoothing, plant, nullptr, cap,
+                       c->cfg.dynamics == ITMPC_DYN_BASIS ? c->theta_d : nullptr);
     if (st == ITMPC_OK && ea == cudaSuccess) ea = tps_launch_advance(c->ginst_d, n, cap);
     e = cudaStreamEndCapture(cap, &graph);
     if (e == cudaSuccess) e = ea;
@@ -736,11 +777,12 @@ TpsShared batch_shared(const itmpc_ctx *c, const TpsInstance *inst_d, const TpsU
 // Units of the tensor-core kernels are one 128-row MMA tile; FP32 units follow the tuned tile.
 int batch_nt(const itmpc_ctx *c) {
   if (c->cfg.precision != ITMPC_FP32) return kTpsThreads;
-  return c->H == 32 ? c->tps_tile.nt : wide_unit_samples(c->H);
+  return (c->H == 32 || c->cfg.dynamics == ITMPC_DYN_BASIS) ? c->tps_tile.nt : wide_unit_samples(c->H);
 }
 
 bool single_as_batch(const itmpc_ctx *c, bool debug_out) {
   if (!c->inst_d) return false;
+  if (c->cfg.dynamics == ITMPC_DYN_BASIS) return true;  // only the thread-per-sample kernels have it
   if (c->H == 32) return !debug_out && c->cfg.K >= kTpsMinK;
   return c->cfg.K >= kWideMinK;  // the wide kernel writes the states (checkpoints) itself
 }
@@ -750,6 +792,8 @@ itmpc_status launch_batch(itmpc_ctx *c, const TpsShared &sh, TpsTile tile, cudaS
   if (g.precision != ITMPC_FP32) {
     CK(c, tc_launch(sh, c->tc_img[g.precision == ITMPC_FP8 ? 1 : 0], g.precision, g.activation, s),
        "tensor-core launch");
+  } else if (g.dynamics == ITMPC_DYN_BASIS) {
+    CK(c, tps_launch(sh, nullptr, c->H, g.activation, tile, s, c->theta_host.data()), "batched basis-model launch");
   } else if (c->H == 32) {
     CK(c, tps_launch(sh, c->net_host.data(), c->H, g.activation, tile, s), "batched launch");
   } else {
@@ -771,7 +815,8 @@ itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst,
                             TpsTile tile, int states_every) {
   itmpc_status st = batch_ready(c);
   if (st != ITMPC_OK) return st;
-  const int nt = (c->cfg.precision == ITMPC_FP32 && c->H == 32) ? tile.nt : batch_nt(c);
+  const int nt = (c->cfg.precision == ITMPC_FP32 && (c->H == 32 || c->cfg.dynamics == ITMPC_DYN_BASIS))
+                     ? tile.nt : batch_nt(c);
   // the previous call's copies out of the staging buffers must have finished
   CK(c, cudaEventSynchronize(c->staged), "event sync");
   int u = 0;
@@ -936,7 +981,8 @@ itmpc_status itmpc_control_step(itmpc_ctx *c, float *x, float *U, uint64_t iter,
   st = run_iteration(c, x, U, iter, c->Uout_d, nullptr, nullptr, nullptr, 0, nullptr);
   if (st != ITMPC_OK) return st;
   const LoopItem it{c->cfg.T, c->Uout_d, U, plant ? x : nullptr, u_applied};
-  CK(c, loop_launch(nullptr, &it, 1, c->H, c->net, make_params(c), smoothing, plant, nullptr, c->stream),
+  CK(c, loop_launch(nullptr, &it, 1, c->H, c->net, make_params(c), smoothing, plant, nullptr, c->stream,
+                    c->cfg.dynamics == ITMPC_DYN_BASIS ? c->theta_d : nullptr),
      "closed-loop launch");
   return ITMPC_OK;
 }
@@ -1028,6 +1074,7 @@ itmpc_status adj_check(itmpc_ctx *c, int32_t every) {
   if (st != ITMPC_OK) return st;
   if (!c->adj_part) return fail(c, ITMPC_ERR_STATE, "itmpc_reserve_adjoint has not been called");
   if (c->cfg.precision != ITMPC_FP32) return fail(c, ITMPC_ERR_ARG, "the adjoint form is FP32 only");
+  if (c->cfg.dynamics != ITMPC_DYN_NETWORK) return fail(c, ITMPC_ERR_ARG, "the adjoint form needs the network model");
   if (every < 1 || every > ITMPC_ADJ_MAX_EVERY)
     return fail(c, ITMPC_ERR_ARG, "checkpoint interval %d outside [1, %d]", every, ITMPC_ADJ_MAX_EVERY);
   if (adj_smem_bytes(c->H, every, c->cfg.T) > c->smem_optin)

@@ -145,8 +145,9 @@ struct TpsNet {
 };
 
 // Launch the rollout (persistent over work units) and the per-instance merge.
+// theta_host != null: the basis-function model with coefficients theta_host (25 x 4) instead of the network.
 cudaError_t tps_launch(const TpsShared &sh, const float *net_host, int H, int activation, TpsTile tile,
-                       cudaStream_t s);
+                       cudaStream_t s, const float *theta_host = nullptr);
 // Advance every instance's Philox iteration index (counter words 2-3, 48 bits) by one:
 // the last node of a captured closed-loop graph, so replay r draws iteration iter + r.
 cudaError_t tps_launch_advance(TpsInstance *inst, int n, cudaStream_t s);
@@ -183,8 +184,10 @@ struct LoopItem {
 // One CTA per item: U_s = smoothing(U', U) (0 none, 1 SGF(U'), 2 U + SGF(U' - U)), u_applied = U_s[0],
 // x <- F(x, g(u_applied)) when plant and x != null (the FP32 network of the context), U <- shift(U_s)
 // with U[T-1] = (0, 0); then *counter += 1 when counter != null (one thread, after the items).
+// theta != null: the plant is the basis-function model with these coefficients (device, 25 x 4).
 cudaError_t loop_launch(const LoopItem *items_dev, const LoopItem *item_host, int n, int H, const float *net,
-                        const IterParams &p, int smoothing, int plant, unsigned long long *counter, cudaStream_t s);
+                        const IterParams &p, int smoothing, int plant, unsigned long long *counter, cudaStream_t s,
+                        const float *theta = nullptr);
 
 // ---- cross-entropy weights (cem.cu): Alg. 3 and the elite-mean update ----
 // w (K) and scal[0] = Z, scal[1] = elite count from the costs S; then U_out = the mean of the

@@ -82,4 +82,57 @@ __device__ __forceinline__ float tps_state_cost(const TpsShared &sh, const float
   return sh.w_track * h + sh.w_speed * sp * sp + sh.w_stab * zeta * zeta + sh.w_crash * imp;
 }
 
+// The basis-function model (Sec. V-B and the appendix): f = Theta^T phi(x_d, u).  In the
+// fast branch tan(alpha) = tan(arctan z) = z, so the slip-angle terms need no arctan / tan.
+struct BasisDyn {
+  float theta[100];  // [basis i][output o]
+  __device__ __forceinline__ void eval(float th, float vx, float vy, float r, float ud, float uF, float &d0,
+                                       float &d1, float &d2, float &d3) const {
+    float tf, tr, q;
+    if (vx > 0.1f) {
+      const float iv = 1.0f / vx;
+      tf = fmaf(0.45f, r, vy) * iv - ud;
+      tr = fmaf(-0.35f, r, vy) * iv;
+      q = vy * iv;
+    } else {
+      tf = -tanf(ud);
+      tr = 0.0f;
+      q = 0.0f;
+    }
+    const float sd = sinf(ud);
+    const float atf = fabsf(tf), atr = fabsf(tr);
+    const float phi[25] = {uF,
+                           vx * 0.1f,
+                           sd * tf * (1.0f / 1200.0f),
+                           sd * tf * atf * (1.0f / 1440000.0f),
+                           sd * tf * tf * tf * (1.0f / 1728000000.0f),
+                           r * vy * (1.0f / 25.0f),
+                           r * 0.1f,
+                           vy * 0.1f,
+                           sd,
+                           q * (1.0f / 40.0f),
+                           tf * (1.0f / 1400.0f),
+                           tf * atf * (1.0f / 1960000.0f),
+                           tf * tf * tf * (1.0f / 2744000000.0f),
+                           tr * (1.0f / 40.0f),
+                           tr * atr * (1.0f / 1600.0f),
+                           tr * tr * tr * (1.0f / 64000.0f),
+                           r * vx * (1.0f / 50.0f),
+                           th,
+                           th * r,
+                           th * vx * (1.0f / 3.0f),
+                           th * vx * r * (1.0f / 5.0f),
+                           vx * vx * 0.01f,
+                           vx * vx * vx * 0.001f,
+                           uF * uF,
+                           uF * uF * uF};
+    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 25; ++i)
+#pragma unroll
+      for (int o = 0; o < 4; ++o) d[o] = fmaf(theta[i * 4 + o], phi[i], d[o]);
+    d0 = d[0]; d1 = d[1]; d2 = d[2]; d3 = d[3];
+  }
+};
+
 }  // namespace itmpc

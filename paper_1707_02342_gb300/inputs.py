@@ -52,6 +52,12 @@ def mlp_xavier(widths=(6, 32, 32, 4), seed: int = 42, bias_scale: float = 0.0):
     return layers
 
 
+def basis_theta(seed: int = 5, scale: float = 0.05) -> np.ndarray:
+    """Synthetic coefficients (25, 4) for the basis-function dynamics model: N(0, scale^2), seeded.
+    (The paper fits Theta to a driving data set that is not available.)"""
+    return (rng(seed).normal(0.0, scale, size=(25, 4))).astype(np.float32)
+
+
 def mlp_param_count(widths) -> int:
     """Number of weights plus biases of a fully connected network."""
     return sum(i * o + o for i, o in zip(widths[:-1], widths[1:]))

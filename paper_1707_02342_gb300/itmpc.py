@@ -17,6 +17,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_OOM = 0, -1, -
 FP32, BF16, FP8 = 0, 1, 2
 ACT_TANH, ACT_IDENTITY = 0, 1
 SMOOTH_NONE, SMOOTH_SGF, SMOOTH_SGF_DELTA = 0, 1, 2
+DYN_NETWORK, DYN_BASIS = 0, 1
 MAX_K, MAX_T, STATS_LEN = 1 << 24, 512, 8
 NOALLOC_MAX_K, NOALLOC_MAX_T, NOALLOC_SCRATCH_BYTES = 8192, 256, 4 << 20
 
@@ -34,7 +35,7 @@ class Config(C.Structure):
         ("v_des", C.c_float), ("crash_cost", C.c_float), ("crash_decay", C.c_float),
         ("track_thresh", C.c_float), ("slip_thresh", C.c_float), ("map_cap", C.c_float),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("precision", C.c_int32),
-        ("activation", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p),
+        ("activation", C.c_int32), ("dynamics", C.c_int32), ("stream", C.c_void_p),
     ]
 
 
@@ -71,6 +72,7 @@ SIGNATURES = {
     "itmpc_batch_graph_create": (C.c_int, [_vp, _i32, _vp, _i32, _i32, _i32]),
     "itmpc_control_step": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _i32, _vp]),
     "itmpc_iterate_cem": (C.c_int, [_vp, _vp, _vp, _u64, _f, _vp, _vp, _vp]),
+    "itmpc_set_basis": (C.c_int, [_vp, _vp, _i32]),
     "itmpc_control_graph_create": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _i32, _vp]),
     "itmpc_control_graph_launch": (C.c_int, [_vp]),
     "itmpc_control_graph_destroy": (C.c_int, [_vp]),
@@ -118,7 +120,7 @@ def make_config(K: int, T: int, *, T_max: int = 0, hidden: int = 32, dt=0.02, la
                 alpha_explore=0.0, sigma=(0.3, 0.35), u_min=(-1.0, -1.0), u_max=(1.0, 1.0),
                 cost_w=(1.0, 1.0, 1.0, 0.0), v_des=6.0, crash_cost=1e4, crash_decay=0.9, track_thresh=0.99,
                 slip_thresh=0.75, map_cap=2.5, seed=0x170702342, instance=0, precision=FP32,
-                activation=ACT_TANH, stream=None) -> Config:
+                activation=ACT_TANH, dynamics=DYN_NETWORK, stream=None) -> Config:
     c = Config()
     c.K, c.T, c.T_max, c.hidden = K, T, T_max, hidden
     c.dt, c.lam, c.gamma, c.alpha_explore = dt, lam, gamma, alpha_explore
@@ -129,6 +131,7 @@ def make_config(K: int, T: int, *, T_max: int = 0, hidden: int = 32, dt=0.02, la
     c.v_des, c.crash_cost, c.crash_decay = v_des, crash_cost, crash_decay
     c.track_thresh, c.slip_thresh, c.map_cap = track_thresh, slip_thresh, map_cap
     c.seed, c.instance, c.precision, c.activation = seed & (2 ** 64 - 1), instance, precision, activation
+    c.dynamics = dynamics
     c.stream = stream
     return c
 
@@ -201,7 +204,7 @@ class Controller:
                           crash_decay=d.pop("crash_decay"), track_thresh=d.pop("track_thresh"),
                           slip_thresh=d.pop("slip_thresh"), map_cap=d.pop("map_cap"), seed=d.pop("seed"),
                           instance=d.pop("instance"), precision=d.pop("precision"),
-                          activation=d.pop("activation"), stream=d.pop("stream"))
+                          activation=d.pop("activation"), dynamics=d.pop("dynamics"), stream=d.pop("stream"))
         for k, v in kw.items():
             if k in ("sigma", "u_min", "u_max", "cost_w"):
                 getattr(cfg, k)[:] = list(v)
@@ -217,6 +220,12 @@ class Controller:
         Ws = (C.c_void_p * 3)(*[_dptr(W) for W, _ in layers])
         bs = (C.c_void_p * 3)(*[_dptr(b) for _, b in layers])
         self._check(self._L.itmpc_set_dynamics(self._h, 3, widths, Ws, bs, 1))
+
+    def set_basis(self, theta):
+        """Coefficients (25, 4) of the basis-function dynamics model (CUDA float32 tensor)."""
+        if tuple(theta.shape) != (25, 4) or not theta.is_contiguous():
+            raise ValueError("theta must be a contiguous (25, 4) tensor")
+        self._check(self._L.itmpc_set_basis(self._h, _dptr(theta), 1))
 
     def set_costmap(self, cmap, res: float, origin_x: float, origin_y: float):
         """cmap: (height, width) CUDA float32 tensor."""
