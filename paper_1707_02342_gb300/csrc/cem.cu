@@ -45,17 +45,32 @@ __device__ float block_sum(float v, float *red) {
   return s;
 }
 
+constexpr int kKeysInSmem = 11264;  // up to this many keys are staged in shared memory (44 KB + 1.2 KB static)
+constexpr uint32_t kNonFinite = 0xFFFFFFFFu;  // above every finite key
+
 __global__ void __launch_bounds__(kSelThreads) cem_select_kernel(int K, int zeta0, const float *__restrict__ S,
                                                                  float *w, float *scal, int *status) {
   __shared__ unsigned int hist[256];
   __shared__ float red[32];
   __shared__ uint32_t prefix_s;
   __shared__ int rank_s;
-  const int tid = threadIdx.x;
+  extern __shared__ uint32_t keys_s[];  // K keys when K <= kKeysInSmem
+  const int tid = threadIdx.x, lane = tid & 31;
+  const bool staged = K <= kKeysInSmem;
+  auto key_at = [&](int k) -> uint32_t {
+    if (staged) return keys_s[k];
+    const float v = S[k];
+    return isfinite(v) ? fkey(v) : kNonFinite;
+  };
   // finite costs and the clamped rank
   float nf = 0.0f;
-  for (int k = tid; k < K; k += kSelThreads) nf += isfinite(S[k]) ? 1.0f : 0.0f;
-  const int n_fin = (int)block_sum(nf, red);
+  for (int k = tid; k < K; k += kSelThreads) {
+    const float v = S[k];
+    const bool fin = isfinite(v);
+    nf += fin ? 1.0f : 0.0f;
+    if (staged) keys_s[k] = fin ? fkey(v) : kNonFinite;
+  }
+  const int n_fin = (int)block_sum(nf, red);  // (its barriers also publish keys_s)
   if (n_fin == 0) {
     for (int k = tid; k < K; k += kSelThreads) w[k] = 0.0f;
     if (tid == 0) {
@@ -73,17 +88,38 @@ __global__ void __launch_bounds__(kSelThreads) cem_select_kernel(int K, int zeta
     for (int i = tid; i < 256; i += kSelThreads) hist[i] = 0u;
     __syncthreads();
     for (int k = tid; k < K; k += kSelThreads) {
-      const float v = S[k];
-      if (!isfinite(v)) continue;
-      const uint32_t key = fkey(v);
+      const uint32_t key = key_at(k);
+      if (key == kNonFinite) continue;
       if ((key & hi_mask) == prefix) atomicAdd(&hist[(key >> shift) & 0xFFu], 1u);
     }
     __syncthreads();
-    if (tid == 0) {
-      int r = rank, d = 0;
-      while (d < 255 && (int)hist[d] < r) r -= (int)hist[d++];
-      prefix_s = prefix | ((uint32_t)d << shift);
-      rank_s = r;
+    if (tid < 32) {
+      // the digit holding rank r: lane l owns bins 8 l .. 8 l + 7; a warp scan of the lane
+      // totals finds the lane, which then walks its eight bins
+      int cnt[8], tot = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        cnt[b] = (int)hist[8 * lane + b];
+        tot += cnt[b];
+      }
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += n;
+      }
+      const unsigned hit = __ballot_sync(FULL_MASK, incl >= rank);
+      const int owner = hit ? __ffs(hit) - 1 : 31;
+      if (lane == owner) {
+        int r = rank - (incl - tot), d = 8 * lane;
+#pragma unroll 1
+        for (int b = 0; b < 7 && cnt[b] < r; ++b) {
+          r -= cnt[b];
+          ++d;
+        }
+        prefix_s = prefix | ((uint32_t)d << shift);
+        rank_s = r;
+      }
     }
     __syncthreads();
     prefix = prefix_s;
@@ -91,16 +127,10 @@ __global__ void __launch_bounds__(kSelThreads) cem_select_kernel(int K, int zeta
   }
   const uint32_t zkey = prefix;
   float ne = 0.0f;
-  for (int k = tid; k < K; k += kSelThreads) {
-    const float v = S[k];
-    ne += (isfinite(v) && fkey(v) <= zkey) ? 1.0f : 0.0f;
-  }
+  for (int k = tid; k < K; k += kSelThreads) ne += key_at(k) <= zkey ? 1.0f : 0.0f;
   const float m = block_sum(ne, red);
   const float inv = 1.0f / m;
-  for (int k = tid; k < K; k += kSelThreads) {
-    const float v = S[k];
-    w[k] = (isfinite(v) && fkey(v) <= zkey) ? inv : 0.0f;
-  }
+  for (int k = tid; k < K; k += kSelThreads) w[k] = key_at(k) <= zkey ? inv : 0.0f;
   if (tid == 0) {
     scal[0] = key_to_float(zkey);
     scal[1] = m;
@@ -139,7 +169,8 @@ __global__ void __launch_bounds__(kUpdThreads) cem_update_kernel(const IterParam
 }  // namespace
 
 cudaError_t cem_launch(const IterParams &p, int zeta0, const float *S, float *w, float *scal, cudaStream_t s) {
-  cem_select_kernel<<<1, kSelThreads, 0, s>>>(p.K, zeta0, S, w, scal, p.status);
+  const size_t smem = p.K <= kKeysInSmem ? sizeof(uint32_t) * (size_t)p.K : 0;
+  cem_select_kernel<<<1, kSelThreads, smem, s>>>(p.K, zeta0, S, w, scal, p.status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   cem_update_kernel<<<p.T, kUpdThreads, 0, s>>>(p, w, scal);

@@ -94,9 +94,17 @@ __global__ void __launch_bounds__(kLoopThreads) loop_kernel(const LoopItem *item
     }
     __syncthreads();
     for (int j = tid; j < H; j += kLoopThreads) {
-      float a = __ldg(net + net_off_b2(H) + j);
-      for (int i = 0; i < H; ++i) a = fmaf(__ldg(net + net_off_W2(H) + j * H + i), hv[i], a);
-      h2[j] = activation<ACT>(a);
+      // four independent chains so that the row's weight loads are in flight together
+      const float *wr = net + net_off_W2(H) + (size_t)j * H;
+      float a0 = __ldg(net + net_off_b2(H) + j), a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll 8
+      for (int i = 0; i < H; i += 4) {
+        a0 = fmaf(__ldg(wr + i), hv[i], a0);
+        a1 = fmaf(__ldg(wr + i + 1), hv[i + 1], a1);
+        a2 = fmaf(__ldg(wr + i + 2), hv[i + 2], a2);
+        a3 = fmaf(__ldg(wr + i + 3), hv[i + 3], a3);
+      }
+      h2[j] = activation<ACT>((a0 + a1) + (a2 + a3));
     }
     __syncthreads();
     if (tid < 32) {
