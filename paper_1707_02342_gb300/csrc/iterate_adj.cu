@@ -8,8 +8,11 @@
 // for theta = the four cost multipliers, the nominal sequence and the network.
 //
 //   adj_scalars_kernel   J, c0 = sum_t gU_t . U'_t and sum of importance weights;
-//   adj_backward_kernel  one warp per sample k with w_k != 0 (a zero weight makes
-//                        every term of sample k vanish).  Its cost cotangent is
+//   adj_backward_kernel  two samples per warp, side by side, so that every W2 element a
+//                        lane loads from shared memory feeds both samples' FMAs.  A sample
+//                        with w_k = 0 contributes nothing: it runs from the zero state with
+//                        a zero cotangent, and a warp whose two samples both have w = 0
+//                        skips.  The cost cotangent of sample k is
 //                          Sbar_k = w_k (gJ (1 - (S_k - J)/lambda) - (a_k - c0)/lambda),
 //                          a_k = sum_t gU_t . v_{k,t}
 //                        (dw_k/dS_j = -(1/lambda) w_k (delta_kj - w_j)).  The horizon is
@@ -35,12 +38,14 @@ namespace itmpc {
 
 namespace {
 
-constexpr int kAdjWarps = 8;
+constexpr int kAdjWarps = 4;                     // warps per CTA
+constexpr int kAdjSPW = 2;                       // samples per warp, side by side
+constexpr int kAdjSamples = kAdjWarps * kAdjSPW; // samples per CTA
 
 __host__ __device__ inline int adj_rec_floats(int H, int T) { return (net_floats(H) + 4 + 2 * T + 3) & ~3; }
 
-// Per-warp shared floats for a segment of `every` steps.
-__host__ __device__ inline size_t adj_warp_floats(int H, int every) {
+// Per-sample shared floats for a segment of `every` steps.
+__host__ __device__ inline size_t adj_sample_floats(int H, int every) {
   return 8 * (size_t)(every + 1)      // states x_{t0..t0+every}, 8 floats each
          + 4 * (size_t)every          // (v0, v1, g0, g1) per step
          + 4 * (size_t)every          // cost slope (px, py, vx, vy) at x_{t0+1+i}
@@ -48,7 +53,7 @@ __host__ __device__ inline size_t adj_warp_floats(int H, int every) {
 }
 
 __host__ __device__ inline size_t adj_smem_floats(int H, int every, int T) {
-  return 2 * (size_t)H * H + kAdjWarps * adj_warp_floats(H, every) + (size_t)kAdjWarps * 2 * T +
+  return 2 * (size_t)H * H + kAdjSamples * adj_sample_floats(H, every) + (size_t)kAdjWarps * 2 * T +
          (size_t)adj_rec_floats(H, T);
 }
 
@@ -156,27 +161,31 @@ __global__ void __launch_bounds__(1024) adj_scalars_kernel(int K, int T, int n_i
 
 template <int H, int ACT>
 __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __grid_constant__ AdjParams a) {
-  constexpr int NW = kAdjWarps;
+  constexpr int NW = kAdjWarps, SPW = kAdjSPW, SC = kAdjSamples;
   constexpr int M = H / 32;
   constexpr int E = H * H / (NW * 32);  // W2-gradient entries per thread
   constexpr int TJ = 4, TI = E / 4, NIB = H / TI;
-  static_assert(E % 4 == 0 && TI >= 1, "tile");
+  static_assert(E % 4 == 0 && (TI == 2 || TI % 4 == 0), "tile");
   const IterParams &p = a.p;
   const int T = p.T, K = p.K, every = a.every;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const size_t wf = adj_warp_floats(H, every);
+  const size_t sf = adj_sample_floats(H, every);
 
   extern __shared__ __align__(16) float sm[];
-  float *W2T_s = sm;            // [i][j] = W2[j][i]
-  float *W2_s = sm + H * H;     // [j][i] = W2[j][i]
-  float *wreg = sm + 2 * H * H; // NW per-warp regions
-  float *ub_s = wreg + NW * wf; // NW x 2T per-warp dL/dU of this CTA's samples
+  float *W2T_s = sm;             // [i][j] = W2[j][i]
+  float *W2_s = sm + H * H;      // [j][i] = W2[j][i]
+  float *sreg = sm + 2 * H * H;  // SC per-sample regions
+  float *ub_s = sreg + SC * sf;  // NW x 2T: per-warp dL/dU of its samples
   float *rec_s = ub_s + NW * 2 * T;
-  float *xs = wreg + warp * wf;
-  float *vg = xs + 8 * (every + 1);
-  float *gc = vg + 4 * every;
-  float *hs1 = gc + 4 * every;
-  float *hs2 = hs1 + H * every;
+  float *xs[SPW], *vg[SPW], *gc[SPW], *hs1[SPW], *hs2[SPW];
+#pragma unroll
+  for (int q = 0; q < SPW; ++q) {
+    xs[q] = sreg + (warp * SPW + q) * sf;
+    vg[q] = xs[q] + 8 * (every + 1);
+    gc[q] = vg[q] + 4 * every;
+    hs1[q] = gc[q] + 4 * every;
+    hs2[q] = hs1[q] + H * every;
+  }
 
   const float *net = p.net;
   for (int e = threadIdx.x; e < H * H; e += NW * 32) {
@@ -193,7 +202,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
   for (int m = 0; m < M; ++m) {
     const int j = lane + 32 * m;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) W1r[m][q] = __ldg(net + net_off_W1(H) + j * 6 + q);
+    for (int c = 0; c < 6; ++c) W1r[m][c] = __ldg(net + net_off_W1(H) + j * 6 + c);
     b1r[m] = __ldg(net + net_off_b1(H) + j);
     b2r[m] = __ldg(net + net_off_b2(H) + j);
 #pragma unroll
@@ -202,17 +211,18 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
 #pragma unroll
   for (int o = 0; o < 4; ++o) b3u[o] = __ldg(net + net_off_b3(H) + o);
 
-  float gW1[M][6], gb1[M], gb2[M], gW3[M][4], gb3[4], compacc[4];
+  // gradient accumulators: both samples of the warp add into the same registers
+  float gW1[M][6], gb1[M], gb2[M], gW3[M][4], gb3[4], gcw[4];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) gW1[m][q] = 0.0f;
+    for (int c = 0; c < 6; ++c) gW1[m][c] = 0.0f;
     gb1[m] = gb2[m] = 0.0f;
 #pragma unroll
     for (int o = 0; o < 4; ++o) gW3[m][o] = 0.0f;
   }
 #pragma unroll
-  for (int o = 0; o < 4; ++o) gb3[o] = compacc[o] = 0.0f;
+  for (int o = 0; o < 4; ++o) gb3[o] = gcw[o] = 0.0f;
   const int jb = threadIdx.x / NIB, ib = threadIdx.x % NIB;
   float gW2[TJ][TI];
 #pragma unroll
@@ -220,229 +230,277 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
 #pragma unroll
     for (int c = 0; c < TI; ++c) gW2[r][c] = 0.0f;
 
-  // this warp's sample and its cost cotangent
-  const int k = blockIdx.x * NW + warp;
-  const bool imp = k < p.n_imp;
-  float Sbar = 0.0f;
-  bool active = false;
-  if (k < K) {
-    const float wk = __ldg(a.w + k);
-    if (wk != 0.0f) {
-      active = true;
+  // this warp's samples and their cost cotangents; an inactive sample (k >= K or w_k = 0)
+  // runs from the zero state with Sbar = 0, so that everything it adds is zero
+  int kq[SPW];
+  bool act[SPW], impq[SPW];
+  float Sbar[SPW];
+  const float J = __ldg(a.scal), c0 = __ldg(a.scal + 1), gJ = __ldg(a.scal + 3);
+#pragma unroll
+  for (int q = 0; q < SPW; ++q) {
+    const int k = blockIdx.x * SC + warp * SPW + q;
+    kq[q] = k;
+    impq[q] = k < p.n_imp;
+    act[q] = k < K && __ldg(a.w + k) != 0.0f;
+    Sbar[q] = 0.0f;
+    if (act[q]) {
       float acc = 0.0f;
       if (a.gUo) {
         for (int t = lane; t < T; t += 32) {
           const float2 e = noise_at(p, (uint32_t)k, (uint32_t)t);
-          const float v0 = imp ? __ldg(p.U + 2 * t) + e.x : e.x;
-          const float v1 = imp ? __ldg(p.U + 2 * t + 1) + e.y : e.y;
+          const float v0 = impq[q] ? __ldg(p.U + 2 * t) + e.x : e.x;
+          const float v1 = impq[q] ? __ldg(p.U + 2 * t + 1) + e.y : e.y;
           acc = fmaf(__ldg(a.gUo + 2 * t), v0, acc);
           acc = fmaf(__ldg(a.gUo + 2 * t + 1), v1, acc);
         }
         acc = warp_sum(acc);
       }
-      const float J = __ldg(a.scal), c0 = __ldg(a.scal + 1), gJ = __ldg(a.scal + 3);
-      Sbar = wk * (gJ * (1.0f - (__ldg(a.S + k) - J) * p.inv_lambda) - (acc - c0) * p.inv_lambda);
+      Sbar[q] = __ldg(a.w + k) * (gJ * (1.0f - (__ldg(a.S + k) - J) * p.inv_lambda) - (acc - c0) * p.inv_lambda);
     }
   }
+  const bool warp_active = act[0] || act[1];
   __syncthreads();
 
   const float dt = p.dt;
   const int n_ck = T / every + 1;
   const int nseg = (T + every - 1) / every;
-  float xb[7];
+  float xb[SPW][7];
 #pragma unroll
-  for (int q = 0; q < 7; ++q) xb[q] = 0.0f;
+  for (int q = 0; q < SPW; ++q)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) xb[q][c] = 0.0f;
 
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int t0 = seg * every;
     const int nst = min(every, T - t0);
-    if (active) {
-      // (a) re-run the segment forward from its checkpoint
-      float x[7];
-      const float *ck = a.ckpt + ((size_t)k * n_ck + seg) * 7;
+    if (warp_active) {
+      // (a) re-run the segment forward from its checkpoints, both samples side by side
+      float x[SPW][7];
 #pragma unroll
-      for (int q = 0; q < 7; ++q) x[q] = __ldg(ck + q);
-      if (lane < nst) {
-        const int t = t0 + lane;
-        const float2 e = noise_at(p, (uint32_t)k, (uint32_t)t);
-        const float v0 = imp ? __ldg(p.U + 2 * t) + e.x : e.x;
-        const float v1 = imp ? __ldg(p.U + 2 * t + 1) + e.y : e.y;
-        *reinterpret_cast<float4 *>(vg + 4 * lane) =
-            make_float4(v0, v1, fminf(fmaxf(v0, p.umin0), p.umax0), fminf(fmaxf(v1, p.umin1), p.umax1));
+      for (int q = 0; q < SPW; ++q) {
+        const float *ck = a.ckpt + ((size_t)kq[q] * n_ck + seg) * 7;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) x[q][c] = act[q] ? __ldg(ck + c) : 0.0f;
+        if (lane < nst) {
+          const int t = t0 + lane;
+          const float2 e = noise_at(p, (uint32_t)kq[q], (uint32_t)t);
+          const float v0 = impq[q] ? __ldg(p.U + 2 * t) + e.x : e.x;
+          const float v1 = impq[q] ? __ldg(p.U + 2 * t + 1) + e.y : e.y;
+          *reinterpret_cast<float4 *>(vg[q] + 4 * lane) =
+              make_float4(v0, v1, fminf(fmaxf(v0, p.umin0), p.umax0), fminf(fmaxf(v1, p.umin1), p.umax1));
+        }
+        if (lane < 7) xs[q][lane] = x[q][lane];
       }
-      if (lane < 7) xs[lane] = x[lane];
       __syncwarp();
       for (int i = 0; i < nst; ++i) {
-        const float z[6] = {x[3], x[4], x[5], x[6], vg[4 * i + 2], vg[4 * i + 3]};
-        float *h1row = hs1 + i * H, *h2row = hs2 + i * H;
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          float acc = b1r[m];
+        for (int q = 0; q < SPW; ++q) {
+          const float z[6] = {x[q][3], x[q][4], x[q][5], x[q][6], vg[q][4 * i + 2], vg[q][4 * i + 3]};
 #pragma unroll
-          for (int q = 0; q < 6; ++q) acc = fmaf(W1r[m][q], z[q], acc);
-          h1row[lane + 32 * m] = activation<ACT>(acc);
+          for (int m = 0; m < M; ++m) {
+            float acc = b1r[m];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc = fmaf(W1r[m][c], z[c], acc);
+            hs1[q][i * H + lane + 32 * m] = activation<ACT>(acc);
+          }
         }
         __syncwarp();
-        float acc2[M];
+        float acc2[SPW][M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) acc2[m] = b2r[m];
+        for (int q = 0; q < SPW; ++q)
+#pragma unroll
+          for (int m = 0; m < M; ++m) acc2[q][m] = b2r[m];
 #pragma unroll 4
         for (int ii = 0; ii < H; ii += 4) {
-          const float4 hv = *reinterpret_cast<const float4 *>(h1row + ii);
+          float4 hv[SPW];
+#pragma unroll
+          for (int q = 0; q < SPW; ++q) hv[q] = *reinterpret_cast<const float4 *>(hs1[q] + i * H + ii);
 #pragma unroll
           for (int m = 0; m < M; ++m) {
             const float *w = W2T_s + ii * H + lane + 32 * m;
-            acc2[m] = fmaf(w[0], hv.x, acc2[m]);
-            acc2[m] = fmaf(w[H], hv.y, acc2[m]);
-            acc2[m] = fmaf(w[2 * H], hv.z, acc2[m]);
-            acc2[m] = fmaf(w[3 * H], hv.w, acc2[m]);
+            const float w0 = w[0], w1 = w[H], w2 = w[2 * H], w3 = w[3 * H];
+#pragma unroll
+            for (int q = 0; q < SPW; ++q) {
+              acc2[q][m] = fmaf(w0, hv[q].x, acc2[q][m]);
+              acc2[q][m] = fmaf(w1, hv[q].y, acc2[q][m]);
+              acc2[q][m] = fmaf(w2, hv[q].z, acc2[q][m]);
+              acc2[q][m] = fmaf(w3, hv[q].w, acc2[q][m]);
+            }
           }
         }
-        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const float h2 = activation<ACT>(acc2[m]);
-          h2row[lane + 32 * m] = h2;
+        for (int q = 0; q < SPW; ++q) {
+          float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-          for (int o = 0; o < 4; ++o) d[o] = fmaf(W3c[m][o], h2, d[o]);
+          for (int m = 0; m < M; ++m) {
+            const float h2 = activation<ACT>(acc2[q][m]);
+            hs2[q][i * H + lane + 32 * m] = h2;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) d[o] = fmaf(W3c[m][o], h2, d[o]);
+          }
+#pragma unroll
+          for (int o = 0; o < 4; ++o) d[o] = warp_sum(d[o]) + b3u[o];
+          float sn, cs;
+          sincosf(x[q][2], &sn, &cs);
+          const float nx0 = x[q][0] + (cs * x[q][4] - sn * x[q][5]) * dt;
+          const float nx1 = x[q][1] + (sn * x[q][4] + cs * x[q][5]) * dt;
+          const float nx2 = x[q][2] + x[q][6] * dt;
+          x[q][0] = nx0;
+          x[q][1] = nx1;
+          x[q][2] = nx2;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) x[q][3 + c] = x[q][3 + c] + d[c] * dt;
+          if (lane < 7) xs[q][8 * (i + 1) + lane] = x[q][lane];
         }
-#pragma unroll
-        for (int o = 0; o < 4; ++o) d[o] = warp_sum(d[o]) + b3u[o];
-        float sn, cs;
-        sincosf(x[2], &sn, &cs);
-        const float nx0 = x[0] + (cs * x[4] - sn * x[5]) * dt;
-        const float nx1 = x[1] + (sn * x[4] + cs * x[5]) * dt;
-        const float nx2 = x[2] + x[6] * dt;
-        x[0] = nx0;
-        x[1] = nx1;
-        x[2] = nx2;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) x[3 + q] = x[3 + q] + d[q] * dt;
-        if (lane < 7) xs[8 * (i + 1) + lane] = x[lane];
       }
       __syncwarp();
-      // (b) cost slopes at x_{t0+1 .. t0+nst}, one step per lane
+      // (b) cost slopes at x_{t0+1 .. t0+nst}, one step per lane; Sbar-weighted components
       if (lane < nst) {
-        const float *xt = xs + 8 * (lane + 1);
-        float g4[4], c4[4];
-        state_cost_slope(p, xt[0], xt[1], xt[4], xt[5], t0 + lane + 1, g4, c4);
-        *reinterpret_cast<float4 *>(gc + 4 * lane) = make_float4(g4[0], g4[1], g4[2], g4[3]);
 #pragma unroll
-        for (int o = 0; o < 4; ++o) compacc[o] += c4[o];
+        for (int q = 0; q < SPW; ++q) {
+          const float *xt = xs[q] + 8 * (lane + 1);
+          float g4[4], c4[4];
+          state_cost_slope(p, xt[0], xt[1], xt[4], xt[5], t0 + lane + 1, g4, c4);
+          *reinterpret_cast<float4 *>(gc[q] + 4 * lane) = make_float4(g4[0], g4[1], g4[2], g4[3]);
+#pragma unroll
+          for (int o = 0; o < 4; ++o) gcw[o] = fmaf(Sbar[q], c4[o], gcw[o]);
+        }
       }
       __syncwarp();
       // (c) reverse the segment's steps
       for (int i = nst - 1; i >= 0; --i) {
         const int t = t0 + i;  // step t -> t + 1 used v_t
-        const float4 gci = *reinterpret_cast<const float4 *>(gc + 4 * i);
-        xb[0] = fmaf(Sbar, gci.x, xb[0]);
-        xb[1] = fmaf(Sbar, gci.y, xb[1]);
-        xb[4] = fmaf(Sbar, gci.z, xb[4]);
-        xb[5] = fmaf(Sbar, gci.w, xb[5]);
-        const float *xp = xs + 8 * i;
-        const float th = xp[2], vx = xp[4], vy = xp[5];
-        float sn, cs;
-        sincosf(th, &sn, &cs);
-        float xbp[7];
+        float xbp[SPW][7], db[SPW][4];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) xbp[q] = xb[q];
-        xbp[2] += dt * (xb[0] * (-sn * vx - cs * vy) + xb[1] * (cs * vx - sn * vy));
-        xbp[4] += dt * (xb[0] * cs + xb[1] * sn);
-        xbp[5] += dt * (-xb[0] * sn + xb[1] * cs);
-        xbp[6] += dt * xb[2];
-        const float db[4] = {dt * xb[3], dt * xb[4], dt * xb[5], dt * xb[6]};
+        for (int q = 0; q < SPW; ++q) {
+          const float4 gci = *reinterpret_cast<const float4 *>(gc[q] + 4 * i);
+          xb[q][0] = fmaf(Sbar[q], gci.x, xb[q][0]);
+          xb[q][1] = fmaf(Sbar[q], gci.y, xb[q][1]);
+          xb[q][4] = fmaf(Sbar[q], gci.z, xb[q][4]);
+          xb[q][5] = fmaf(Sbar[q], gci.w, xb[q][5]);
+          const float *xp = xs[q] + 8 * i;
+          const float th = xp[2], vx = xp[4], vy = xp[5];
+          float sn, cs;
+          sincosf(th, &sn, &cs);
 #pragma unroll
-        for (int o = 0; o < 4; ++o) gb3[o] += db[o];
-        float *h1row = hs1 + i * H, *h2row = hs2 + i * H;
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const float h2 = h2row[lane + 32 * m];
-          float hb = 0.0f;
+          for (int c = 0; c < 7; ++c) xbp[q][c] = xb[q][c];
+          xbp[q][2] += dt * (xb[q][0] * (-sn * vx - cs * vy) + xb[q][1] * (cs * vx - sn * vy));
+          xbp[q][4] += dt * (xb[q][0] * cs + xb[q][1] * sn);
+          xbp[q][5] += dt * (-xb[q][0] * sn + xb[q][1] * cs);
+          xbp[q][6] += dt * xb[q][2];
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
-            hb = fmaf(W3c[m][o], db[o], hb);
-            gW3[m][o] = fmaf(db[o], h2, gW3[m][o]);
+            db[q][o] = dt * xb[q][3 + o];
+            gb3[o] += db[q][o];
           }
-          const float a2b = ACT == 1 ? hb : hb * (1.0f - h2 * h2);
-          gb2[m] += a2b;
-          h2row[lane + 32 * m] = a2b;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            const float h2 = hs2[q][i * H + lane + 32 * m];
+            float hb = 0.0f;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+              hb = fmaf(W3c[m][o], db[q][o], hb);
+              gW3[m][o] = fmaf(db[q][o], h2, gW3[m][o]);
+            }
+            const float a2b = ACT == 1 ? hb : hb * (1.0f - h2 * h2);
+            gb2[m] += a2b;
+            hs2[q][i * H + lane + 32 * m] = a2b;
+          }
         }
         __syncwarp();
-        float h1b[M];
+        float h1b[SPW][M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) h1b[m] = 0.0f;
+        for (int q = 0; q < SPW; ++q)
+#pragma unroll
+          for (int m = 0; m < M; ++m) h1b[q][m] = 0.0f;
 #pragma unroll 4
         for (int jj = 0; jj < H; jj += 4) {
-          const float4 av = *reinterpret_cast<const float4 *>(h2row + jj);
+          float4 av[SPW];
+#pragma unroll
+          for (int q = 0; q < SPW; ++q) av[q] = *reinterpret_cast<const float4 *>(hs2[q] + i * H + jj);
 #pragma unroll
           for (int m = 0; m < M; ++m) {
             const float *w = W2_s + jj * H + lane + 32 * m;
-            h1b[m] = fmaf(w[0], av.x, h1b[m]);
-            h1b[m] = fmaf(w[H], av.y, h1b[m]);
-            h1b[m] = fmaf(w[2 * H], av.z, h1b[m]);
-            h1b[m] = fmaf(w[3 * H], av.w, h1b[m]);
+            const float w0 = w[0], w1 = w[H], w2 = w[2 * H], w3 = w[3 * H];
+#pragma unroll
+            for (int q = 0; q < SPW; ++q) {
+              h1b[q][m] = fmaf(w0, av[q].x, h1b[q][m]);
+              h1b[q][m] = fmaf(w1, av[q].y, h1b[q][m]);
+              h1b[q][m] = fmaf(w2, av[q].z, h1b[q][m]);
+              h1b[q][m] = fmaf(w3, av[q].w, h1b[q][m]);
+            }
           }
         }
-        const float4 vgi = *reinterpret_cast<const float4 *>(vg + 4 * i);
-        const float z[6] = {xp[3], xp[4], xp[5], xp[6], vgi.z, vgi.w};
-        float zb[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        float ub[2] = {0.0f, 0.0f};
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          const float h1 = h1row[lane + 32 * m];
-          const float a1b = ACT == 1 ? h1b[m] : h1b[m] * (1.0f - h1 * h1);
-          gb1[m] += a1b;
+        for (int q = 0; q < SPW; ++q) {
+          const float *xp = xs[q] + 8 * i;
+          const float4 vgi = *reinterpret_cast<const float4 *>(vg[q] + 4 * i);
+          const float z[6] = {xp[3], xp[4], xp[5], xp[6], vgi.z, vgi.w};
+          float zb[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            gW1[m][q] = fmaf(a1b, z[q], gW1[m][q]);
-            zb[q] = fmaf(W1r[m][q], a1b, zb[q]);
+          for (int m = 0; m < M; ++m) {
+            const float h1 = hs1[q][i * H + lane + 32 * m];
+            const float a1b = ACT == 1 ? h1b[q][m] : h1b[q][m] * (1.0f - h1 * h1);
+            gb1[m] += a1b;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              gW1[m][c] = fmaf(a1b, z[c], gW1[m][c]);
+              zb[c] = fmaf(W1r[m][c], a1b, zb[c]);
+            }
           }
-        }
 #pragma unroll
-        for (int q = 0; q < 6; ++q) zb[q] = warp_sum(zb[q]);
+          for (int c = 0; c < 6; ++c) zb[c] = warp_sum(zb[c]);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) xbp[3 + q] += zb[q];
-        // the clamp g passes the slope inside [u_min, u_max]; the control-cost term
-        // gamma u' Sigma^-1 v adds gamma u/sigma^2 to dL/dv and gamma v/sigma^2 to dL/du
-        float vb0 = (vgi.x >= p.umin0 && vgi.x <= p.umax0) ? zb[4] : 0.0f;
-        float vb1 = (vgi.y >= p.umin1 && vgi.y <= p.umax1) ? zb[5] : 0.0f;
-        float ub0 = 0.0f, ub1 = 0.0f;
-        if (p.gamma != 0.0f) {
-          const float u0 = __ldg(p.U + 2 * t), u1 = __ldg(p.U + 2 * t + 1);
-          const float sg = Sbar * p.gamma;
-          vb0 = fmaf(sg * u0, p.inv_sig2_0, vb0);
-          vb1 = fmaf(sg * u1, p.inv_sig2_1, vb1);
-          ub0 = sg * vgi.x * p.inv_sig2_0;
-          ub1 = sg * vgi.y * p.inv_sig2_1;
-        }
-        if (imp) {
-          ub0 += vb0;
-          ub1 += vb1;
+          for (int c = 0; c < 4; ++c) xbp[q][3 + c] += zb[c];
+          // the clamp g passes the slope inside [u_min, u_max]; the control-cost term
+          // gamma u' Sigma^-1 v adds gamma u/sigma^2 to dL/dv and gamma v/sigma^2 to dL/du
+          float vb0 = (vgi.x >= p.umin0 && vgi.x <= p.umax0) ? zb[4] : 0.0f;
+          float vb1 = (vgi.y >= p.umin1 && vgi.y <= p.umax1) ? zb[5] : 0.0f;
+          float ub0 = 0.0f, ub1 = 0.0f;
+          if (p.gamma != 0.0f) {
+            const float u0 = __ldg(p.U + 2 * t), u1 = __ldg(p.U + 2 * t + 1);
+            const float sg = Sbar[q] * p.gamma;
+            vb0 = fmaf(sg * u0, p.inv_sig2_0, vb0);
+            vb1 = fmaf(sg * u1, p.inv_sig2_1, vb1);
+            ub0 = sg * vgi.x * p.inv_sig2_0;
+            ub1 = sg * vgi.y * p.inv_sig2_1;
+          }
+          if (impq[q]) {
+            ub0 += vb0;
+            ub1 += vb1;
+          }
+          ub[0] += ub0;
+          ub[1] += ub1;
+#pragma unroll
+          for (int c = 0; c < 7; ++c) xb[q][c] = xbp[q][c];
         }
         if (lane == 0) {
-          ub_s[warp * 2 * T + 2 * t] = ub0;
-          ub_s[warp * 2 * T + 2 * t + 1] = ub1;
+          ub_s[warp * 2 * T + 2 * t] = ub[0];
+          ub_s[warp * 2 * T + 2 * t + 1] = ub[1];
         }
-#pragma unroll
-        for (int q = 0; q < 7; ++q) xb[q] = xbp[q];
       }
     }
     __syncthreads();
     // (d) W2 gradient: sum over this CTA's active samples and the segment's steps of a2bar h1^T
-    for (int w = 0; w < NW; ++w) {
-      const int kw = blockIdx.x * NW + w;
-      if (kw >= K || __ldg(a.w + kw) == 0.0f) continue;
-      const float *h1w = wreg + w * wf + 8 * (every + 1) + 8 * every;
+    for (int sidx = 0; sidx < SC; ++sidx) {
+      const int ks = blockIdx.x * SC + sidx;
+      if (ks >= K || __ldg(a.w + ks) == 0.0f) continue;
+      const float *h1w = sreg + sidx * sf + 8 * (every + 1) + 8 * every;
       const float *a2w = h1w + H * every;
       for (int i = 0; i < nst; ++i) {
         const float4 av = *reinterpret_cast<const float4 *>(a2w + i * H + TJ * jb);
         const float ar[4] = {av.x, av.y, av.z, av.w};
         float hr[TI];
-        if constexpr (TI == 4) {
-          const float4 hv = *reinterpret_cast<const float4 *>(h1w + i * H + TI * ib);
-          hr[0] = hv.x; hr[1] = hv.y; hr[2] = hv.z; hr[3] = hv.w;
+        if constexpr (TI == 2) {
+          const float2 hv = *reinterpret_cast<const float2 *>(h1w + i * H + TI * ib);
+          hr[0] = hv.x; hr[1] = hv.y;
         } else {
 #pragma unroll
-          for (int c = 0; c < TI; ++c) hr[c] = h1w[i * H + TI * ib + c];
+          for (int c4 = 0; c4 < TI; c4 += 4) {
+            const float4 hv = *reinterpret_cast<const float4 *>(h1w + i * H + TI * ib + c4);
+            hr[c4] = hv.x; hr[c4 + 1] = hv.y; hr[c4 + 2] = hv.z; hr[c4 + 3] = hv.w;
+          }
         }
 #pragma unroll
         for (int r = 0; r < TJ; ++r)
@@ -461,7 +519,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
       for (int m = 0; m < M; ++m) {
         const int j = lane + 32 * m;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) rec_s[net_off_W1(H) + j * 6 + q] += gW1[m][q];
+        for (int c = 0; c < 6; ++c) rec_s[net_off_W1(H) + j * 6 + c] += gW1[m][c];
         rec_s[net_off_b1(H) + j] += gb1[m];
         rec_s[net_off_b2(H) + j] += gb2[m];
 #pragma unroll
@@ -471,11 +529,11 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
 #pragma unroll
         for (int o = 0; o < 4; ++o) rec_s[net_off_b3(H) + o] += gb3[o];
       }
-      // cost multipliers: Sbar times the sample's summed components
+      // cost multipliers: the Sbar-weighted components, summed over the lanes' steps
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
-        const float c = warp_sum(compacc[o]);
-        if (lane == 0) rec_s[nf + o] += Sbar * c;
+        const float c = warp_sum(gcw[o]);
+        if (lane == 0) rec_s[nf + o] += c;
       }
     }
     __syncthreads();
@@ -485,9 +543,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
 #pragma unroll
     for (int c = 0; c < TI; ++c) rec_s[net_off_W2(H) + (TJ * jb + r) * H + TI * ib + c] = gW2[r][c];
   for (int e = threadIdx.x; e < 2 * T; e += NW * 32) {
-    float s = 0.0f;
-    for (int w = 0; w < NW; ++w) s += ub_s[w * 2 * T + e];
-    rec_s[nf + 4 + e] = s;
+    float sum = 0.0f;
+    for (int w = 0; w < NW; ++w) sum += ub_s[w * 2 * T + e];
+    rec_s[nf + 4 + e] = sum;
   }
   __syncthreads();
   float *rec = a.part + (size_t)blockIdx.x * nrec;
@@ -541,7 +599,7 @@ cudaError_t launch_bwd(const AdjParams &a, int n_cta, size_t smem, cudaStream_t 
 
 }  // namespace
 
-int adj_num_ctas(int K) { return (K + kAdjWarps - 1) / kAdjWarps; }
+int adj_num_ctas(int K) { return (K + kAdjSamples - 1) / kAdjSamples; }
 size_t adj_part_floats(int K, int H, int T_max) { return (size_t)adj_num_ctas(K) * adj_rec_floats(H, T_max); }
 size_t adj_smem_bytes(int H, int every, int T) { return sizeof(float) * adj_smem_floats(H, every, T); }
 

@@ -241,3 +241,37 @@ def test_large_K_single_instance_thread_per_sample_path():
     stats = ctl.stats()
     assert stats[0] == pytest.approx(S.min(), rel=1e-6)
     assert stats[4] == 8192
+
+
+def test_maximum_horizon():
+    """T = ITMPC_MAX_T = 512 (the largest horizon), small K: costs and stage-wise U'."""
+    K, T = 48, 512
+    params, tmap, layers = G.small_workload(K=K, T=T)
+    ctl = G.controller(params, tmap, layers)
+    P = oracle_for(params, tmap, layers)
+    x0 = problems.x0_for(tmap, speed=2.0)
+    U = inputs.nominal_controls(T, seed=3, scale=0.2)
+    Uo, w, S, st = G.run(ctl, x0, U, 1)
+    assert st == 0
+    S_ref, margins = oracle.rollout_many(P, x0, U, 1)
+    check_costs(S, S_ref, margins)
+    check_stagewise(P, 1, U, Uo, w, S, params["sigma"])
+    ctl.close()
+
+
+def test_million_samples_sampled():
+    """K = 2^20 on one instance (thread-per-sample kernels, 8192 work units): sampled costs against
+    the oracle, U' and the weights recomputed by the oracle from all of the GPU's costs."""
+    K, T = 1 << 20, 16
+    params, tmap, layers = G.small_workload(K=K, T=T)
+    ctl = G.controller(params, tmap, layers)
+    P = oracle_for(params, tmap, layers)
+    x0 = problems.x0_for(tmap, speed=3.0)
+    U = inputs.nominal_controls(T, seed=5, scale=0.2)
+    Uo, w, S, st = G.run(ctl, x0, U, 9)
+    assert st == 0
+    ks = np.concatenate([np.arange(8), np.random.default_rng(2).choice(K, 56, replace=False), [K - 1]])
+    S_ref, margins = oracle.rollout_many(P, x0, U, 9, ks)
+    check_costs(S[ks], S_ref, margins)
+    check_stagewise(P, 9, U, Uo, w, S, params["sigma"])
+    ctl.close()
