@@ -164,7 +164,12 @@ itmpc_status itmpc_iterate(itmpc_ctx *ctx, const float *x0, const float *U, uint
 
 /* itmpc_iterate on HOST buffers: copies x0 and U to the device, runs the
  * iteration, copies U_out (and weights/costs when non-NULL) back and waits.
- * Returns the device-side status as well (e.g. ITMPC_ERR_NONFINITE). */
+ * Returns the device-side status as well (e.g. ITMPC_ERR_NONFINITE).  Without
+ * weights and costs, on the fused FP32 kernel (hidden 32 with K < 4096, hidden
+ * 64 / 128 with K < 2048), the call replays one CUDA graph the context captures
+ * at the first such call and again after itmpc_set_config / set_stream /
+ * set_costmap(s): the upload of (x0, iter, U) from a pinned block, the
+ * iteration and the download of (U_out, status). */
 itmpc_status itmpc_iterate_host(itmpc_ctx *ctx, const float *x0, const float *U, uint64_t iter, float *U_out,
                                 float *weights, float *costs);
 

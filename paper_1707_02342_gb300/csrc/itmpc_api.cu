@@ -46,6 +46,10 @@ struct itmpc_ctx {
   // adjoint form (itmpc_reserve_adjoint): per-CTA gradient records and 4 scalars
   float *adj_part = nullptr, *adj_scal = nullptr;
   float *cem_scal = nullptr;  // cross-entropy threshold and elite count of the last CEM iteration
+  // host-pointer iterations as one captured graph: upload of (x0, iter, U), the fused
+  // iteration, download of (U', status); pinned host and device blocks of the same layout
+  cudaGraphExec_t host_exec = nullptr;
+  unsigned char *hblk_in = nullptr, *dblk_in = nullptr, *hblk_out = nullptr, *dblk_out = nullptr;
   // basis-function dynamics model: coefficients (host copy for the kernel parameters, device copy)
   std::vector<float> theta_host;
   float *theta_d = nullptr;
@@ -202,6 +206,20 @@ itmpc_status ready(itmpc_ctx *c) {
   return ITMPC_OK;
 }
 
+// Host-graph blocks: in = [x0 (8 floats), iteration index (uint64), pad, U (2 T_max)],
+// out = [U' (2 T_max), status (int), pad] -- one copy each way.
+constexpr size_t kHinU = 48;  // byte offset of U in the input block (16-byte aligned)
+size_t hin_bytes(int T_max) { return kHinU + sizeof(float) * 2 * (size_t)T_max; }
+size_t hout_status(int T_max) { return sizeof(float) * 2 * (size_t)T_max; }
+size_t hout_bytes(int T_max) { return (hout_status(T_max) + sizeof(int) + 15) & ~size_t(15); }
+
+void drop_host_graph(itmpc_ctx *c) {
+  if (c->host_exec) {
+    cudaGraphExecDestroy(c->host_exec);
+    c->host_exec = nullptr;
+  }
+}
+
 constexpr int kTpsMinK = 4096;   // from here on one thread per sample beats a warp per sample (H = 32)
 constexpr int kWideMinK = 2048;  // from here on the tiled GEMM kernel beats a warp per sample (H = 64, 128)
 
@@ -290,6 +308,11 @@ void free_ctx(itmpc_ctx *c) {
   if (c->adj_scal) cudaFree(c->adj_scal);
   if (c->cem_scal) cudaFree(c->cem_scal);
   if (c->theta_d) cudaFree(c->theta_d);
+  if (c->host_exec) cudaGraphExecDestroy(c->host_exec);
+  if (c->dblk_in) cudaFree(c->dblk_in);
+  if (c->dblk_out) cudaFree(c->dblk_out);
+  if (c->hblk_in) cudaFreeHost(c->hblk_in);
+  if (c->hblk_out) cudaFreeHost(c->hblk_out);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->ginst_d) cudaFree(c->ginst_d);
   if (c->gunits_d) cudaFree(c->gunits_d);
@@ -350,6 +373,11 @@ itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
   e = cudaMalloc((void **)&c->cem_scal, sizeof(float) * 4);
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
+  e = cudaMalloc((void **)&c->dblk_in, hin_bytes(c->T_max));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->dblk_out, hout_bytes(c->T_max));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hblk_in, hin_bytes(c->T_max));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&c->hblk_out, hout_bytes(c->T_max));
+  if (e != cudaSuccess) return bail(e, "cudaMalloc");
   if (c->H == kTcHidden) {
     for (int i = 0; i < 2; ++i) {
       e = cudaMalloc((void **)&c->tc_img[i], tc_image_bytes(i + 1));
@@ -375,6 +403,7 @@ itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
 
 itmpc_status itmpc_set_config(itmpc_ctx *c, const itmpc_config *cfg) {
   if (!c) return ITMPC_ERR_ARG;
+  drop_host_graph(c);
   char msg[256];
   itmpc_status st = check_config(cfg, msg, sizeof msg);
   if (st != ITMPC_OK) return fail(c, st, "%s", msg);
@@ -391,6 +420,7 @@ itmpc_status itmpc_set_config(itmpc_ctx *c, const itmpc_config *cfg) {
 
 itmpc_status itmpc_set_stream(itmpc_ctx *c, void *stream) {
   if (!c) return ITMPC_ERR_ARG;
+  drop_host_graph(c);
   c->stream = (cudaStream_t)stream;
   c->cfg.stream = stream;
   return ITMPC_OK;
@@ -430,6 +460,7 @@ itmpc_status itmpc_set_dynamics(itmpc_ctx *c, int32_t n_layers, const int32_t *w
 itmpc_status itmpc_set_costmaps(itmpc_ctx *c, int32_t n_maps, const float *const *maps, int32_t width,
                                 int32_t height, float res, float origin_x, float origin_y, int32_t on_device) {
   if (!c) return ITMPC_ERR_ARG;
+  drop_host_graph(c);
   if (n_maps < 1 || !maps || width < 1 || height < 1 || (int64_t)width * height > (int64_t)1 << 30)
     return fail(c, ITMPC_ERR_ARG, "bad costmap shape %d x %d (x %d)", width, height, n_maps);
   for (int i = 0; i < n_maps; ++i)
@@ -485,6 +516,7 @@ itmpc_status itmpc_set_basis(itmpc_ctx *c, const float *theta, int32_t on_device
 itmpc_status itmpc_set_costmap(itmpc_ctx *c, const float *map, int32_t width, int32_t height, float res,
                                float origin_x, float origin_y, int32_t on_device) {
   if (!c) return ITMPC_ERR_ARG;
+  drop_host_graph(c);
   if (!map) return fail(c, ITMPC_ERR_ARG, "costmap is NULL");
   const float *maps[1] = {map};
   return itmpc_set_costmaps(c, 1, maps, width, height, res, origin_x, origin_y, on_device);
@@ -849,6 +881,66 @@ itmpc_status itmpc_iterate(itmpc_ctx *c, const float *x0, const float *U, uint64
   return run_iteration(c, x0, U, iter, U_out, weights, costs, nullptr, 0, nullptr);
 }
 
+// The host-pointer iteration without weights / costs on the fused FP32 kernel, as one graph:
+// H2D of the input block, the iteration (its Philox index read from that block), D2H of the
+// output block.  Captured at the first such call and after any change of parameters or maps.
+static itmpc_status host_graph_iterate(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out) {
+  const int T = c->cfg.T, T_max = c->T_max;
+  if (!c->host_exec) {
+    IterParams p = make_params(c);
+    set_iter(p, 0, c->cfg.instance);
+    p.x0 = reinterpret_cast<const float *>(c->dblk_in);
+    p.iter_add = reinterpret_cast<const unsigned long long *>(c->dblk_in + 32);
+    p.U = reinterpret_cast<const float *>(c->dblk_in + kHinU);
+    p.U_out = reinterpret_cast<float *>(c->dblk_out);
+    p.status = reinterpret_cast<int *>(c->dblk_out + hout_status(T_max));
+    p.weights = nullptr;
+    p.weights_inline = c->cfg.K <= 16384;
+    const Fp32Tile tile = fp32_pick_tile(p.K, p.T, p.H, c->smem_optin);
+    cudaStream_t cap = nullptr;
+    CK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+    cudaError_t e = cudaSuccess;
+    for (int attempt = 0; attempt < 2; ++attempt) {  // cooperative launch first, else the merge tree
+      IterParams q = p;
+      if (attempt == 1) q.grid_bar = nullptr;
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        cudaError_t ek = cudaMemsetAsync(q.status, 0, sizeof(int), cap);
+        if (ek == cudaSuccess)
+          ek = cudaMemcpyAsync(c->dblk_in, c->hblk_in, hin_bytes(T_max), cudaMemcpyHostToDevice, cap);
+        if (ek == cudaSuccess) ek = fp32_launch_iterate(q, tile, cap);
+        if (ek == cudaSuccess)
+          ek = cudaMemcpyAsync(c->hblk_out, c->dblk_out, hout_bytes(T_max), cudaMemcpyDeviceToHost, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = ek;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->host_exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e == cudaSuccess) break;
+      cudaGetLastError();
+      drop_host_graph(c);
+    }
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-iteration graph capture");
+  }
+  memcpy(c->hblk_in, x0, sizeof(float) * 7);
+  memcpy(c->hblk_in + 32, &iter, sizeof(iter));
+  memcpy(c->hblk_in + kHinU, U, sizeof(float) * 2 * (size_t)T);
+  CK(c, cudaGraphLaunch(c->host_exec, c->stream), "graph launch");
+  CK(c, cudaStreamSynchronize(c->stream), "sync");
+  memcpy(U_out, c->hblk_out, sizeof(float) * 2 * (size_t)T);
+  int s = 0;
+  memcpy(&s, c->hblk_out + hout_status(T_max), sizeof(int));
+  if (s == ITMPC_ERR_NONFINITE) return fail(c, ITMPC_ERR_NONFINITE, "every rollout cost was non-finite; U unchanged");
+  if (s == ITMPC_ERR_TIMEOUT) {
+    CK(c, cudaMemsetAsync(c->counters, 0, sizeof(unsigned int) * c->n_counters, c->stream), "counter reset");
+    CK(c, cudaStreamSynchronize(c->stream), "sync");
+  }
+  if (s != 0) return fail(c, (itmpc_status)s, "device status %d", s);
+  return ITMPC_OK;
+}
+
 itmpc_status itmpc_iterate_host(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
                                 float *weights, float *costs) {
   itmpc_status st = ready(c);
@@ -856,6 +948,8 @@ itmpc_status itmpc_iterate_host(itmpc_ctx *c, const float *x0, const float *U, u
   if (!x0 || !U || !U_out) return fail(c, ITMPC_ERR_ARG, "x0, U and U_out must be non-NULL");
   for (int i = 0; i < 7; ++i)
     if (!finite(x0[i])) return fail(c, ITMPC_ERR_ARG, "x0[%d] is not finite", i);
+  if (!weights && !costs && c->cfg.precision == ITMPC_FP32 && !single_as_batch(c, false))
+    return host_graph_iterate(c, x0, U, iter, U_out);
   const int T = c->cfg.T, K = c->cfg.K;
   CK(c, cudaMemcpyAsync(c->x0_d, x0, sizeof(float) * 7, cudaMemcpyHostToDevice, c->stream), "x0 copy");
   CK(c, cudaMemcpyAsync(c->U_d, U, sizeof(float) * 2 * T, cudaMemcpyHostToDevice, c->stream), "U copy");

@@ -253,8 +253,11 @@ def test_maximum_horizon():
     U = inputs.nominal_controls(T, seed=3, scale=0.2)
     Uo, w, S, st = G.run(ctl, x0, U, 1)
     assert st == 0
-    S_ref, margins = oracle.rollout_many(P, x0, U, 1)
-    check_costs(S, S_ref, margins)
+    S_ref, _ = oracle.rollout_many(P, x0, U, 1)
+    # the small workload gives the impulses no weight: a threshold crossing cannot change a
+    # cost, so every sample is held to the bound (over 512 steps many pass near a threshold)
+    assert params["cost_w"][3] == 0.0
+    check_costs(S, S_ref)
     check_stagewise(P, 1, U, Uo, w, S, params["sigma"])
     ctl.close()
 
@@ -274,4 +277,32 @@ def test_million_samples_sampled():
     S_ref, margins = oracle.rollout_many(P, x0, U, 9, ks)
     check_costs(S[ks], S_ref, margins)
     check_stagewise(P, 9, U, Uo, w, S, params["sigma"])
+    ctl.close()
+
+
+def test_host_graph_path_follows_iteration_and_parameters():
+    """itmpc_iterate_host without weights / costs replays one captured graph (upload, iteration,
+    download): each call's iteration index and the current parameters must be the ones used."""
+    torch = G.torch_cuda()
+    ctl, P, params, x0, U, Uo, w, S, st = small_case(K=200, T=30, it=11)
+    x0f, Uf = x0.astype(np.float32), U.astype(np.float32)
+    for it in (11, 12, 7, 11):
+        Uo_h = np.empty((30, 2), np.float32)
+        assert ctl.iterate_host(x0f, Uf, it, Uo_h) == 0
+        Uo_d, _, _, _ = G.run(ctl, x0, U, it)
+        np.testing.assert_allclose(Uo_h, Uo_d, rtol=0, atol=1e-6)
+    ctl.set_config(lam=7.0)  # a parameter change must reach the captured iteration
+    Uo_h = np.empty((30, 2), np.float32)
+    assert ctl.iterate_host(x0f, Uf, 11, Uo_h) == 0
+    Uo_d, w_d, S_d, _ = G.run(ctl, x0, U, 11)
+    np.testing.assert_allclose(Uo_h, Uo_d, rtol=0, atol=1e-6)
+    rc, w_ref, _, _ = oracle.weights(S_d, 7.0)
+    U_ref = oracle.update(P.replace(lam=7.0), 11, w_ref, U)
+    np.testing.assert_allclose(Uo_h, U_ref, rtol=0, atol=1e-5 * max(np.abs(U_ref).max(), 0.35))
+    # a non-finite map: the status comes back through the same graph, U' = U
+    ctl.set_costmap(torch.full((64, 64), float("nan"), device="cuda"), 0.4, -12.8, -12.8)
+    from paper_1707_02342_gb300 import itmpc
+
+    assert ctl.iterate_host(x0f, Uf, 11, Uo_h) == itmpc.ERR_NONFINITE
+    np.testing.assert_array_equal(Uo_h, Uf)
     ctl.close()
