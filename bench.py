@@ -152,9 +152,19 @@ def cpu_oracle_rate(seconds: float = 10.0, min_iters: int = 2):
         rc, U64, _, _ = oracle.iterate(P, x0, U64, n)
         n += 1
     dt = time.perf_counter() - t0
+    # the same oracle on one host core, a few iterations
+    P1 = P.replace(n_threads=1)
+    U1 = U.astype(np.float64)
+    n1, t1 = 0, time.perf_counter()
+    while n1 < 1 or time.perf_counter() - t1 < min(3.0, seconds / 3):
+        rc, U1, _, _ = oracle.iterate(P1, x0, U1, n1)
+        n1 += 1
+    d1 = time.perf_counter() - t1
     return {"value": K_WORK * T_WORK * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} full iterations of K={K_WORK}, T={T_WORK} (FP64 C oracle, OpenMP over samples) "
-                      f"in {dt:.1f} s"}, dt / n
+                      f"in {dt:.1f} s",
+            "single_core": {"value": K_WORK * T_WORK * n1 / d1, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} full iterations on one core in {d1:.1f} s"}}, dt / n
 
 
 def measure_batched(params, layers, steps: int = 10, warmup: int = 3):

@@ -190,7 +190,7 @@ itmpc_status itmpc_get_stats(itmpc_ctx *ctx, float out[ITMPC_STATS_LEN]);
 itmpc_status itmpc_set_costmaps(itmpc_ctx *ctx, int32_t n_maps, const float *const *maps, int32_t width,
                                 int32_t height, float res, float origin_x, float origin_y, int32_t on_device);
 
-/* One independent MPC problem of a batched iteration (SURVEY config "batching").
+/* One independent MPC problem of a batched iteration.
  * Every instance shares the context's network and parameters (lambda, sigma,
  * costs, seed); it has its own size, costmap, start state and nominal
  * controls.  Pointers are device pointers; weights, costs and stats may be
