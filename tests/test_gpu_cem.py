@@ -91,3 +91,16 @@ def test_cem_working_size():
     assert st == 0
     assert check(P, U, 11, 0.8, Uo, w, S, params["sigma"]) == 410
     ctl.close()
+
+
+def test_cem_keys_from_global_memory():
+    # K above the shared-memory staging limit of the select kernel (11264 keys)
+    K, T = 20000, 12
+    params, tmap, layers = G.small_workload(K=K, T=T)
+    ctl = G.controller(params, tmap, layers)
+    P = oracle_for(params, tmap, layers)
+    U = inputs.nominal_controls(T, seed=3, scale=0.3)
+    Uo, w, S, st = run_cem(ctl, problems.x0_for(tmap, speed=3.0), U, 4, 0.8)
+    assert st == 0
+    assert check(P, U, 4, 0.8, Uo, w, S, params["sigma"]) == 4000
+    ctl.close()
