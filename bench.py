@@ -167,7 +167,7 @@ def cpu_oracle_rate(seconds: float = 10.0, min_iters: int = 2):
                             "sample": f"{n1} full iterations on one core in {d1:.1f} s"}}, dt / n
 
 
-def measure_batched(params, layers, steps: int = 10, warmup: int = 3):
+def measure_batched(params, layers, steps: int = 50, warmup: int = 10):
     """The batching form: 256 independent instances (K in {512..8192}, T in {40, 60, 100, 150},
     8 seeded 1024 x 1024 spline maps; instance table seed 7) in one itmpc_iterate_batch call."""
     import numpy as np
@@ -270,7 +270,7 @@ def _controller(K, T, H, tmap, layers, params, **kw):
     return ctl
 
 
-def measure_precision(params, flush, cores, steps: int = 20, warmup: int = 3):
+def measure_precision(params, flush, cores, steps: int = 50, warmup: int = 10):
     """The precision form: K = 16384, T = 100, 6->128->128->4 network, FP32 vs BF16 vs FP8 (tcgen05),
     each timed through itmpc_iterate and compared with the FP64 oracle run on every sample."""
     import numpy as np
@@ -318,7 +318,7 @@ def measure_precision(params, flush, cores, steps: int = 20, warmup: int = 3):
     return out
 
 
-def measure_adjoint(params, flush, cores, steps: int = 20, warmup: int = 3, every: int = 10):
+def measure_adjoint(params, flush, cores, steps: int = 50, warmup: int = 10, every: int = 10):
     """The adjoint form: K = 4096, T = 100, 6->64->64->4, checkpoints every 10 steps; forward + backward
     time next to the plain iteration and to central differences, gradient error vs the FP64 oracle."""
     import numpy as np
@@ -436,7 +436,7 @@ def measure_cem(tmap, layers, x0, U, params, flush, steps: int = 200, warmup: in
             "value": K_WORK * T_WORK / (ms_cem * 1e-3), "unit": UNIT, "gpu_launches_per_step": 3}
 
 
-def measure_basis(tmap, params, flush, steps: int = 50, warmup: int = 5):
+def measure_basis(tmap, params, flush, steps: int = 50, warmup: int = 10):
     """The basis-function dynamics model (25 basis functions, synthetic Theta, seed 5) on the working
     map, T = 100: one iteration at K = 2048 and at K = 65536 (thread-per-sample kernels)."""
     import torch
