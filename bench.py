@@ -461,6 +461,37 @@ def measure_basis(tmap, params, flush, steps: int = 50, warmup: int = 10):
     return out
 
 
+def measure_update_hbm(params, layers, flush, steps: int = 50, warmup: int = 10):
+    """The control law from materialised noise (itmpc_update_from_noise), the HBM-bound form of the
+    update: eps of the batched workload's size (K = 776192 samples x T = 100 steps, 621 MB) streamed
+    once per call, weights from a real iteration on the working map."""
+    import torch
+
+    from paper_1707_02342_gb300 import inputs
+
+    K, T = 776192, 100
+    tmap = inputs.track_costmap(inputs.spline_centerline(1), 1024, 0.1, 2.5)
+    ctl = _controller(K, T, H_WORK, tmap, layers, params)
+    x0 = inputs.start_state(tmap.centerline)
+    x0[4] = 4.0
+    x = torch.tensor(x0, device="cuda")
+    U = torch.tensor(inputs.nominal_controls(T, seed=9, scale=0.2), device="cuda")
+    Uo, w, S = torch.empty_like(U), torch.empty(K, device="cuda"), torch.empty(K, device="cuda")
+    ctl.iterate(x, U, 3, Uo, w, S)
+    eps = torch.empty((K, T, 2), device="cuda")
+    ctl.noise(3, eps)
+    U2 = torch.empty_like(U)
+    med, mean = _timed(lambda: ctl.update_from_noise(eps, w, U, U2), steps, warmup, flush)
+    assert ctl.read_status() == 0
+    err = float((U2 - Uo).abs().max())
+    ctl.close()
+    nbytes = K * T * 8 + 2 * K * 4 + 3 * 2 * T * 4  # eps once, weights twice, U / records / U'
+    return {"workload": f"U' = sum_k w_k v_k from materialised noise, K={K} T={T} ({K * T * 8 / 1e6:.0f} MB)",
+            "ms_per_call": mean, "ms_median": med, "algorithmic_bytes": nbytes,
+            "achieved_gbs": nbytes / (mean * 1e-3) / 1e9, "max_abs_diff_vs_fused_update": err,
+            "gpu_launches_per_call": 2}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     d = json.load(open(path)) if os.path.exists(path) else {}
@@ -641,6 +672,11 @@ def run_ours(args, rank, world, local_rank):
         line["forms"]["closed_loop"] = measure_closed_loop(tmap, layers, x0, U, params, flush)
         line["forms"]["cem"] = measure_cem(tmap, layers, x0, U, params, flush)
         line["forms"]["basis"] = measure_basis(tmap, params, flush)
+        uh = measure_update_hbm(params, layers, flush)
+        hbm = pk.get("hbm_gbs", 6800.0)
+        uh["roofline"] = {"bound": "hbm", "achieved": uh["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                          "frac": uh["achieved_gbs"] / hbm, "peak_note": "measured copy bandwidth"}
+        line["forms"]["update_from_noise"] = uh
         ad = measure_adjoint(params, flush, cores)
         ad["bwd_roofline"]["peak"] = peak_tflops
         ad["bwd_roofline"]["frac"] = ad["bwd_roofline"]["achieved"] / peak_tflops
@@ -668,6 +704,8 @@ def run_only(args):
         out = measure_batched(params, layers, steps=steps, warmup=warm)
     elif args.only == "precision":
         out = measure_precision(params, flush, cores, steps=steps, warmup=warm)
+    elif args.only == "update_from_noise":
+        out = measure_update_hbm(params, layers, flush, steps=steps, warmup=warm)
     elif args.only == "basis":
         out = measure_basis(tmap, params, flush, steps=steps, warmup=warm)
     elif args.only == "cem":
@@ -688,7 +726,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / precision / adjoint forms")
-    ap.add_argument("--only", choices=["batched", "precision", "adjoint", "closed_loop", "cem", "basis"], default=None,
+    ap.add_argument("--only", choices=["batched", "precision", "adjoint", "closed_loop", "cem", "basis", "update_from_noise"], default=None,
                     help="run one form alone and print its JSON (profiling runs); not a benchmark line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

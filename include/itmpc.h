@@ -272,6 +272,19 @@ itmpc_status itmpc_batch_graph_launch(itmpc_ctx *ctx);
 /* Release the captured graph (waits for the context's stream); no-op without one. */
 itmpc_status itmpc_batch_graph_destroy(itmpc_ctx *ctx);
 
+/* The control law of Sec. III-D from materialised noise: U_out[t] = sum_k w_k v_{k,t}
+ * = U[t] sum_{k < (1 - alpha) K} w_k + sum_k w_k eps[k][t], for K and T of the
+ * context's configuration.  eps: device, K x T x 2 (as itmpc_noise writes it),
+ * weights: device, K (normalised), U, U_out: device T x 2 (U_out may not alias U).
+ * The streamed form of the update for callers that hold their noise in memory
+ * (K T 8 bytes read once); the iterations themselves never write eps.  eps must
+ * be 8-byte aligned; with even T and a 16-byte aligned eps the rows are read with
+ * 16-byte loads.  Deterministic (fixed summation order).  Asynchronous.
+ * Errors: ITMPC_ERR_ARG (NULL pointer, U_out == U, eps not 8-byte aligned),
+ * ITMPC_ERR_CUDA. */
+itmpc_status itmpc_update_from_noise(itmpc_ctx *ctx, const float *eps, const float *weights, const float *U,
+                                     float *U_out);
+
 /* One iteration of the paper's comparison controller, cross-entropy MPC: the
  * same rollouts and costs, the weights of Alg. 3 -- zeta = round(K (1 - delta)),
  * Z = the zeta-th smallest finite cost, w_k = 1/|E| on the elite set
@@ -311,7 +324,8 @@ itmpc_status itmpc_control_graph_launch(itmpc_ctx *ctx);
 itmpc_status itmpc_control_graph_destroy(itmpc_ctx *ctx);
 
 /* Diagnostics for stage-wise checks.
- * itmpc_noise: eps of iteration iter for every (k, t), device K x T x 2.
+ * itmpc_noise: eps of iteration iter for every (k, t), device K x T x 2,
+ *   8-byte aligned (ITMPC_ERR_ARG otherwise).
  * itmpc_rollout_states: the full rollout of samples 0..n-1 (device,
  *   n x (T+1) x 7, states x_0..x_T) plus all costs (device, K); n <= K. */
 itmpc_status itmpc_noise(itmpc_ctx *ctx, uint64_t iter, float *eps);

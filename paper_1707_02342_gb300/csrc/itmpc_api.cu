@@ -46,6 +46,8 @@ struct itmpc_ctx {
   // adjoint form (itmpc_reserve_adjoint): per-CTA gradient records and 4 scalars
   float *adj_part = nullptr, *adj_scal = nullptr;
   float *cem_scal = nullptr;  // cross-entropy threshold and elite count of the last CEM iteration
+  float *wsum_part = nullptr;  // records of the update from materialised noise
+  int sms = 0;
   // host-pointer iterations as one captured graph: upload of (x0, iter, U), the fused
   // iteration, download of (U', status); pinned host and device blocks of the same layout
   cudaGraphExec_t host_exec = nullptr;
@@ -307,6 +309,7 @@ void free_ctx(itmpc_ctx *c) {
   if (c->adj_part) cudaFree(c->adj_part);
   if (c->adj_scal) cudaFree(c->adj_scal);
   if (c->cem_scal) cudaFree(c->cem_scal);
+  if (c->wsum_part) cudaFree(c->wsum_part);
   if (c->theta_d) cudaFree(c->theta_d);
   if (c->host_exec) cudaGraphExecDestroy(c->host_exec);
   if (c->dblk_in) cudaFree(c->dblk_in);
@@ -372,6 +375,9 @@ itmpc_status itmpc_create(const itmpc_config *cfg, itmpc_ctx **out) {
   e = cudaMalloc((void **)&c->status, sizeof(int));
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
   e = cudaMalloc((void **)&c->cem_scal, sizeof(float) * 4);
+  if (e != cudaSuccess) return bail(e, "cudaMalloc");
+  e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->wsum_part, sizeof(float) * wsum_part_floats(c->T_max, c->sms));
   if (e != cudaSuccess) return bail(e, "cudaMalloc");
   e = cudaMalloc((void **)&c->dblk_in, hin_bytes(c->T_max));
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->dblk_out, hout_bytes(c->T_max));
@@ -988,6 +994,7 @@ itmpc_status itmpc_get_stats(itmpc_ctx *c, float out[ITMPC_STATS_LEN]) {
 itmpc_status itmpc_noise(itmpc_ctx *c, uint64_t iter, float *eps) {
   if (!c) return ITMPC_ERR_ARG;
   if (!eps) return fail(c, ITMPC_ERR_ARG, "eps is NULL");
+  if (reinterpret_cast<uintptr_t>(eps) & 7u) return fail(c, ITMPC_ERR_ARG, "eps must be 8-byte aligned");
   IterParams p = make_params(c);
   set_iter(p, iter, c->cfg.instance);
   CK(c, launch_noise(p, eps, c->stream), "noise launch");
@@ -1045,6 +1052,18 @@ itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *part
     }
     U_out[o] = (float)((double)U[o] * (eta_imp / eta) + E / eta);
   }
+  return ITMPC_OK;
+}
+
+itmpc_status itmpc_update_from_noise(itmpc_ctx *c, const float *eps, const float *weights, const float *U,
+                                     float *U_out) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (!eps || !weights || !U || !U_out) return fail(c, ITMPC_ERR_ARG, "eps, weights, U and U_out must be non-NULL");
+  if (U_out == U) return fail(c, ITMPC_ERR_ARG, "U_out may not alias U");
+  if (reinterpret_cast<uintptr_t>(eps) & 7u) return fail(c, ITMPC_ERR_ARG, "eps must be 8-byte aligned");
+  const IterParams p = make_params(c);
+  CK(c, wsum_launch(p.K, p.T, p.n_imp, eps, weights, U, U_out, c->wsum_part, c->sms, c->stream),
+     "materialised-noise update launch");
   return ITMPC_OK;
 }
 

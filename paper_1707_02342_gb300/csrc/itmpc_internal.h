@@ -194,6 +194,11 @@ cudaError_t loop_launch(const LoopItem *items_dev, const LoopItem *item_host, in
 // elite samples' v (p.U, p.U_out, noise counters of p).  zeta0 = round(K (1 - delta)).
 cudaError_t cem_launch(const IterParams &p, int zeta0, const float *S, float *w, float *scal, cudaStream_t s);
 
+// ---- the control law from materialised noise (wsum.cu), the HBM-bound form of the update ----
+size_t wsum_part_floats(int T_max, int sms);
+cudaError_t wsum_launch(int K, int T, int n_imp, const float *eps, const float *w, const float *U, float *U_out,
+                        float *part, int sms, cudaStream_t s);
+
 // ---- adjoint form (iterate_adj.cu): reverse sweep over checkpointed FP32 rollouts ----
 struct AdjParams {
   IterParams p;        // dynamics, costs, noise counters, map, network, U

@@ -73,6 +73,7 @@ SIGNATURES = {
     "itmpc_control_step": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _i32, _vp]),
     "itmpc_iterate_cem": (C.c_int, [_vp, _vp, _vp, _u64, _f, _vp, _vp, _vp]),
     "itmpc_set_basis": (C.c_int, [_vp, _vp, _i32]),
+    "itmpc_update_from_noise": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "itmpc_control_graph_create": (C.c_int, [_vp, _vp, _vp, _u64, _i32, _i32, _vp]),
     "itmpc_control_graph_launch": (C.c_int, [_vp]),
     "itmpc_control_graph_destroy": (C.c_int, [_vp]),
@@ -268,6 +269,10 @@ class Controller:
         end of Alg. 1 per instance (smoothing, applied control into stats[5:7], plant step, warm start)."""
         self._check(self._L.itmpc_batch_graph_create(self._h, len(instances), self._instances(instances),
                                                      closed_loop, smoothing, plant))
+
+    def update_from_noise(self, eps, weights, U, U_out):
+        """U_out = sum_k w_k v_k from materialised noise eps (K, T, 2) (device tensors)."""
+        self._check(self._L.itmpc_update_from_noise(self._h, _dptr(eps), _dptr(weights), _dptr(U), _dptr(U_out)))
 
     def iterate_cem(self, x0, U, it: int, delta: float, U_out, weights=None, costs=None):
         """One cross-entropy MPC iteration (Alg. 3 weights) on device tensors."""

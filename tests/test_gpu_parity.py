@@ -306,3 +306,35 @@ def test_host_graph_path_follows_iteration_and_parameters():
     assert ctl.iterate_host(x0f, Uf, 11, Uo_h) == itmpc.ERR_NONFINITE
     np.testing.assert_array_equal(Uo_h, Uf)
     ctl.close()
+
+
+@pytest.mark.parametrize("K,T,alpha,offset", [(300, 50, 0.2, 0), (100, 300, 0.0, 0), (100000, 20, 0.1, 0),
+                                               (257, 37, 0.1, 0), (300, 50, 0.2, 2)])
+def test_update_from_materialised_noise(K, T, alpha, offset):
+    """itmpc_update_from_noise on itmpc_noise's eps and an iteration's weights reproduces the
+    fused iteration's U' and the oracle's control law (Sec. III-D) from those weights."""
+    torch = G.torch_cuda()
+    params, tmap, layers = G.small_workload(K=K, T=T, alpha_explore=alpha)
+    ctl = G.controller(params, tmap, layers)
+    P = oracle_for(params, tmap, layers)
+    x0 = problems.x0_for(tmap, speed=2.5)
+    U = inputs.nominal_controls(T, seed=6, scale=0.3)
+    Uo, w, S, st = G.run(ctl, x0, U, 5)
+    assert st == 0
+    # offset 2 floats: eps 8- but not 16-byte aligned, read with 8-byte loads (as odd T is)
+    eps = torch.empty(K * T * 2 + offset, device="cuda")[offset:].view(K, T, 2)
+    ctl.noise(5, eps)
+    U_d = torch.tensor(U, device="cuda")
+    w_d = torch.tensor(w, dtype=torch.float32, device="cuda")
+    U2 = torch.empty_like(U_d)
+    ctl.update_from_noise(eps, w_d, U_d, U2)
+    assert ctl.read_status() == 0
+    U2 = U2.double().cpu().numpy()
+    np.testing.assert_allclose(U2, Uo, rtol=0, atol=2e-6 * max(np.abs(Uo).max(), 0.35))
+    U_ref = oracle.update(P, 5, w, U)
+    np.testing.assert_allclose(U2, U_ref, rtol=0, atol=REL * max(np.abs(U_ref).max(), 0.35))
+    from paper_1707_02342_gb300 import itmpc
+
+    with pytest.raises(itmpc.ItmpcError):  # 4-byte aligned eps is refused before any launch
+        ctl.update_from_noise(torch.empty(K * T * 2 + 1, device="cuda")[1:], w_d, U_d, torch.empty_like(U_d))
+    ctl.close()
