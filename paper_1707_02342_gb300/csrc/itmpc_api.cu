@@ -872,6 +872,7 @@ itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst,
 
 itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
                        int states_every) {
+  if (!c) return ITMPC_ERR_ARG;
   return run_batch_tile(c, n, inst, states, n_states, c->tps_tile, states_every);
 }
 

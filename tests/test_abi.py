@@ -61,6 +61,20 @@ def test_null_arguments(L):
     L.itmpc_destroy(None)
 
 
+# entry points whose first argument is not a context, or that return no status
+_NO_CTX = {"itmpc_create", "itmpc_philox4x32_10", "itmpc_tanh_f32", "itmpc_merge_partials", "itmpc_iterate_noalloc",
+           "itmpc_adjoint_ckpt_floats", "itmpc_last_error", "itmpc_status_string", "itmpc_version", "itmpc_destroy"}
+
+
+@pytest.mark.parametrize("name", sorted(n for n in itmpc.SIGNATURES if n not in _NO_CTX))
+def test_every_context_entry_point_rejects_a_null_context(L, name):
+    """A NULL context is refused on the host (ITMPC_ERR_ARG) before anything else is read."""
+    _, args = itmpc.SIGNATURES[name]
+    vals = [0.5 if a in (C.c_float, C.c_double) else 1 if a in (C.c_int32, C.c_int64, C.c_uint64) else None
+            for a in args]
+    assert getattr(L, name)(*vals) == itmpc.ERR_ARG
+
+
 def test_merge_partials_host_math(L):
     # two shards with known sums; lambda = 2: shard 1 is rescaled by exp(-(3 - 1)/2)
     T = 3
