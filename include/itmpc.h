@@ -168,8 +168,9 @@ itmpc_status itmpc_iterate(itmpc_ctx *ctx, const float *x0, const float *U, uint
  * weights and costs, on the fused FP32 kernel (hidden 32 with K < 4096, hidden
  * 64 / 128 with K < 2048), the call replays one CUDA graph the context captures
  * at the first such call and again after itmpc_set_config / set_stream /
- * set_costmap(s): the upload of (x0, iter, U) from a pinned block, the
- * iteration and the download of (U_out, status). */
+ * set_costmap(s): the upload of (x0, iter, U) from a pinned block and the
+ * iteration, whose kernel writes (U_out, status) into a mapped pinned block
+ * (copied back by the graph where the block cannot be mapped). */
 itmpc_status itmpc_iterate_host(itmpc_ctx *ctx, const float *x0, const float *U, uint64_t iter, float *U_out,
                                 float *weights, float *costs);
 

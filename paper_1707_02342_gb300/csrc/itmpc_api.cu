@@ -52,6 +52,7 @@ struct itmpc_ctx {
   // iteration, download of (U', status); pinned host and device blocks of the same layout
   cudaGraphExec_t host_exec = nullptr;
   unsigned char *hblk_in = nullptr, *dblk_in = nullptr, *hblk_out = nullptr, *dblk_out = nullptr;
+  bool host_mapped = false;  // the host graph's kernel writes U' and the status into hblk_out itself
   // basis-function dynamics model: coefficients (host copy for the kernel parameters, device copy)
   std::vector<float> theta_host;
   float *theta_d = nullptr;
@@ -208,8 +209,10 @@ itmpc_status ready(itmpc_ctx *c) {
   return ITMPC_OK;
 }
 
-// Host-graph blocks: in = [x0 (8 floats), iteration index (uint64), pad, U (2 T_max)],
-// out = [U' (2 T_max), status (int), pad] -- one copy each way.
+// Host-graph blocks: in = [x0 (8 floats), iteration index (uint64), pad, U (2 T_max)], copied
+// to the device by the graph; out = [U' (2 T_max), status (int), pad], written by the kernel
+// straight into the pinned block (mapped into the device's address space), or copied back
+// where the block cannot be mapped.
 constexpr size_t kHinU = 48;  // byte offset of U in the input block (16-byte aligned)
 size_t hin_bytes(int T_max) { return kHinU + sizeof(float) * 2 * (size_t)T_max; }
 size_t hout_status(int T_max) { return sizeof(float) * 2 * (size_t)T_max; }
@@ -899,8 +902,15 @@ static itmpc_status host_graph_iterate(itmpc_ctx *c, const float *x0, const floa
     p.x0 = reinterpret_cast<const float *>(c->dblk_in);
     p.iter_add = reinterpret_cast<const unsigned long long *>(c->dblk_in + 32);
     p.U = reinterpret_cast<const float *>(c->dblk_in + kHinU);
-    p.U_out = reinterpret_cast<float *>(c->dblk_out);
-    p.status = reinterpret_cast<int *>(c->dblk_out + hout_status(T_max));
+    // U' and the status word go straight to the pinned output block (mapped into the device's
+    // address space): no copy node back; the host clears the status word before each launch.
+    unsigned char *out_d = nullptr;
+    const bool mapped = cudaHostGetDevicePointer((void **)&out_d, c->hblk_out, 0) == cudaSuccess;
+    if (!mapped) cudaGetLastError();
+    unsigned char *out = mapped ? out_d : c->dblk_out;
+    p.U_out = reinterpret_cast<float *>(out);
+    p.status = reinterpret_cast<int *>(out + hout_status(T_max));
+    c->host_mapped = mapped;
     p.weights = nullptr;
     p.weights_inline = c->cfg.K <= 16384;
     const Fp32Tile tile = fp32_pick_tile(p.K, p.T, p.H, c->smem_optin);
@@ -913,11 +923,12 @@ static itmpc_status host_graph_iterate(itmpc_ctx *c, const float *x0, const floa
       cudaGraph_t graph = nullptr;
       e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
       if (e == cudaSuccess) {
-        cudaError_t ek = cudaMemsetAsync(q.status, 0, sizeof(int), cap);
+        cudaError_t ek = cudaSuccess;
+        if (!c->host_mapped) ek = cudaMemsetAsync(q.status, 0, sizeof(int), cap);
         if (ek == cudaSuccess)
           ek = cudaMemcpyAsync(c->dblk_in, c->hblk_in, hin_bytes(T_max), cudaMemcpyHostToDevice, cap);
         if (ek == cudaSuccess) ek = fp32_launch_iterate(q, tile, cap);
-        if (ek == cudaSuccess)
+        if (ek == cudaSuccess && !c->host_mapped)
           ek = cudaMemcpyAsync(c->hblk_out, c->dblk_out, hout_bytes(T_max), cudaMemcpyDeviceToHost, cap);
         e = cudaStreamEndCapture(cap, &graph);
         if (e == cudaSuccess) e = ek;
@@ -934,6 +945,10 @@ static itmpc_status host_graph_iterate(itmpc_ctx *c, const float *x0, const floa
   memcpy(c->hblk_in, x0, sizeof(float) * 7);
   memcpy(c->hblk_in + 32, &iter, sizeof(iter));
   memcpy(c->hblk_in + kHinU, U, sizeof(float) * 2 * (size_t)T);
+  if (c->host_mapped) {
+    const int zero = 0;
+    memcpy(c->hblk_out + hout_status(T_max), &zero, sizeof(int));
+  }
   CK(c, cudaGraphLaunch(c->host_exec, c->stream), "graph launch");
   CK(c, cudaStreamSynchronize(c->stream), "sync");
   memcpy(U_out, c->hblk_out, sizeof(float) * 2 * (size_t)T);
