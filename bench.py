@@ -482,13 +482,27 @@ def measure_update_hbm(params, layers, flush, steps: int = 50, warmup: int = 10)
     ctl.noise(3, eps)
     U2 = torch.empty_like(U)
     med, mean = _timed(lambda: ctl.update_from_noise(eps, w, U, U2), steps, warmup, flush)
+    # streamed: calls back to back between two events on the launching stream; eps is 4.8x the
+    # L2, so every call reads it from HBM without a flush (host launch latency overlapped)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        ctl.update_from_noise(eps, w, U, U2)
+    b.record(stream)
+    b.synchronize()
+    streamed = a.elapsed_time(b) / steps
     assert ctl.read_status() == 0
     err = float((U2 - Uo).abs().max())
     ctl.close()
     nbytes = K * T * 8 + 2 * K * 4 + 3 * 2 * T * 4  # eps once, weights twice, U / records / U'
     return {"workload": f"U' = sum_k w_k v_k from materialised noise, K={K} T={T} ({K * T * 8 / 1e6:.0f} MB)",
-            "ms_per_call": mean, "ms_median": med, "algorithmic_bytes": nbytes,
-            "achieved_gbs": nbytes / (mean * 1e-3) / 1e9, "max_abs_diff_vs_fused_update": err,
+            "ms_per_call": streamed, "ms_per_call_isolated": mean, "ms_median_isolated": med,
+            "timing": f"{steps} calls back to back (eps larger than L2, no flush); isolated: one call between "
+                      "events, L2 flushed before each",
+            "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (streamed * 1e-3) / 1e9,
+            "achieved_gbs_isolated": nbytes / (mean * 1e-3) / 1e9, "max_abs_diff_vs_fused_update": err,
             "gpu_launches_per_call": 2}
 
 
