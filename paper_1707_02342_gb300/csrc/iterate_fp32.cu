@@ -1,16 +1,18 @@
 // iterate_fp32.cu -- fused FP32 IT-MPC control iteration for sm_103a.
 //
-// One launch performs the whole iteration of Alg. 1 / Alg. 2.  Each warp owns
-// one sample k; a CTA owns NW consecutive samples.
+// One launch performs the whole iteration of Alg. 1 / Alg. 2.  A warp owns two
+// samples (H = 32) or one (H = 64, 128); a CTA owns NW warps' consecutive samples.
 //   phase 1  noise      eps and the clamped control g(v) for the CTA's samples x T
 //                       steps (Philox-4x32-10 + Box-Muller), kept in shared memory;
 //   phase 2  dynamics   the serial recurrence x_d(t+1) = x_d(t) + dt f(x_d(t), g(v_t))
 //                       of Sec. V-B.  Only x_d feeds the network, so this is the one
-//                       serial chain.  Lane j owns hidden neuron j (+32, +64, ...):
-//                       layer 1 in registers, h1 broadcast through a per-warp
-//                       shared row, layer 2 as four independent FMA chains with W2
-//                       in registers (H = 32), the 4 outputs of layer 3 reduced
-//                       across the warp with a register butterfly;
+//                       serial chain.  H = 32: a half-warp per sample, two neurons
+//                       per lane, W2 rows in registers, the layer-1 pre-activation
+//                       carried from step to step (recurrence_half32).  H = 64, 128:
+//                       lane j owns neurons j, j + 32, ...; layer 1 in registers, h1
+//                       broadcast through a per-warp shared row, W2 transposed in
+//                       shared memory, the 4 outputs of layer 3 reduced across the
+//                       warp with a register butterfly;
 //   phase 3  kinematics heading and position are prefix sums over t of dt*theta_dot
 //            and cost   and dt*R(theta)v (warp scans, lane = time step); then the state
 //                       cost of Sec. V-C at t = 1..T plus the control-cost term of
@@ -48,7 +50,7 @@ __host__ __device__ inline SmemLayout fp32_layout(int T, int H, int nw, int spw)
   L.traj = off; off += align16(sizeof(float4) * (size_t)scta * (T + 1));
   L.pos = off;  off += align16(sizeof(float4) * (size_t)scta * T);
   L.W2T = off;  off += (H > 32) ? align16(sizeof(float) * (size_t)H * H) : 0;
-  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * (spw == 2 ? 2 * 32 * 36 + 16 + 80 : (H == 32 ? 32 * 36 + 32 : 2 * H)));
+  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * (spw == 2 ? 2 * 32 * 36 + 16 + 80 : 2 * H));
   L.W3b3 = off; off += align16(sizeof(float) * (4 * H + 4));
   L.S = off;    off += align16(sizeof(float) * scta);
   L.e = off;    off += align16(sizeof(float) * scta);
@@ -219,116 +221,10 @@ __device__ void coop_tail(const IterParams &p, const float *S_s, int k0) {
 // left in traj[t + 1]; phase 3 turns it into x_d by prefix sums.
 constexpr int kRingStride = 36;  // padded row: lanes reading rows t, t+1, .. hit distinct banks
 
-template <int ACT>
-__device__ __forceinline__ void recurrence_ring32(const IterParams &p, const float *net, float *ring, float *hB,
-                                                  const float *W3b3_s, const float2 *gvr, float4 *traj, int T,
-                                                  int lane) {
-  constexpr int H = 32;
-  const float dt = p.dt;
-  float w1x[4], b3[4];
-#pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    w1x[o] = __ldg(net + net_off_W1(H) + lane * 6 + o);
-    b3[o] = __ldg(net + net_off_b3(H) + o);
-  }
-  const float w1u0 = __ldg(net + net_off_W1(H) + lane * 6 + 4);
-  const float w1u1 = __ldg(net + net_off_W1(H) + lane * 6 + 5);
-  const float b1 = __ldg(net + net_off_b1(H) + lane);
-  const float b2 = __ldg(net + net_off_b2(H) + lane);
-  float beta = 0.f;
-#pragma unroll
-  for (int o = 0; o < 4; ++o) beta = fmaf(dt * w1x[o], b3[o], beta);
-  float m[H], w2[H];
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-    float a = 0.f;
-#pragma unroll
-    for (int o = 0; o < 4; ++o) a = fmaf(w1x[o], W3b3_s[o * H + i], a);
-    m[i] = dt * a;
-    w2[i] = __ldg(net + net_off_W2(H) + lane * H + i);
-  }
-  const float4 *hB4 = reinterpret_cast<const float4 *>(hB);
-
-  // a1(0) = b1 + W1x x_d(0) + W1u g(0)
-  float2 g = gvr[0];
-  float a1 = b1;
-  a1 = fmaf(w1x[0], __ldg(p.x0 + 3), a1);
-  a1 = fmaf(w1x[1], __ldg(p.x0 + 4), a1);
-  a1 = fmaf(w1x[2], __ldg(p.x0 + 5), a1);
-  a1 = fmaf(w1x[3], __ldg(p.x0 + 6), a1);
-  a1 = fmaf(w1u0, g.x, a1);
-  a1 = fmaf(w1u1, g.y, a1);
-  float a1c = 0.f;  // Kahan compensation of the running sum a1
-  for (int t = 0; t < T; ++t) {
-    const float2 gn = gvr[t + 1 < T ? t + 1 : t];
-    // layer 1 activation, broadcast through hB
-    hB[lane] = activation<ACT>(a1);
-    __syncwarp();
-    // layer 2
-    float c0 = b2, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < H; kk += 4) {
-      const float4 hv = hB4[kk >> 2];
-      c0 = fmaf(w2[kk], hv.x, c0);
-      c1 = fmaf(w2[kk + 1], hv.y, c1);
-      c2 = fmaf(w2[kk + 2], hv.z, c2);
-      c3 = fmaf(w2[kk + 3], hv.w, c3);
-    }
-    const float h2 = activation<ACT>((c0 + c1) + (c2 + c3));
-    float *row = ring + (t & 31) * kRingStride;
-    row[lane] = h2;
-    __syncwarp();
-    // next step's pre-activation: a1 += M h2 + beta + W1u (g(t+1) - g(t))
-    if (t + 1 < T) {
-      const float4 *row4 = reinterpret_cast<const float4 *>(row);
-      float e0 = beta, e1 = 0.f, e2 = 0.f, e3 = 0.f;
-      e0 = fmaf(w1u0, gn.x - g.x, e0);
-      e1 = fmaf(w1u1, gn.y - g.y, e1);
-#pragma unroll
-      for (int kk = 0; kk < H; kk += 4) {
-        const float4 hv = row4[kk >> 2];
-        e0 = fmaf(m[kk], hv.x, e0);
-        e1 = fmaf(m[kk + 1], hv.y, e1);
-        e2 = fmaf(m[kk + 2], hv.z, e2);
-        e3 = fmaf(m[kk + 3], hv.w, e3);
-      }
-      const float y = ((e0 + e1) + (e2 + e3)) - a1c;
-      const float sum = a1 + y;
-      a1c = (sum - a1) - y;
-      a1 = sum;
-      g = gn;
-    }
-    // every 32 steps (and at the end): the output layer for the block, lane = step
-    if ((t & 31) == 31 || t + 1 == T) {
-      const int t0 = t & ~31;
-      if (t0 + lane <= t) {
-        const float4 *r4 = reinterpret_cast<const float4 *>(ring + lane * kRingStride);
-        float d0 = W3b3_s[4 * H + 0], d1 = W3b3_s[4 * H + 1], d2 = W3b3_s[4 * H + 2], d3 = W3b3_s[4 * H + 3];
-#pragma unroll
-        for (int kk = 0; kk < H; kk += 4) {
-          const float4 hv = r4[kk >> 2];
-          const float4 w0 = *reinterpret_cast<const float4 *>(W3b3_s + 0 * H + kk);
-          const float4 wq1 = *reinterpret_cast<const float4 *>(W3b3_s + 1 * H + kk);
-          const float4 wq2 = *reinterpret_cast<const float4 *>(W3b3_s + 2 * H + kk);
-          const float4 wq3 = *reinterpret_cast<const float4 *>(W3b3_s + 3 * H + kk);
-          d0 = fmaf(w0.x, hv.x, fmaf(w0.y, hv.y, fmaf(w0.z, hv.z, fmaf(w0.w, hv.w, d0))));
-          d1 = fmaf(wq1.x, hv.x, fmaf(wq1.y, hv.y, fmaf(wq1.z, hv.z, fmaf(wq1.w, hv.w, d1))));
-          d2 = fmaf(wq2.x, hv.x, fmaf(wq2.y, hv.y, fmaf(wq2.z, hv.z, fmaf(wq2.w, hv.w, d2))));
-          d3 = fmaf(wq3.x, hv.x, fmaf(wq3.y, hv.y, fmaf(wq3.z, hv.z, fmaf(wq3.w, hv.w, d3))));
-        }
-        traj[t0 + lane + 1] = make_float4(d0, d1, d2, d3);
-      }
-      __syncwarp();  // the ring is reused by the next block
-    }
-  }
-}
-
-// Phase 2 for H = 32 with two samples per warp: half-warp h = lane / 16 owns
-// sample s_first + h and lane j = lane % 16 owns neurons j and j + 16 of it.
-// Same recurrence as recurrence_ring32 (carried a1, h2 ring, output layer
-// every 32 steps with lane = step), but every activation broadcast now feeds
-// two FMAs per lane, halving the shared-memory -> register traffic per sample
-// step, which bounds the one-neuron-per-lane form at this sample count.
+// Two samples per warp: half-warp h = lane / 16 owns sample s_first + h and
+// lane j = lane % 16 owns neurons j and j + 16 of it, so every activation
+// broadcast feeds two FMAs per lane (half the shared-memory -> register traffic
+// per sample-step of a one-neuron-per-lane layout).
 // Per-warp buffer: ring 0 at 0, ring 1 at 32 rows + 16 floats (the other 16
 // banks), then the two h1 rows at +0 and +48 floats: the halves' stores and
 // loads never share a bank.
@@ -471,11 +367,10 @@ __device__ __forceinline__ void recurrence_half32(const IterParams &p, const flo
 
 template <int H, int NW, int SPW, int ACT>
 __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_constant__ IterParams p) {
-  static_assert(SPW == 1 || H == 32, "two samples per warp needs H = 32");
+  static_assert((SPW == 2) == (H == 32), "H = 32 runs two samples per warp, H = 64 / 128 one");
   constexpr int NT = NW * 32;
   constexpr int SCTA = NW * SPW;  // samples per CTA
   constexpr int NPL = H / 32;  // hidden neurons per lane
-  constexpr bool W2_IN_REGS = (H == 32);
 
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = p.T;
@@ -512,7 +407,7 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
   }
   for (int i = tid; i < 2 * T; i += NT) U_s[i] = __ldg(p.U + i);
   for (int i = tid; i < 4 * H + 4; i += NT) W3b3_s[i] = __ldg(net + net_off_W3(H) + i);  // W3 then b3
-  if constexpr (!W2_IN_REGS) {
+  if constexpr (H > 32) {
     for (int i = tid; i < H * H; i += NT) {
       const int j = i / H, kk = i - j * H;  // W2[j][kk] -> W2T[kk][j]
       W2T_s[kk * H + j] = __ldg(net + net_off_W2(H) + i);
@@ -545,7 +440,6 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
 
   // per-lane network slices
   float w1[NPL][6], b1r[NPL], b2r[NPL], w3[NPL][4];
-  float w2[W2_IN_REGS ? H : 1];
 #pragma unroll
   for (int n = 0; n < NPL; ++n) {
     const int j = lane + 32 * n;
@@ -555,10 +449,6 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
     b2r[n] = __ldg(net + net_off_b2(H) + j);
 #pragma unroll
     for (int o = 0; o < 4; ++o) w3[n][o] = __ldg(net + net_off_W3(H) + o * H + j);
-  }
-  if constexpr (W2_IN_REGS) {
-#pragma unroll
-    for (int kk = 0; kk < H; ++kk) w2[kk] = __ldg(net + net_off_W2(H) + lane * H + kk);
   }
   float b3r[4];
 #pragma unroll
@@ -577,17 +467,14 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
     recurrence_half32<ACT>(p, net, wbuf, W3b3_s, gv_s, traj_s, warp * 2, T, lane);
     __syncwarp();
   } else if (k0 + warp < p.K) {
+    // H = 64 / 128: one warp per sample
     const int s = warp;
-    // ---- phase 2: the serial network recurrence ----
     float xd0 = __ldg(p.x0 + 3), xd1 = __ldg(p.x0 + 4), xd2 = __ldg(p.x0 + 5), xd3 = __ldg(p.x0 + 6);
-    float *hrow = reinterpret_cast<float *>(smem + L.hbuf) + s * (H == 32 ? 32 * kRingStride + 32 : 2 * H);
+    float *hrow = reinterpret_cast<float *>(smem + L.hbuf) + s * 2 * H;
     const float4 *hrow4 = reinterpret_cast<const float4 *>(hrow);
     float4 *traj = traj_s + s * (T + 1);
     const float2 *gvr = gv_s + s * T;
     if (lane == 0) traj[0] = make_float4(xd0, xd1, xd2, xd3);
-    if constexpr (H == 32) {
-      recurrence_ring32<ACT>(p, net, hrow, hrow + 32 * kRingStride, W3b3_s, gv_s + s * T, traj, T, lane);
-    } else {
     const int hi16 = (lane >> 4) & 1, hi8 = (lane >> 3) & 1;
     float2 g_next = gvr[0];
     for (int t = 0; t < T; ++t) {
@@ -618,14 +505,9 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
         const float4 hv = hrow4[kk >> 2];
 #pragma unroll
         for (int n = 0; n < NPL; ++n) {
-          float wa, wb, wc, wd;
-          if constexpr (W2_IN_REGS) {
-            wa = w2[kk]; wb = w2[kk + 1]; wc = w2[kk + 2]; wd = w2[kk + 3];
-          } else {
-            const int j = lane + 32 * n;
-            wa = W2T_s[kk * H + j]; wb = W2T_s[(kk + 1) * H + j];
-            wc = W2T_s[(kk + 2) * H + j]; wd = W2T_s[(kk + 3) * H + j];
-          }
+          const int j = lane + 32 * n;
+          const float wa = W2T_s[kk * H + j], wb = W2T_s[(kk + 1) * H + j];
+          const float wc = W2T_s[(kk + 2) * H + j], wd = W2T_s[(kk + 3) * H + j];
           acc[n][0] = fmaf(wa, hv.x, acc[n][0]);
           acc[n][1] = fmaf(wb, hv.y, acc[n][1]);
           acc[n][2] = fmaf(wc, hv.z, acc[n][2]);
@@ -661,9 +543,6 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
       if (lane == 0) traj[t + 1] = make_float4(xd0, xd1, xd2, xd3);
     }
     __syncwarp();
-    }
-    __syncwarp();
-
   }
 
   // ---- phase 3: kinematics and running costs, this warp's samples side by side ----
@@ -1010,8 +889,6 @@ cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t
   ITMPC_TILE(32, 4, 2)
   ITMPC_TILE(32, 7, 2)
   ITMPC_TILE(32, 8, 2)
-  ITMPC_TILE(32, 4, 1)
-  ITMPC_TILE(32, 16, 1)
   ITMPC_TILE(64, 4, 1)
   ITMPC_TILE(64, 8, 1)
   ITMPC_TILE(64, 16, 1)
