@@ -10,6 +10,10 @@ the paper's order of operations); this file only marshals numpy arrays.
 Functions whose result has no independent pin say so in their docstring and
 in the design notes ("parity unpinned"); at present every exported function
 is pinned by a CPU test under ``tests/``.
+
+``ITMPC_ORACLE_LIB``, when set, names a compiled oracle to load instead of
+building ``itmpc_oracle.c``: the mutation tests point it at copies with a
+planted mistake and check that the pins reject each of them.
 """
 from __future__ import annotations
 
@@ -27,14 +31,18 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 OK, ERR_ARG, ERR_NONFINITE = 0, -1, -3
 
 
+# gcc flags of the oracle library: IEEE double (no contraction, no fast math), OpenMP
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-Wall"]
+SOURCE = _SRC
+
+
 def build(force: bool = False) -> str:
     """Compile itmpc_oracle.c into a shared library (gcc, IEEE double, OpenMP)."""
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
-           "-Wall", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -63,7 +71,7 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        _lib = C.CDLL(os.environ.get("ITMPC_ORACLE_LIB") or build())
         P = C.POINTER(_Problem)
         d, u32p, i64p = C.c_void_p, C.c_void_p, C.c_void_p
         sig = {

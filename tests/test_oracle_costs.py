@@ -82,6 +82,20 @@ def test_terms_closed_forms():
         assert c == pytest.approx(comp.sum(), abs=1e-9)
 
 
+def test_each_multiplier_weights_its_own_term():
+    # Sec. V-C: c = alpha_1 Track + alpha_2 Speed + alpha_3 Stabilizing; the fourth multiplier
+    # scales the impulse terms.  v = (3, 3.5): |zeta| = atan(3.5 / 3) > 0.75, so the slip impulse fires.
+    x = np.array([0.0, 0.0, 0.0, 0.0, 3.0, 3.5, 0.0])
+    _, comp, _ = oracle.state_cost(prob(const_map(0.4), cost_w=(1.0, 1.0, 1.0, 1.0)), x, 2)
+    assert comp[1] == pytest.approx(9.0) and comp[3] == 1e4
+    for i, m in enumerate((2.0, 3.0, 5.0, 7.0)):
+        w = [0.0] * 4
+        w[i] = m
+        c, comp_i, _ = oracle.state_cost(prob(const_map(0.4), cost_w=tuple(w)), x, 2)
+        np.testing.assert_array_equal(comp_i, comp)
+        assert c == pytest.approx(m * comp[i], rel=1e-15)
+
+
 def test_track_cap_and_weights():
     P = prob(const_map(7.0), cost_w=(2.0, 0.0, 0.0, 0.0), map_cap=2.5)
     c, comp, _ = oracle.state_cost(P, np.zeros(7), 1)

@@ -49,6 +49,26 @@ def test_identity_activation_is_affine():
     np.testing.assert_allclose(oracle.mlp(P, z), ref, rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("sel", [(0, 1, 2, 3), (4, 5, 4, 5), (3, 2, 1, 0)])
+def test_network_reads_state_and_controls_in_the_paper_order(sel):
+    # Sec. V-B: the network's input is (roll, v_x, v_y, yaw rate, steering, throttle).  An
+    # identity-activation network whose output o copies input sel[o] turns one Euler step of
+    # the dynamic states into x_d + dt * z[sel].
+    H = 32
+    W1 = np.zeros((H, 6), np.float32)
+    W1[np.arange(6), np.arange(6)] = 1.0
+    W3 = np.zeros((4, H), np.float32)
+    W3[np.arange(4), list(sel)] = 1.0
+    layers = [(W1, np.zeros(H, np.float32)), (np.eye(H, dtype=np.float32), np.zeros(H, np.float32)),
+              (W3, np.zeros(4, np.float32))]
+    P = problems.oracle_problem(problems.params_small(activation=1), problems.ellipse_map(), layers)
+    x = np.array([1.0, -2.0, 0.3, 0.05, 4.0, -0.7, 0.9])
+    g = np.array([0.25, -0.6])
+    z = np.array([x[3], x[4], x[5], x[6], g[0], g[1]])
+    xn = oracle.dynamics_step(P, x, g)
+    np.testing.assert_allclose(xn[3:], x[3:] + P.dt * z[list(sel)], rtol=0, atol=1e-14)
+
+
 def zero_layers(H=32, b3=(0.0, 0.0, 0.0, 0.0)):
     layers = [(np.zeros((H, 6), np.float32), np.zeros(H, np.float32)),
               (np.zeros((H, H), np.float32), np.zeros(H, np.float32)),

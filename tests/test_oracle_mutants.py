@@ -1,0 +1,153 @@
+"""Mutation check of the oracle's pins.
+
+Each entry below plants one plausible mistake in a copy of ``oracle/itmpc_oracle.c``:
+a dropped term, a flipped sign, a wrong, swapped or transposed index, an off-by-one,
+a wrong constant.  The copy is compiled like the oracle and the pin tests that cover
+that part of the oracle run against it (``ITMPC_ORACLE_LIB``) in a subprocess.  Every
+mutant must make at least one of those pins fail; the unmutated source, compiled and
+run the same way, must pass them.  The oracle's own source is never modified.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+NOISE = ["tests/test_oracle_noise.py"]
+DYN = ["tests/test_oracle_dynamics.py"]
+COST = ["tests/test_oracle_costs.py"]
+WU = ["tests/test_oracle_weights_update.py"]
+LOOP = ["tests/test_oracle_closed_loop.py"]
+CEM = ["tests/test_oracle_cem.py"]
+BASIS = ["tests/test_oracle_basis.py"]
+ADJ = ["tests/test_oracle_adjoint.py"]
+
+# (name, text in the oracle, replacement, pin files, occurrences of the text, which one to replace)
+MUTANTS = [
+    # Philox-4x32-10, Box-Muller, the noise counter (Sec. II sampling; Salmon et al.; Box & Muller)
+    ("philox_weyl_constant", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;", NOISE),
+    ("philox_lane_swap", "uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi0 ^ c1 ^ k0;", NOISE),
+    ("philox_nine_rounds", "round < 10; ++round", "round < 9; ++round", NOISE),
+    ("uniform_offset", "((double)(a >> 8) + 1.0)", "((double)(a >> 8) + 0.5)", NOISE),
+    ("box_muller_cos_sin", "z[0] = r * cos(two_pi * u1);", "z[0] = r * sin(two_pi * u1);", NOISE),
+    ("box_muller_radius", "sqrt(-2.0 * log(u0))", "sqrt(-log(u0))", NOISE),
+    ("sigma_index", "eps[1] = P->sigma[1] * z[1];", "eps[1] = P->sigma[0] * z[1];", NOISE),
+    ("counter_k_t_swapped", "{(uint32_t)k, (uint32_t)t,", "{(uint32_t)t, (uint32_t)k,", NOISE),
+    ("counter_instance_shift", "| (P->instance << 16)}", "| (P->instance << 8)}", NOISE),
+    # network and equations of motion (Sec. V-B)
+    ("mlp_w2_transposed",
+     "a += P->W2[(size_t)j * H + i] * h1[i];\n    h2[j] = act(P, a);\n  }\n  for (int o = 0; o < 4; ++o) {",
+     "a += P->W2[(size_t)i * H + j] * h1[i];\n    h2[j] = act(P, a);\n  }\n  for (int o = 0; o < 4; ++o) {", DYN),
+    ("mlp_b2_dropped", "double a = P->b2[j];", "double a = 0.0;", DYN, 2, 0),
+    ("mlp_w1_input_reversed", "a += P->W1[j * 6 + i] * z[i];", "a += P->W1[j * 6 + i] * z[5 - i];", DYN, 2, 0),
+    ("mlp_output_no_bias", "double a = P->b3[o];", "double a = 0.0;", DYN),
+    ("kinematics_px_sign", "(cos(th) * vx - sin(th) * vy) * P->dt", "(cos(th) * vx + sin(th) * vy) * P->dt", DYN),
+    ("kinematics_py_sin_cos", "(sin(th) * vx + cos(th) * vy) * P->dt", "(cos(th) * vx + sin(th) * vy) * P->dt", DYN),
+    ("yaw_without_dt", "xn[2] = x[2] + thd * P->dt;", "xn[2] = x[2] + thd;", DYN),
+    ("network_input_order", "double z[6] = {x[3], x[4], x[5], x[6], gv[0], gv[1]};",
+     "double z[6] = {x[4], x[3], x[5], x[6], gv[0], gv[1]};", DYN, 2, 0),
+    ("network_control_order", "double z[6] = {x[3], x[4], x[5], x[6], gv[0], gv[1]};",
+     "double z[6] = {x[3], x[4], x[5], x[6], gv[1], gv[0]};", DYN, 2, 0),
+    # costmap and state cost (Sec. V-C)
+    ("texel_centre", "double fx = (px - P->origin_x) / P->res - 0.5;", "double fx = (px - P->origin_x) / P->res;",
+     COST),
+    ("bilinear_weight", "+ a * (1.0 - b) * m01 +", "+ b * (1.0 - a) * m01 +", COST),
+    ("map_rows_cols", "double m00 = P->map[i0 * W + j0], m01 = P->map[i0 * W + j1];",
+     "double m00 = P->map[i0 * W + j0], m01 = P->map[i1 * W + j0];", COST, 2, 0),
+    ("y_uses_origin_x", "double fy = (py - P->origin_y) / P->res - 0.5;",
+     "double fy = (py - P->origin_x) / P->res - 0.5;", COST),
+    ("map_cap_dropped", "if (h > P->map_cap) h = P->map_cap;", "", COST),
+    ("speed_not_squared", "double speed = (vx - P->v_des) * (vx - P->v_des);", "double speed = (vx - P->v_des);", COST),
+    ("track_threshold_not_strict", "if (h > P->track_thresh) imp", "if (h >= P->track_thresh) imp", COST),
+    ("impulse_decay_off_by_one", "imp += pow(P->crash_decay, (double)t) * P->crash_cost;",
+     "imp += pow(P->crash_decay, (double)(t - 1)) * P->crash_cost;", COST),
+    ("slip_without_abs_vx", "double zeta = -atan2(vy, fabs(vx));\n  double speed",
+     "double zeta = -atan2(vy, vx);\n  double speed", COST),
+    ("slip_threshold_signed", "if (fabs(zeta) > P->slip_thresh) imp", "if (zeta > P->slip_thresh) imp", COST),
+    ("cost_weights_swapped", "P->cost_w[1] * speed + P->cost_w[2] * zeta * zeta",
+     "P->cost_w[2] * speed + P->cost_w[1] * zeta * zeta", COST),
+    ("cost_time_index", "double c = oracle_state_cost(P, x, t, c4, &m);",
+     "double c = oracle_state_cost(P, x, t - 1, c4, &m);", COST),
+    # Alg. 1 rollout, Alg. 2 weights, the update of Sec. III-D, the control cost of Sec. III-E
+    ("rollout_noise_index", "oracle_noise(P, iter, k, t - 1, eps);", "oracle_noise(P, iter, k, t, eps);", WU, 2, 0),
+    ("weights_not_normalised", "exp(-(S[k] - rho) / lambda) / eta : 0.0;", "exp(-(S[k] - rho) / lambda) : 0.0;", WU),
+    ("weights_sign", "exp(-(S[k] - rho) / lambda) / eta : 0.0;", "exp((S[k] - rho) / lambda) / eta : 0.0;", WU),
+    ("weights_lambda_dropped", "w[k] = isfinite(S[k]) ? exp(-(S[k] - rho) / lambda) / eta",
+     "w[k] = isfinite(S[k]) ? exp(-(S[k] - rho)) / eta", WU),
+    ("update_exploration_split", "int importance = (double)k < (1.0 - P->alpha_explore) * (double)P->K;\n      double v0",
+     "int importance = (double)k <= (1.0 - P->alpha_explore) * (double)P->K;\n      double v0", WU),
+    ("rollout_exploration_split", "int importance = (double)k < (1.0 - P->alpha_explore) * (double)P->K;\n  double S",
+     "int importance = (double)k <= (1.0 - P->alpha_explore) * (double)P->K;\n  double S", WU),
+    ("update_channel", "s1 += w[k] * v1;", "s1 += w[k] * v0;", WU),
+    ("update_exploration_adds_U", "double v1 = importance ? U[2 * t + 1] + eps[1] : eps[1];",
+     "double v1 = U[2 * t + 1] + eps[1];", WU),
+    ("control_cost_sigma", "U[2 * (t - 1)] * v[0] / (P->sigma[0] * P->sigma[0])", "U[2 * (t - 1)] * v[0] / P->sigma[0]",
+     WU),
+    ("control_cost_dropped", "S += c + P->gamma * ctrl;", "S += c;", WU),
+    # Savitzky-Golay smoothing and the closed-loop step (Sec. III-E, Alg. 1)
+    ("savgol_basis_shift", "pw[r] = pw[r - 1] * (double)o;", "pw[r] = pw[r - 1] * (double)(o + 1);", LOOP),
+    ("savgol_mirror_edges", "i = i < 0 ? 0 : (i > n - 1 ? n - 1 : i);",
+     "i = i < 0 ? -i : (i > n - 1 ? 2 * (n - 1) - i : i);", LOOP),
+    ("warm_start_keeps_last", "U_next[2 * (T - 1)] = 0.0;", "U_next[2 * (T - 1)] = Us[2 * (T - 1)];", LOOP),
+    ("applied_control_unsmoothed", "u_applied[0] = Us[0];", "u_applied[0] = U_prime[0];", LOOP),
+    ("delta_smoothing_without_U", "for (int32_t t = 0; t < 2 * T; ++t) Us[t] += U[t];", "", LOOP),
+    # cross-entropy weights (Alg. 3)
+    ("cem_strict_elite", "w[k] = (isfinite(S[k]) && S[k] <= Z)", "w[k] = (isfinite(S[k]) && S[k] < Z)", CEM),
+    ("cem_floor_not_round", "floor((double)K * (1.0 - delta) + 0.5)", "floor((double)K * (1.0 - delta))", CEM),
+    ("cem_delta_direction", "floor((double)K * (1.0 - delta) + 0.5)", "floor((double)K * delta + 0.5)", CEM),
+    # basis-function model (Sec. V-B, appendix)
+    ("basis_phi5_vx", "phi[5] = r * vy / 25.0;", "phi[5] = r * vx / 25.0;", BASIS),
+    ("basis_front_slip_sign", "atan(vy / vx + 0.45 * r / vx - ud)", "atan(vy / vx - 0.45 * r / vx - ud)", BASIS),
+    ("basis_low_speed_sign", ": -ud;", ": ud;", BASIS),
+    ("basis_theta_transposed", "a += P->theta[i * 4 + o] * phi[i];", "a += P->theta[o * 25 + i] * phi[i];", BASIS),
+    ("basis_phi21_scale", "phi[21] = vx * vx / 100.0;", "phi[21] = vx * vx / 10.0;", BASIS),
+    # the adjoint (reverse mode of the above)
+    ("adj_tanh_derivative", "1.0 - h * h;", "1.0 - h;", ADJ),
+    ("adj_w2_backprop_transposed", "s += P->W2[(size_t)j * H + i] * a2bar[j];",
+     "s += P->W2[(size_t)i * H + j] * a2bar[j];", ADJ),
+    ("adj_speed_gradient_factor", "gx[4] += P->cost_w[1] * 2.0 * (x[4] - P->v_des);",
+     "gx[4] += P->cost_w[1] * (x[4] - P->v_des);", ADJ),
+    ("adj_map_slope_y_weights", "double dh_dfy = (1.0 - a) * (m10 - m00) + a * (m11 - m01);",
+     "double dh_dfy = (1.0 - b) * (m10 - m00) + b * (m11 - m01);", ADJ),
+]
+
+
+def _mutate(src, old, new, count=1, nth=0):
+    assert src.count(old) == count, f"expected {count} occurrence(s) of {old!r} in the oracle"
+    i = -1
+    for _ in range(nth + 1):
+        i = src.index(old, i + 1)
+    return src[:i] + new + src[i + len(old):]
+
+
+def _build_and_run(text, lib, files):
+    """Compile `text` like the oracle into `lib`, run the pin files against it; pytest's return code."""
+    c_file = lib[:-3] + ".c"
+    with open(c_file, "w") as f:
+        f.write(text)
+    subprocess.run(["gcc", *oracle.CFLAGS, "-o", lib, c_file, "-lm"], check=True, capture_output=True)
+    env = dict(os.environ, ITMPC_ORACLE_LIB=lib, OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               PYTHONPATH=ROOT + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                        *files], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    return r.returncode
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    src = open(oracle.SOURCE).read()
+    names = [m[0] for m in MUTANTS]
+    assert len(set(names)) == len(names)
+    texts = {m[0]: _mutate(src, *m[1:3], *m[4:]) for m in MUTANTS}  # fails here if the oracle text moved
+    files_all = sorted({f for m in MUTANTS for f in m[3]})
+    workers = max(1, min(8, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else 4))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        control = ex.submit(_build_and_run, src, str(tmp_path / "control.so"), files_all)
+        runs = {m[0]: ex.submit(_build_and_run, texts[m[0]], str(tmp_path / f"{m[0]}.so"), m[3]) for m in MUTANTS}
+        assert control.result() == 0, "the unmutated oracle must pass its pins under the same harness"
+        codes = {n: f.result() for n, f in runs.items()}
+    # 1: a pin failed; negative: the mutant crashed the test process (also a detection)
+    survivors = {n: rc for n, rc in codes.items() if not (rc == 1 or rc < 0)}
+    assert not survivors, f"mistakes no pin detects: {survivors}"

@@ -112,6 +112,20 @@ def test_exploration_split():
         np.testing.assert_allclose(Uo, U.astype(np.float64) * n_imp / 8 + eps.mean(0), rtol=1e-12, atol=1e-14)
 
 
+def test_exploration_split_in_the_rollouts():
+    # Alg. 1: sample k rolls out g(U + eps) when k < (1 - alpha) K and g(eps) otherwise, so an
+    # exploration sample's trajectory does not depend on U and an importance sample's does.
+    x0 = problems.x0_for(problems.ellipse_map(), speed=3.0)
+    U = inputs.nominal_controls(10, seed=8)
+    Z = np.zeros_like(U)
+    for alpha, n_imp in [(0.25, 6), (0.2, 7), (0.0, 8), (1.0, 0)]:
+        P = small_problem(K=8, T=10, alpha_explore=alpha)
+        for k in range(8):
+            _, tU, _, _ = oracle.rollout_sample(P, x0, U, 1, k)
+            _, t0, _, _ = oracle.rollout_sample(P, x0, Z, 1, k)
+            assert np.array_equal(tU, t0) == (k >= n_imp), (alpha, k)
+
+
 def linear_system(P: oracle.Problem, layers, xd0, T):
     """vx(t) = a_t + G[t] . V for the identity-activation network (t = 1..T)."""
     (W1, b1), (W2, b2), (W3, b3) = [(W.astype(np.float64), b.astype(np.float64)) for W, b in layers]
