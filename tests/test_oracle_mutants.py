@@ -112,6 +112,22 @@ MUTANTS = [
      "gx[4] += P->cost_w[1] * (x[4] - P->v_des);", ADJ),
     ("adj_map_slope_y_weights", "double dh_dfy = (1.0 - a) * (m10 - m00) + a * (m11 - m01);",
      "double dh_dfy = (1.0 - b) * (m10 - m00) + b * (m11 - m01);", ADJ),
+    ("adj_cost_cotangent_J_sign", "gJ * (1.0 - (Sw[k] - J) / P->lambda)", "gJ * (1.0 + (Sw[k] - J) / P->lambda)", ADJ),
+    ("adj_cost_cotangent_U_sign", "- (a - c0) / P->lambda);", "+ (a - c0) / P->lambda);", ADJ),
+    ("adj_clamp_passes_gradient", "(v[i] >= P->u_min[i] && v[i] <= P->u_max[i]) ? gvbar[i] : 0.0", "gvbar[i]", ADJ),
+    ("adj_exploration_gets_dU", "if (importance) ubar += vbar;", "ubar += vbar;", ADJ),
+    ("adj_direct_dU_without_w_imp", "g_U[t] = gUo ? gUo[t] * w_imp : 0.0;", "g_U[t] = gUo ? gUo[t] : 0.0;", ADJ),
+    ("adj_heading_sign", "xbar_n[0] * (-s * vx - c * vy)", "xbar_n[0] * (s * vx - c * vy)", ADJ),
+    ("adj_yaw_rate_dropped", "xbar[6] += dt * xbar_n[2];", "", ADJ),
+    ("adj_cost_weight_grad_unscaled", "gcw[i] += Sbar * comp[i];", "gcw[i] += comp[i];", ADJ),
+    ("adj_control_cost_du_dropped", "ubar += Sbar * P->gamma * v[i] * is2;", "", ADJ),
+    ("adj_slip_slope_sign", "dz_dvy = -fabs(vx) / r2;", "dz_dvy = fabs(vx) / r2;", ADJ),
+    ("adj_gW2_transposed", "gW2[(size_t)j * H + i] += a2bar[j] * h1[i];", "gW2[(size_t)i * H + j] += a2bar[j] * h1[i];",
+     ADJ),
+    ("adj_gb1_dropped", "gb1[j] += a1bar[j];", "", ADJ),
+    # the sort of the cross-entropy ranks and the Savitzky-Golay solve
+    ("cem_sort_descending", "while (i > 0 && f[i - 1] > S[k])", "while (i > 0 && f[i - 1] < S[k])", CEM),
+    ("savgol_back_substitution", "b[c] = s / A[c * n + c];", "b[c] = s;", LOOP),
 ]
 
 
