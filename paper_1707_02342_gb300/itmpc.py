@@ -10,6 +10,8 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libitmpc.so")
 
@@ -137,13 +139,33 @@ def make_config(K: int, T: int, *, T_max: int = 0, hidden: int = 32, dt=0.02, la
     return c
 
 
-def _dptr(t) -> int:
-    """Device pointer of a contiguous float32/uint32 CUDA tensor (or None)."""
+def _dptr(t, n: int = 0, words: bool = False) -> int:
+    """Device pointer of a contiguous CUDA tensor of at least n float32 elements (32-bit
+    integer words when ``words``), or None for None.  Anything else is refused here, before a
+    kernel could read or write past the end of the buffer."""
     if t is None:
         return None
-    if not t.is_cuda or not t.is_contiguous():
+    if not getattr(t, "is_cuda", False) or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
+    import torch
+
+    ok = t.dtype in (torch.int32, getattr(torch, "uint32", torch.int32)) if words else t.dtype == torch.float32
+    if not ok:
+        raise ValueError(f"expected a {'32-bit integer' if words else 'float32'} tensor, got {t.dtype}")
+    if t.numel() < n:
+        raise ValueError(f"tensor of {t.numel()} elements where at least {n} are needed")
     return t.data_ptr()
+
+
+def _hptr(a, n: int = 0) -> int:
+    """Address of a C-contiguous float32 numpy array of at least n elements, or None for None."""
+    if a is None:
+        return None
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous float32 numpy array")
+    if a.size < n:
+        raise ValueError(f"array of {a.size} elements where at least {n} are needed")
+    return a.ctypes.data
 
 
 def _stream_handle(stream) -> int:
@@ -218,25 +240,28 @@ class Controller:
         """layers: three (W, b) CUDA float32 tensors, W of shape (fan_out, fan_in)."""
         H = self.cfg.hidden
         widths = (C.c_int32 * 4)(6, H, H, 4)
-        Ws = (C.c_void_p * 3)(*[_dptr(W) for W, _ in layers])
-        bs = (C.c_void_p * 3)(*[_dptr(b) for _, b in layers])
+        shapes = [(H * 6, H), (H * H, H), (4 * H, 4)]
+        if len(layers) != 3:
+            raise ValueError("expected three (W, b) layers")
+        Ws = (C.c_void_p * 3)(*[_dptr(W, nw) for (W, _), (nw, _) in zip(layers, shapes)])
+        bs = (C.c_void_p * 3)(*[_dptr(b, nb) for (_, b), (_, nb) in zip(layers, shapes)])
         self._check(self._L.itmpc_set_dynamics(self._h, 3, widths, Ws, bs, 1))
 
     def set_basis(self, theta):
         """Coefficients (25, 4) of the basis-function dynamics model (CUDA float32 tensor)."""
         if tuple(theta.shape) != (25, 4) or not theta.is_contiguous():
             raise ValueError("theta must be a contiguous (25, 4) tensor")
-        self._check(self._L.itmpc_set_basis(self._h, _dptr(theta), 1))
+        self._check(self._L.itmpc_set_basis(self._h, _dptr(theta, 100), 1))
 
     def set_costmap(self, cmap, res: float, origin_x: float, origin_y: float):
         """cmap: (height, width) CUDA float32 tensor."""
         h, w = cmap.shape
-        self._check(self._L.itmpc_set_costmap(self._h, _dptr(cmap), w, h, res, origin_x, origin_y, 1))
+        self._check(self._L.itmpc_set_costmap(self._h, _dptr(cmap, h * w), w, h, res, origin_x, origin_y, 1))
 
     def set_costmaps(self, cmaps, res: float, origin_x: float, origin_y: float):
         """cmaps: list of (height, width) CUDA float32 tensors of one size."""
         h, w = cmaps[0].shape
-        ptrs = (C.c_void_p * len(cmaps))(*[_dptr(m) for m in cmaps])
+        ptrs = (C.c_void_p * len(cmaps))(*[_dptr(m, h * w) for m in cmaps])
         self._check(self._L.itmpc_set_costmaps(self._h, len(cmaps), ptrs, w, h, res, origin_x, origin_y, 1))
 
     def reserve_batch(self, max_instances: int, max_total_samples: int):
@@ -248,8 +273,10 @@ class Controller:
         for a, d in zip(arr, instances):
             a.K, a.T, a.map_index = d["K"], d["T"], d.get("map_index", 0)
             a.instance, a.iter = d.get("instance", 0), d.get("iter", 0)
-            a.x0, a.U, a.U_out = _dptr(d["x0"]), _dptr(d["U"]), _dptr(d["U_out"])
-            a.weights, a.costs, a.stats = _dptr(d.get("weights")), _dptr(d.get("costs")), _dptr(d.get("stats"))
+            K, T = int(d["K"]), int(d["T"])
+            a.x0, a.U, a.U_out = _dptr(d["x0"], 7), _dptr(d["U"], 2 * T), _dptr(d["U_out"], 2 * T)
+            a.weights, a.costs = _dptr(d.get("weights"), K), _dptr(d.get("costs"), K)
+            a.stats = _dptr(d.get("stats"), STATS_LEN)
         return arr
 
     def iterate_batch(self, instances):
@@ -272,20 +299,26 @@ class Controller:
 
     def update_from_noise(self, eps, weights, U, U_out):
         """U_out = sum_k w_k v_k from materialised noise eps (K, T, 2) (device tensors)."""
-        self._check(self._L.itmpc_update_from_noise(self._h, _dptr(eps), _dptr(weights), _dptr(U), _dptr(U_out)))
+        K, T = self.cfg.K, self.cfg.T
+        self._check(self._L.itmpc_update_from_noise(self._h, _dptr(eps, 2 * K * T), _dptr(weights, K), _dptr(U, 2 * T),
+                                                    _dptr(U_out, 2 * T)))
 
     def iterate_cem(self, x0, U, it: int, delta: float, U_out, weights=None, costs=None):
         """One cross-entropy MPC iteration (Alg. 3 weights) on device tensors."""
-        self._check(self._L.itmpc_iterate_cem(self._h, _dptr(x0), _dptr(U), it, delta, _dptr(U_out),
-                                              _dptr(weights), _dptr(costs)))
+        K, T = self.cfg.K, self.cfg.T
+        self._check(self._L.itmpc_iterate_cem(self._h, _dptr(x0, 7), _dptr(U, 2 * T), it, delta, _dptr(U_out, 2 * T),
+                                              _dptr(weights, K), _dptr(costs, K)))
 
     def control_step(self, x, U, it: int, smoothing: int = SMOOTH_SGF, plant: int = 1, u_applied=None):
         """One closed-loop step of Alg. 1 on device tensors x (7) and U (T, 2), both updated in place."""
-        self._check(self._L.itmpc_control_step(self._h, _dptr(x), _dptr(U), it, smoothing, plant, _dptr(u_applied)))
+        T = self.cfg.T
+        self._check(self._L.itmpc_control_step(self._h, _dptr(x, 7), _dptr(U, 2 * T), it, smoothing, plant,
+                                               _dptr(u_applied, 2)))
 
     def control_graph_create(self, x, U, it0: int, smoothing: int = SMOOTH_SGF, plant: int = 1, u_applied=None):
-        self._check(self._L.itmpc_control_graph_create(self._h, _dptr(x), _dptr(U), it0, smoothing, plant,
-                                                       _dptr(u_applied)))
+        T = self.cfg.T
+        self._check(self._L.itmpc_control_graph_create(self._h, _dptr(x, 7), _dptr(U, 2 * T), it0, smoothing, plant,
+                                                       _dptr(u_applied, 2)))
 
     def control_graph_launch(self):
         self._check(self._L.itmpc_control_graph_launch(self._h))
@@ -301,14 +334,15 @@ class Controller:
 
     def iterate(self, x0, U, it: int, U_out, weights=None, costs=None):
         """Queue one iteration on the context's stream (device tensors)."""
-        self._check(self._L.itmpc_iterate(self._h, _dptr(x0), _dptr(U), it, _dptr(U_out), _dptr(weights),
-                                          _dptr(costs)))
+        K, T = self.cfg.K, self.cfg.T
+        self._check(self._L.itmpc_iterate(self._h, _dptr(x0, 7), _dptr(U, 2 * T), it, _dptr(U_out, 2 * T),
+                                          _dptr(weights, K), _dptr(costs, K)))
 
     def iterate_host(self, x0, U, it: int, U_out, weights=None, costs=None) -> int:
         """One synchronous iteration on host numpy float32 arrays; returns the status."""
-        def p(a):
-            return None if a is None else a.ctypes.data
-        st = self._L.itmpc_iterate_host(self._h, p(x0), p(U), it, p(U_out), p(weights), p(costs))
+        K, T = self.cfg.K, self.cfg.T
+        st = self._L.itmpc_iterate_host(self._h, _hptr(x0, 7), _hptr(U, 2 * T), it, _hptr(U_out, 2 * T),
+                                        _hptr(weights, K), _hptr(costs, K))
         if st not in (OK, ERR_NONFINITE):
             self._check(st)
         return st
@@ -322,11 +356,12 @@ class Controller:
         return list(out)
 
     def noise(self, it: int, eps):
-        self._check(self._L.itmpc_noise(self._h, it, _dptr(eps)))
+        self._check(self._L.itmpc_noise(self._h, it, _dptr(eps, 2 * self.cfg.K * self.cfg.T)))
 
     def rollout_states(self, x0, U, it: int, n: int, states, costs=None):
-        self._check(self._L.itmpc_rollout_states(self._h, _dptr(x0), _dptr(U), it, n, _dptr(states),
-                                                 _dptr(costs)))
+        K, T = self.cfg.K, self.cfg.T
+        self._check(self._L.itmpc_rollout_states(self._h, _dptr(x0, 7), _dptr(U, 2 * T), it, n,
+                                                 _dptr(states, max(n, 0) * (T + 1) * 7), _dptr(costs, K)))
 
     # -- adjoint form -----------------------------------------------------------
     def set_dynamics_packed(self, net):
@@ -349,14 +384,23 @@ class Controller:
 
     def iterate_fwd(self, x0, U, it: int, every: int, ckpt, U_out, weights, costs, J=None):
         """Forward pass of the adjoint form: itmpc_iterate plus checkpoints and J (device tensors)."""
-        self._check(self._L.itmpc_iterate_fwd(self._h, _dptr(x0), _dptr(U), it, every, _dptr(ckpt), _dptr(U_out),
-                                              _dptr(weights), _dptr(costs), _dptr(J)))
+        K, T = self.cfg.K, self.cfg.T
+        self._check(self._L.itmpc_iterate_fwd(self._h, _dptr(x0, 7), _dptr(U, 2 * T), it, every,
+                                              _dptr(ckpt, self._ckpt_need(every)), _dptr(U_out, 2 * T),
+                                              _dptr(weights, K), _dptr(costs, K), _dptr(J, 1)))
 
     def iterate_bwd(self, U, it: int, every: int, ckpt, weights, costs, U_out, gJ, gU_out, g_cost_w, g_U, g_net):
         """Backward pass: gradients of gJ J + sum gU_out . U' (gJ, gU_out device tensors or None)."""
-        self._check(self._L.itmpc_iterate_bwd(self._h, _dptr(U), it, every, _dptr(ckpt), _dptr(weights),
-                                              _dptr(costs), _dptr(U_out), _dptr(gJ), _dptr(gU_out),
-                                              _dptr(g_cost_w), _dptr(g_U), _dptr(g_net)))
+        K, T = self.cfg.K, self.cfg.T
+        self._check(self._L.itmpc_iterate_bwd(self._h, _dptr(U, 2 * T), it, every, _dptr(ckpt, self._ckpt_need(every)),
+                                              _dptr(weights, K), _dptr(costs, K), _dptr(U_out, 2 * T), _dptr(gJ, 1),
+                                              _dptr(gU_out, 2 * T), _dptr(g_cost_w, 4), _dptr(g_U, 2 * T),
+                                              _dptr(g_net, net_floats(self.cfg.hidden))))
+
+    def _ckpt_need(self, every: int) -> int:
+        """Checkpoint floats for a valid interval; 0 otherwise (the library refuses the interval)."""
+        n = int(self._L.itmpc_adjoint_ckpt_floats(self.cfg.K, self.cfg.T, every))
+        return max(n, 0)
 
 
 def net_floats(H: int) -> int:
@@ -426,14 +470,15 @@ def iterate_differentiable(ctl: Controller, x0, U, cost_w, net, it: int, every: 
 
 
 def philox(ctr, key, out, stream=None):
-    st = lib().itmpc_philox4x32_10(_dptr(ctr), (C.c_uint32 * 2)(*key), _dptr(out), ctr.shape[0],
+    st = lib().itmpc_philox4x32_10(_dptr(ctr, 4 * ctr.shape[0], True), (C.c_uint32 * 2)(*key),
+                                   _dptr(out, 4 * ctr.shape[0], True), ctr.shape[0],
                                    _stream_handle(stream))
     if st != OK:
         raise ItmpcError(st, "itmpc_philox4x32_10")
 
 
 def tanh_f32(x, y, stream=None):
-    st = lib().itmpc_tanh_f32(_dptr(x), _dptr(y), x.numel(), _stream_handle(stream))
+    st = lib().itmpc_tanh_f32(_dptr(x), _dptr(y, x.numel()), x.numel(), _stream_handle(stream))
     if st != OK:
         raise ItmpcError(st, "itmpc_tanh_f32")
 
@@ -465,8 +510,11 @@ def iterate_noalloc(cfg: Config, layers, cmap, res: float, origin_x: float, orig
     For callers that cannot allocate device memory while iterating; the
     library's scratch is a fixed device array shared by all calls on a device.
     """
-    Ws = (C.c_void_p * 3)(*[_dptr(W) for W, _ in layers])
-    bs = (C.c_void_p * 3)(*[_dptr(b) for _, b in layers])
+    H, K, T = cfg.hidden, cfg.K, cfg.T
+    shapes = [(H * 6, H), (H * H, H), (4 * H, 4)]
+    Ws = (C.c_void_p * 3)(*[_dptr(W, nw) for (W, _), (nw, _) in zip(layers, shapes)])
+    bs = (C.c_void_p * 3)(*[_dptr(b, nb) for (_, b), (_, nb) in zip(layers, shapes)])
     h, w = cmap.shape
-    return int(lib().itmpc_iterate_noalloc(C.byref(cfg), Ws, bs, _dptr(cmap), w, h, res, origin_x, origin_y,
-                                           _dptr(x0), _dptr(U), it, _dptr(U_out), _dptr(weights), _dptr(costs)))
+    return int(lib().itmpc_iterate_noalloc(C.byref(cfg), Ws, bs, _dptr(cmap, h * w), w, h, res, origin_x, origin_y,
+                                           _dptr(x0, 7), _dptr(U, 2 * T), it, _dptr(U_out, 2 * T), _dptr(weights, K),
+                                           _dptr(costs, K)))
