@@ -161,7 +161,7 @@ def _hptr(a, n: int = 0) -> int:
     """Address of a C-contiguous float32 numpy array of at least n elements, or None for None."""
     if a is None:
         return None
-    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags.c_contiguous:
+    if not isinstance(a, np.ndarray) or a.dtype.char != "f" or not a.flags.c_contiguous:
         raise ValueError("expected a C-contiguous float32 numpy array")
     if a.size < n:
         raise ValueError(f"array of {a.size} elements where at least {n} are needed")
