@@ -25,7 +25,8 @@
  *   - Errors never cross the ABI as exceptions: every call returns an
  *     itmpc_status, and itmpc_last_error() gives a message for the last
  *     failing call on a context.  Argument errors are detected before any GPU
- *     work is queued and leave the context unchanged.
+ *     work is queued and leave the context unchanged; every entry point that
+ *     takes a context returns ITMPC_ERR_ARG for a NULL one.
  *   - Noise is Philox-4x32-10 (Salmon et al., SC'11) with one block per
  *     (k, t): counter = (k, t, iter_lo, (iter_hi & 0xFFFF) | instance << 16),
  *     key = (seed_lo, seed_hi); words 0 and 1 give u_i = ((w_i >> 8) + 1) 2^-24
