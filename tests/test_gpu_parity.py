@@ -280,6 +280,27 @@ def test_million_samples_sampled():
     ctl.close()
 
 
+def test_maximum_samples_sampled():
+    """K = ITMPC_MAX_K = 2^24, the largest K a context accepts (thread-per-sample kernels): sampled
+    costs against the oracle, the first and last samples included; U' and the weights recomputed by
+    the oracle from all of the GPU's costs."""
+    from paper_1707_02342_gb300 import itmpc
+
+    K, T = itmpc.MAX_K, 8
+    params, tmap, layers = G.small_workload(K=K, T=T)
+    ctl = G.controller(params, tmap, layers)
+    P = oracle_for(params, tmap, layers)
+    x0 = problems.x0_for(tmap, speed=3.0)
+    U = inputs.nominal_controls(T, seed=5, scale=0.2)
+    Uo, w, S, st = G.run(ctl, x0, U, 13)
+    assert st == 0
+    ks = np.concatenate([np.arange(4), np.random.default_rng(3).choice(K, 44, replace=False), [K - 2, K - 1]])
+    S_ref, margins = oracle.rollout_many(P, x0, U, 13, ks)
+    check_costs(S[ks], S_ref, margins)
+    check_stagewise(P, 13, U, Uo, w, S, params["sigma"])
+    ctl.close()
+
+
 def test_host_graph_path_follows_iteration_and_parameters():
     """itmpc_iterate_host without weights / costs replays one captured graph (upload, iteration,
     download): each call's iteration index and the current parameters must be the ones used."""
