@@ -270,13 +270,12 @@ def _controller(K, T, H, tmap, layers, params, **kw):
     return ctl
 
 
-def measure_precision(params, flush, cores, steps: int = 50, warmup: int = 10):
+def measure_precision(params, flush, steps: int = 50, warmup: int = 10):
     """The precision form: K = 16384, T = 100, 6->128->128->4 network, FP32 vs BF16 vs FP8 (tcgen05),
-    each timed through itmpc_iterate and compared with the FP64 oracle run on every sample."""
-    import numpy as np
+    each timed through itmpc_iterate.  Returns the JSON object and the GPU outputs (costs, weights, U')
+    that the CPU-baseline leg compares with the FP64 oracle."""
     import torch
 
-    import oracle
     from paper_1707_02342_gb300 import inputs, itmpc
 
     K, T, H = 16384, 100, 128
@@ -286,15 +285,9 @@ def measure_precision(params, flush, cores, steps: int = 50, warmup: int = 10):
     x0[4] = 4.0
     U = inputs.nominal_controls(T, seed=9, scale=0.2)
     it = 5
-    P = oracle.Problem(K=K, T=T, layers=layers, costmap=tmap.data, res=tmap.res, origin_x=tmap.origin_x,
-                       origin_y=tmap.origin_y, lam=params["lam"], sigma=params["sigma"], cost_w=params["cost_w"],
-                       n_threads=cores)
-    t0 = time.perf_counter()
-    rc, U64, w64, S64 = oracle.iterate(P, x0, U, it)
-    t_oracle = time.perf_counter() - t0
-    J64 = float(np.sum(w64[w64 > 0] * S64[w64 > 0]))
     out = {"workload": f"it-mpc iteration K={K} T={T} 6->{H}->{H}->4 spline-1024 map",
-           "sample_steps_per_launch": K * T, "oracle_s": t_oracle}
+           "sample_steps_per_launch": K * T}
+    gpu = {}
     flop = 2 * (6 * H + H * H + 4 * H) * K * T
     x0_d, U_d = torch.tensor(x0, device="cuda"), torch.tensor(U, device="cuda")
     base_ms = None
@@ -303,28 +296,23 @@ def measure_precision(params, flush, cores, steps: int = 50, warmup: int = 10):
         Uo, w, S = torch.empty_like(U_d), torch.empty(K, device="cuda"), torch.empty(K, device="cuda")
         med, mean = _timed(lambda: ctl.iterate(x0_d, U_d, it, Uo, w, S), steps, warmup, flush)
         assert ctl.read_status() == itmpc.OK
-        Sg, wg, Ug = (t.double().cpu().numpy() for t in (S, w, Uo))
-        rel = np.abs(Sg - S64) / np.maximum(np.abs(S64), 1.0)
-        Jg = float(np.sum(wg[wg > 0] * Sg[wg > 0]))
+        gpu[name] = tuple(t.double().cpu().numpy() for t in (S, w, Uo))
         base_ms = base_ms or mean
         out[name] = {"ms_per_step": mean, "ms_median": med, "value": K * T / (mean * 1e-3), "unit": UNIT,
                      "speedup_vs_fp32": base_ms / mean, "algorithmic_tflops": flop / (mean * 1e-3) / 1e12,
-                     "err_vs_fp64": {"cost_rel_median": float(np.median(rel)),
-                                     "cost_rel_p99": float(np.quantile(rel, 0.99)),
-                                     "cost_rel_max": float(rel.max()),
-                                     "expected_cost_rel": abs(Jg - J64) / abs(J64),
-                                     "U_out_err_over_update": float(np.abs(Ug - U64).max() / np.abs(U64 - U).max())}}
+                     "err_vs_fp64": None}
         ctl.close()
-    return out
+    case = {"K": K, "T": T, "layers": layers, "tmap": tmap, "x0": x0, "U": U, "it": it, "gpu": gpu}
+    return out, case
 
 
-def measure_adjoint(params, flush, cores, steps: int = 50, warmup: int = 10, every: int = 10):
+def measure_adjoint(params, flush, steps: int = 50, warmup: int = 10, every: int = 10):
     """The adjoint form: K = 4096, T = 100, 6->64->64->4, checkpoints every 10 steps; forward + backward
-    time next to the plain iteration and to central differences, gradient error vs the FP64 oracle."""
+    time next to the plain iteration and to central differences.  Returns the JSON object and the GPU
+    gradients that the CPU-baseline leg compares with the FP64 oracle's."""
     import numpy as np
     import torch
 
-    import oracle
     from paper_1707_02342_gb300 import inputs
 
     K, T, H = 4096, 100, 64
@@ -349,28 +337,54 @@ def measure_adjoint(params, flush, cores, steps: int = 50, warmup: int = 10, eve
     bwd = _timed(lambda: ctl.iterate_bwd(U_d, it, every, ck, w, S, Uo, gJ, gU, g_cw, g_U, g_net), steps, warmup,
                  flush)[1]
     assert ctl.read_status() == 0
-    Sg = S.double().cpu().numpy()
     active = int(np.count_nonzero(w.cpu().numpy()))
-    P = oracle.Problem(K=K, T=T, layers=layers, costmap=tmap.data, res=tmap.res, origin_x=tmap.origin_x,
-                       origin_y=tmap.origin_y, lam=params["lam"], sigma=params["sigma"], cost_w=params["cost_w"],
-                       n_threads=cores)
-    ref = oracle.iterate_vjp(P, x0, U, it, 1.0, gU_h.astype(np.float64), S_use=Sg)
-    got = {"cost_w": g_cw, "U": g_U, "net": g_net}
-    want = {"cost_w": ref["g_cost_w"], "U": ref["g_U"], "net": ref["g_net"]}
-    err = {k: float(np.linalg.norm(got[k].double().cpu().numpy().ravel() - want[k].ravel()) /
-                    np.linalg.norm(want[k])) for k in got}
+    case = {"K": K, "T": T, "layers": layers, "tmap": tmap, "x0": x0, "U": U, "it": it, "gU": gU_h,
+            "S": S.double().cpu().numpy(),
+            "gpu": {k: v.double().cpu().numpy().ravel() for k, v in (("cost_w", g_cw), ("U", g_U), ("net", g_net))}}
     ctl.close()
     n_params = nf + 4 + 2 * T
     bwd_flop = 2 * 2 * (6 * H + H * H + 4 * H) * active * T  # reverse network sweep: twice the forward MACs
-    return {"workload": f"adjoint of one iteration K={K} T={T} 6->{H}->{H}->4 spline-1024 map, "
-                        f"checkpoints every {every} steps", "active_samples": active,
-            "plain_ms": plain, "fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_over_plain": (fwd + bwd) / plain,
-            "n_params": n_params,
-            "speedup_vs_central_differences": 2 * n_params * plain / (fwd + bwd),
-            "grad_rel_err_vs_fp64": err,
-            "bwd_roofline": {"bound": "alu", "achieved": bwd_flop / (bwd * 1e-3) / 1e12, "unit": "TFLOP/s",
-                             "algorithmic_flop": bwd_flop,
-                             "traffic": profiled_traffic(ADJ_PROFILE, ADJ_SOURCES)}}
+    out = {"workload": f"adjoint of one iteration K={K} T={T} 6->{H}->{H}->4 spline-1024 map, "
+                       f"checkpoints every {every} steps", "active_samples": active,
+           "plain_ms": plain, "fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_over_plain": (fwd + bwd) / plain,
+           "n_params": n_params,
+           "speedup_vs_central_differences": 2 * n_params * plain / (fwd + bwd),
+           "grad_rel_err_vs_fp64": None,
+           "bwd_roofline": {"bound": "alu", "achieved": bwd_flop / (bwd * 1e-3) / 1e12, "unit": "TFLOP/s",
+                            "algorithmic_flop": bwd_flop,
+                            "traffic": profiled_traffic(ADJ_PROFILE, ADJ_SOURCES)}}
+    return out, case
+
+
+def fp64_error_reports(forms, cases, params, cores):
+    """Part of the CPU-baseline leg: the FP64 oracle on the host cores computes the references of the
+    precision and adjoint forms' error reports from the GPU outputs measured above."""
+    import numpy as np
+
+    import oracle
+
+    def problem(c):
+        return oracle.Problem(K=c["K"], T=c["T"], layers=c["layers"], costmap=c["tmap"].data, res=c["tmap"].res,
+                              origin_x=c["tmap"].origin_x, origin_y=c["tmap"].origin_y, lam=params["lam"],
+                              sigma=params["sigma"], cost_w=params["cost_w"], n_threads=cores)
+
+    c = cases["precision"]
+    t0 = time.perf_counter()
+    rc, U64, w64, S64 = oracle.iterate(problem(c), c["x0"], c["U"], c["it"])
+    forms["precision"]["oracle_s"] = time.perf_counter() - t0
+    J64 = float(np.sum(w64[w64 > 0] * S64[w64 > 0]))
+    for name, (Sg, wg, Ug) in c["gpu"].items():
+        rel = np.abs(Sg - S64) / np.maximum(np.abs(S64), 1.0)
+        Jg = float(np.sum(wg[wg > 0] * Sg[wg > 0]))
+        forms["precision"][name]["err_vs_fp64"] = {
+            "cost_rel_median": float(np.median(rel)), "cost_rel_p99": float(np.quantile(rel, 0.99)),
+            "cost_rel_max": float(rel.max()), "expected_cost_rel": abs(Jg - J64) / abs(J64),
+            "U_out_err_over_update": float(np.abs(Ug - U64).max() / np.abs(U64 - c["U"]).max())}
+    c = cases["adjoint"]
+    ref = oracle.iterate_vjp(problem(c), c["x0"], c["U"], c["it"], 1.0, c["gU"].astype(np.float64), S_use=c["S"])
+    want = {"cost_w": ref["g_cost_w"], "U": ref["g_U"], "net": ref["g_net"]}
+    forms["adjoint"]["grad_rel_err_vs_fp64"] = {
+        k: float(np.linalg.norm(c["gpu"][k] - want[k].ravel()) / np.linalg.norm(want[k])) for k in want}
 
 
 def measure_closed_loop(tmap, layers, x0, U, params, flush, steps: int = 200, warmup: int = 10):
@@ -672,8 +686,7 @@ def run_ours(args, rank, world, local_rank):
                           "unit": "TFLOP/s"}
         bt["roofline"]["frac"] = bt["roofline"]["achieved"] / peak_tflops
         line["forms"] = {"batched": bt}
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-        pr = measure_precision(params, flush, cores)
+        pr, pr_case = measure_precision(params, flush)
         bf_peak = pk.get("bf16_tflops", 1900.0)
         for name, pkv in (("bf16", bf_peak), ("fp8", 2 * bf_peak)):
             pr[name]["roofline"] = {"bound": "tensor", "achieved": pr[name]["algorithmic_tflops"], "peak": pkv,
@@ -691,13 +704,19 @@ def run_ours(args, rank, world, local_rank):
         uh["roofline"] = {"bound": "hbm", "achieved": uh["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                           "frac": uh["achieved_gbs"] / hbm, "peak_note": "measured copy bandwidth"}
         line["forms"]["update_from_noise"] = uh
-        ad = measure_adjoint(params, flush, cores)
+        ad, ad_case = measure_adjoint(params, flush)
         ad["bwd_roofline"]["peak"] = peak_tflops
         ad["bwd_roofline"]["frac"] = ad["bwd_roofline"]["achieved"] / peak_tflops
         line["forms"]["adjoint"] = ad
     if world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_oracle_rate(seconds=args.cpu_seconds)
         line["cpu_baseline"] = cb
+        if "forms" in line:
+            cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+            fp64_error_reports(line["forms"], {"precision": pr_case, "adjoint": ad_case}, params, cores)
+            cb["also"] = "FP64 references of the precision and adjoint forms' error reports"
+    elif "forms" in line:
+        line["forms"]["error_reports"] = "skipped with the CPU-baseline leg (--no-cpu-baseline)"
     print(json.dumps(line), flush=True)
     ctl.close()
 
@@ -712,12 +731,11 @@ def run_only(args):
     nbuild.build()
     tmap, layers, x0, U, params = workload()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     steps, warm = max(1, args.steps), args.warmup
     if args.only == "batched":
         out = measure_batched(params, layers, steps=steps, warmup=warm)
     elif args.only == "precision":
-        out = measure_precision(params, flush, cores, steps=steps, warmup=warm)
+        out, _ = measure_precision(params, flush, steps=steps, warmup=warm)
     elif args.only == "update_from_noise":
         out = measure_update_hbm(params, layers, flush, steps=steps, warmup=warm)
     elif args.only == "basis":
@@ -727,7 +745,7 @@ def run_only(args):
     elif args.only == "closed_loop":
         out = measure_closed_loop(tmap, layers, x0, U, params, flush, steps=steps, warmup=warm)
     else:
-        out = measure_adjoint(params, flush, cores, steps=steps, warmup=warm)
+        out, _ = measure_adjoint(params, flush, steps=steps, warmup=warm)
     print(json.dumps({"only": args.only, **out}), flush=True)
 
 
