@@ -632,6 +632,11 @@ def run_ours(args, rank, world, local_rank):
     U_h = torch.tensor(U).pin_memory().numpy()
     Uo_h = torch.empty((T_WORK, 2), dtype=torch.float32).pin_memory().numpy()
     e2e_n = min(n, 500)
+    # untimed warm-up calls: the first call captures the context's host graph (and every call after a
+    # parameter change would); the timed calls replay it
+    for i in range(max(10, args.warmup)):
+        st = ctl.iterate_host(x0_h, U_h, i, Uo_h)
+        assert st == itmpc.OK
     e2e_s = []
     for i in range(e2e_n):
         flush.zero_()
@@ -670,7 +675,8 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step_median": float(np.median(step_ms)),
         "wall_s_timed_region_incl_flush": t_wall,
         "e2e": {"value": world * K_WORK * T_WORK / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": 4 * (7 + 2 * T_WORK),
-                "d2h_bytes_per_step": 4 * 2 * T_WORK, "steps": e2e_n,
+                "d2h_bytes_per_step": 4 * 2 * T_WORK, "steps": e2e_n, "warmup": max(10, args.warmup),
+                "us_per_call_mean": e2e_mean * 1e6, "us_per_call_median": float(np.median(e2e_s)) * 1e6,
                 "entry_point": "itmpc_iterate_host (pinned host buffers; includes copies and stream sync)"},
         "gpu_launches": n * launches_per_step,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",

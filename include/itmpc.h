@@ -360,6 +360,44 @@ itmpc_status itmpc_tanh_f32(const float *x, float *y, int64_t n, void *stream);
 itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *partials, const float *U,
                                   float lambda, float *U_out);
 
+/* ---- Sample-sharded iteration (one exchange of partial records) ----
+ * Alg. 2's weights need rho = min_k S_k and eta~ over all K samples, but both
+ * are log-sum-exp reductions: a subset of the samples can be reduced on its own
+ * to the partial record above (shifted by the subset's own minimum), and the
+ * records of disjoint subsets merge exactly into U' (Alg. 2's shift applied per
+ * shard, then across shards).  A K_total-sample iteration can therefore run as
+ * several contexts -- one per GPU, or several on one GPU -- each owning a
+ * contiguous range of global sample indices, followed by one exchange of
+ * ITMPC_PARTIAL_STRIDE(T) floats per shard (e.g. an all-gather) and a merge.
+ * Because the noise of sample k is Philox(k, t, iter) of its GLOBAL index, the
+ * sharded iteration draws exactly the samples of the unsharded one; its U'
+ * differs only by the order of the final sums.
+ *
+ * itmpc_iterate_shard: the context's K samples are global samples
+ * k_base .. k_base + K - 1 of an iteration of K_total samples.
+ *   x0, U, iter   as itmpc_iterate (device); every shard passes the same values
+ *   k_base        0 <= k_base and k_base + K <= K_total <= 2^31 - 1
+ *   K_total       the whole iteration's sample count: the exploration split of
+ *                 Alg. 1 (v = u + eps iff k < (1 - alpha) K_total) uses the global index
+ *   partial       device, ITMPC_PARTIAL_STRIDE(T) floats, 4-byte aligned: the shard's
+ *                 record [rho_s, eta_s, eta_imp_s, sum of squares, finite count, 0, 0, 0,
+ *                 E_s[T][2]] (as itmpc_merge_partials reads it)
+ *   costs         device K, or NULL: S of the shard's samples (local index)
+ * Works for every precision and network width of the context.  Asynchronous.
+ * The weights need the global rho and eta~: itmpc_merge_shards gives them.
+ *
+ * itmpc_merge_shards: merge n_shards records (device, 16-byte aligned, stride
+ * ITMPC_PARTIAL_STRIDE(T) for the context's T) on the GPU into U_out (device
+ * T x 2, may alias U) and the context's stats (itmpc_get_stats; the free energy
+ * uses K_total); when weights is given (device K), also the weights of this
+ * context's own samples from their costs (device K, as itmpc_iterate_shard
+ * wrote them) under the merged rho and eta~.  No shard with a finite cost:
+ * U_out = U, weights 0, device status ITMPC_ERR_NONFINITE.  Asynchronous. */
+itmpc_status itmpc_iterate_shard(itmpc_ctx *ctx, const float *x0, const float *U, uint64_t iter, int64_t k_base,
+                                 int64_t K_total, float *partial, float *costs);
+itmpc_status itmpc_merge_shards(itmpc_ctx *ctx, int32_t n_shards, const float *partials, int64_t K_total,
+                                const float *U, float *U_out, const float *costs, float *weights);
+
 /* One FP32 control iteration that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate GPU memory when they iterate -- a real-time control loop
@@ -375,12 +413,19 @@ itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *part
  *   x0, U, iter, U_out, weights, costs   as itmpc_iterate (device pointers)
  * Scratch comes from one file-scope device array of ITMPC_NOALLOC_SCRATCH_BYTES
  * that every GPU loading the library keeps until the process exits.  The
- * first call on a device resolves that array's address on the current device,
- * so make that first call before any stream capture.  Every call on a device
- * shares the array: calls whose work overlaps on the GPU (different streams or
- * threads without ordering) race and give wrong results.  The call queues its
- * work on cfg->stream, waits for it and returns the device-side status
- * (ITMPC_OK, ITMPC_ERR_NONFINITE with U copied to U_out, ITMPC_ERR_TIMEOUT). */
+ * first call on a device resolves that array's address on the current device
+ * (once per device).  Every call on a device shares the array and finds the
+ * previous call's contents there (the call clears what must start at zero):
+ * calls whose work overlaps on the GPU (different streams or threads without
+ * ordering) race and give wrong results.  The call queues its work on
+ * cfg->stream, then copies the device status to the host and synchronises
+ * that stream: it blocks until the iteration is done, so it must not be made
+ * while cfg->stream is capturing a CUDA graph.  It returns the device-side
+ * status (ITMPC_OK, ITMPC_ERR_NONFINITE with U copied to U_out,
+ * ITMPC_ERR_TIMEOUT).  The size limits hold on GB300 (227 KB of shared memory
+ * per block); on a GPU with less shared memory per block the kernel runs
+ * smaller CTAs, needs more scratch per sample, and the largest sizes may be
+ * refused with ITMPC_ERR_ARG. */
 #define ITMPC_NOALLOC_SCRATCH_BYTES (4u << 20)
 #define ITMPC_NOALLOC_MAX_K 8192
 #define ITMPC_NOALLOC_MAX_T 256

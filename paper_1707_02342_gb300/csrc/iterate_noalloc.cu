@@ -121,7 +121,11 @@ extern "C" itmpc_status itmpc_iterate_noalloc(const itmpc_config *cfg, const flo
   float *stats = (float *)take(sizeof(float) * ITMPC_STATS_LEN);
   unsigned int *counters = (unsigned int *)take(sizeof(unsigned int) * (size_t)(1 + nG + 2));
   int *status = (int *)take(sizeof(int));
-  if (off > (size_t)ITMPC_NOALLOC_SCRATCH_BYTES) return ITMPC_ERR_ARG;  // cannot happen within the stated limits
+  // With GB300's 227 KB of shared memory per block the tile picker's CTAs keep
+  // every size within the stated limits under about 2.2 MB of scratch.  A GPU
+  // with less shared memory per block gets smaller CTAs, hence more records, and
+  // the largest sizes can exceed the array: they are refused here.
+  if (off > (size_t)ITMPC_NOALLOC_SCRATCH_BYTES) return ITMPC_ERR_ARG;
 
   cudaStream_t s = (cudaStream_t)cfg->stream;
   const size_t nW[3] = {(size_t)6 * H, (size_t)H * H, (size_t)4 * H};

@@ -43,6 +43,7 @@
 
 #include "itmpc_device.cuh"
 #include "itmpc_merge.cuh"
+#include "itmpc_sum.cuh"
 #include "itmpc_tcgen05.cuh"
 #include "itmpc_units.cuh"
 
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int unit_s;
   __shared__ int abort_s;
-  __shared__ float red[4][5];
+  __shared__ float red[4][8];
   volatile int *abort_v = &abort_s;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -355,11 +356,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       } else {
         // ---------------- epilogue warps ----------------
         const int k = un.k0 + s;
-        const bool imp = k < I.n_imp;
+        const bool imp = (long long)I.k_base + k < I.n_imp;  // global index (sharded iterations)
         const float *map = sh.maps + (size_t)I.map * (size_t)sh.map_stride;
         const bool state = sub == 0, coster = sub == 2;
         const bool dbg = state && sh.states_out && un.inst == 0 && k < sh.n_states;
-        float px = 0.f, py = 0.f, th = 0.f, xd0 = 0.f, xd1 = 0.f, xd2 = 0.f, xd3 = 0.f, cc = 0.f, S = 0.f;
+        float px = 0.f, py = 0.f, th = 0.f, xd0 = 0.f, xd1 = 0.f, xd2 = 0.f, xd3 = 0.f, cc = 0.f;
+        CSum S;  // running cost over t, compensated
         auto save_state = [&](int t) {
           float *o = sh.states_out + ((size_t)k * (T + 1) + t) * 7;
           o[0] = px; o[1] = py; o[2] = th; o[3] = xd0; o[4] = xd1; o[5] = xd2; o[6] = xd3;
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int nst = min(Tc, T - t);
             for (int it = tid; it < nst * kRows; it += kEpiThreads) {
               const int tt = it / kRows, s2 = it % kRows;
-              eps_s[it] = tps_noise(sh, (uint32_t)(un.k0 + s2), (uint32_t)(t + tt), I.ctr2, I.ctr3);
+              eps_s[it] = tps_noise(sh, I.k_base + (uint32_t)(un.k0 + s2), (uint32_t)(t + tt), I.ctr2, I.ctr3);
             }
             nbar_sync(kBarNoise, kEpiThreads);
           }
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tc_fence_after();
           epilogue<ACT, FP8, false>(t_lane, 0, kColH1, sub, 1.0f);
           nbar_arrive(kBarH1, kTcThreads);
-          if (coster && t > 0) S += cost_finish(sh, cf, t) + cc_prev;  // running cost of x(t) (Alg. 1)
+          if (coster && t > 0) S.add(cost_finish(sh, cf, t) + cc_prev);  // running cost of x(t) (Alg. 1)
           // layer-2 epilogue: h2 = tanh(D2)
           nbar_sync(kBarD2, kTcThreads);
           tc_fence_after();
@@ -451,8 +453,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (coster) {
           nbar_sync(kBarState, 256);
           cf = cost_fetch(sh, map, st_s[s]);
-          S += cost_finish(sh, cf, T) + cc_s[s];
-          S_s[s] = S;
+          S.add(cost_finish(sh, cf, T) + cc_s[s]);
+          S_s[s] = S.value();
         }
       }
       if (__syncthreads_or(*abort_v)) break;
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (warp < 4) {
         const int kk = un.k0 + tid;
         live = kk < K;
-        impk = kk < I.n_imp;
+        impk = (long long)I.k_base + kk < I.n_imp;
         Sv = S_s[tid];
         if (live) I.costs[kk] = Sv;
         fin = live && isfinite(Sv);
@@ -475,19 +477,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (warp < 4) {
         const float e = (fin && isfinite(rho)) ? expf(-(Sv - rho) * sh.inv_lambda) : 0.0f;
         e_s[tid] = e;
-        const float eta = warp_sum(e), eta_imp = warp_sum(impk && live ? e : 0.0f);
-        const float sq = warp_sum(e * e), nf = warp_sum(fin ? 1.0f : 0.0f);
+        CSum ce, ci, cq;  // compensated (itmpc_sum.cuh)
+        ce.s = e;
+        ci.s = impk && live ? e : 0.0f;
+        cq.add_prod(e, e);
+        ce = csum_warp(ce);
+        ci = csum_warp(ci);
+        cq = csum_warp(cq);
+        const float nf = warp_sum(fin ? 1.0f : 0.0f);
         if (lane == 0) {
-          red[warp][1] = eta; red[warp][2] = eta_imp; red[warp][3] = sq; red[warp][4] = nf;
+          red[warp][1] = ce.s; red[warp][2] = ce.c; red[warp][3] = ci.s; red[warp][4] = ci.c;
+          red[warp][5] = cq.s; red[warp][6] = cq.c; red[warp][7] = nf;
         }
       }
       __syncthreads();
       const int PL = partial_len(T);
       float *rec = sh.partials + I.rec_off + (size_t)un.idx * PL;
       if (tid == 0) {
-        float a = 0.f, bb = 0.f, c = 0.f, d = 0.f;
-        for (int w = 0; w < 4; ++w) { a += red[w][1]; bb += red[w][2]; c += red[w][3]; d += red[w][4]; }
-        rec[0] = rho; rec[1] = a; rec[2] = bb; rec[3] = c; rec[4] = d;
+        CSum a, bb, c;
+        float d = 0.f;
+        for (int w = 0; w < 4; ++w) {
+          a.add(CSum{red[w][1], red[w][2]});
+          bb.add(CSum{red[w][3], red[w][4]});
+          c.add(CSum{red[w][5], red[w][6]});
+          d += red[w][7];
+        }
+        rec[0] = rho; rec[1] = a.value(); rec[2] = bb.value(); rec[3] = c.value(); rec[4] = d;
         rec[5] = 0.f; rec[6] = 0.f; rec[7] = 0.f;
       }
       // E_c[t] = sum_s e_s eps_s(t): item (t, quarter) sums 32 samples -- from the noise block when
@@ -498,25 +513,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int item = tid + r * kTcThreads;
         const bool valid = item < 4 * T;
         const int t = item >> 2, qq = item & 3;
-        float a0 = 0.f, a1 = 0.f;
+        CSum a0, a1;
         if (valid) {
           for (int s2 = qq * 32; s2 < qq * 32 + 32; ++s2) {
             const float es = e_s[s2];
             if (es != 0.0f) {
               const float2 ep = resident ? eps_s[t * kRows + s2]
-                                         : tps_noise(sh, (uint32_t)(un.k0 + s2), (uint32_t)t, I.ctr2, I.ctr3);
-              a0 = fmaf(es, ep.x, a0);
-              a1 = fmaf(es, ep.y, a1);
+                                         : tps_noise(sh, I.k_base + (uint32_t)(un.k0 + s2), (uint32_t)t, I.ctr2, I.ctr3);
+              a0.add_prod(es, ep.x);
+              a1.add_prod(es, ep.y);
             }
           }
         }
-        a0 += __shfl_xor_sync(FULL_MASK, a0, 1);
-        a1 += __shfl_xor_sync(FULL_MASK, a1, 1);
-        a0 += __shfl_xor_sync(FULL_MASK, a0, 2);
-        a1 += __shfl_xor_sync(FULL_MASK, a1, 2);
+        a0 = csum_lanes(a0, 4);
+        a1 = csum_lanes(a1, 4);
         if (valid && qq == 0) {
-          rec[8 + 2 * t] = a0;
-          rec[8 + 2 * t + 1] = a1;
+          rec[8 + 2 * t] = a0.value();
+          rec[8 + 2 * t + 1] = a1.value();
         }
       }
     }

@@ -26,6 +26,7 @@
 
 #include "itmpc_device.cuh"
 #include "itmpc_merge.cuh"
+#include "itmpc_sum.cuh"
 #include "itmpc_units.cuh"
 
 namespace itmpc {
@@ -107,7 +108,7 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
   const DYN &dyn = P.dyn;
   __shared__ float U_s[2 * ITMPC_MAX_T_DEV];
   __shared__ float e_s[NT];
-  __shared__ float red[NWARP][5];
+  __shared__ float red[NWARP][8];
   __shared__ int unit_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -125,9 +126,9 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
 
     const int k = un.k0 + tid;
     const bool live = k < K;
-    const bool imp = k < I.n_imp;
+    const bool imp = (long long)I.k_base + k < I.n_imp;  // global index (sharded iterations)
     const float *map = sh.maps + (size_t)I.map * (size_t)sh.map_stride;
-    float S = 0.0f;
+    CSum Sc;  // S_k = sum_t c_t, compensated
     if (live) {
       float px = __ldg(I.x0 + 0), py = __ldg(I.x0 + 1), th = __ldg(I.x0 + 2);
       float xd0 = __ldg(I.x0 + 3), xd1 = __ldg(I.x0 + 4), xd2 = __ldg(I.x0 + 5), xd3 = __ldg(I.x0 + 6);
@@ -139,7 +140,7 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
         st_o[0] = px; st_o[1] = py; st_o[2] = th; st_o[3] = xd0; st_o[4] = xd1; st_o[5] = xd2; st_o[6] = xd3;
       }
       for (int t = 0; t < T; ++t) {
-        const float2 e = tps_noise(sh, (uint32_t)k, (uint32_t)t, I.ctr2, I.ctr3);
+        const float2 e = tps_noise(sh, I.k_base + (uint32_t)k, (uint32_t)t, I.ctr2, I.ctr3);
         const float u0 = U_s[2 * t], u1 = U_s[2 * t + 1];
         const float v0 = imp ? u0 + e.x : e.x, v1 = imp ? u1 + e.y : e.y;
         const float g0 = fminf(fmaxf(v0, sh.umin0), sh.umax0), g1 = fminf(fmaxf(v1, sh.umin1), sh.umax1);
@@ -164,10 +165,11 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
         // running cost at x(t + 1) (Alg. 1) and the control-cost term (Sec. III-E)
         float c = tps_state_cost(sh, map, px, py, xd1, xd2, t + 1);
         if (sh.gamma != 0.0f) c += sh.gamma * (u0 * v0 * sh.inv_sig2_0 + u1 * v1 * sh.inv_sig2_1);
-        S += c;
+        Sc.add(c);
       }
-      I.costs[k] = S;
+      I.costs[k] = Sc.value();
     }
+    const float S = Sc.value();
 
     // this unit's partial record (Alg. 2 shifted by the unit's own minimum)
     const bool fin = live && isfinite(S);
@@ -179,19 +181,33 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
     for (int w = 0; w < NWARP; ++w) rho = fminf(rho, red[w][0]);
     const float e = (fin && isfinite(rho)) ? expf(-(S - rho) * sh.inv_lambda) : 0.0f;
     e_s[tid] = e;
-    const float eta = warp_sum(e), eta_imp = warp_sum(imp && live ? e : 0.0f);
-    const float sq = warp_sum(e * e), nf = warp_sum(fin ? 1.0f : 0.0f);
+    // compensated sums (itmpc_sum.cuh) over the warp, then over the warps
+    CSum ce, ci, cq;
+    ce.s = e;
+    ci.s = imp && live ? e : 0.0f;
+    cq.add_prod(e, e);
+    ce = csum_warp(ce);
+    ci = csum_warp(ci);
+    cq = csum_warp(cq);
+    const float nf = warp_sum(fin ? 1.0f : 0.0f);
     __syncthreads();  // every thread has read red[.][0]
     if (lane == 0) {
-      red[warp][1] = eta; red[warp][2] = eta_imp; red[warp][3] = sq; red[warp][4] = nf;
+      red[warp][1] = ce.s; red[warp][2] = ce.c; red[warp][3] = ci.s; red[warp][4] = ci.c;
+      red[warp][5] = cq.s; red[warp][6] = cq.c; red[warp][7] = nf;
     }
     __syncthreads();
     const int PL = partial_len(T);
     float *rec = sh.partials + I.rec_off + (size_t)un.idx * PL;
     if (tid == 0) {
-      float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
-      for (int w = 0; w < NWARP; ++w) { a += red[w][1]; b += red[w][2]; c += red[w][3]; d += red[w][4]; }
-      rec[0] = rho; rec[1] = a; rec[2] = b; rec[3] = c; rec[4] = d;
+      CSum a, b, c;
+      float d = 0.f;
+      for (int w = 0; w < NWARP; ++w) {
+        a.add(CSum{red[w][1], red[w][2]});
+        b.add(CSum{red[w][3], red[w][4]});
+        c.add(CSum{red[w][5], red[w][6]});
+        d += red[w][7];
+      }
+      rec[0] = rho; rec[1] = a.value(); rec[2] = b.value(); rec[3] = c.value(); rec[4] = d;
       rec[5] = 0.f; rec[6] = 0.f; rec[7] = 0.f;
     }
     // E_c[t] = sum_s e_s eps_s(t): item (t, group) sums 32 samples; the noise is
@@ -202,25 +218,22 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
       const int item = tid + r * NT;
       const bool valid = item < G * T;
       const int t = item / G, q = item % G;
-      float a0 = 0.f, a1 = 0.f;
+      CSum a0, a1;
       if (valid) {
         for (int s2 = q * 32; s2 < q * 32 + 32; ++s2) {
           const float es = e_s[s2];
           if (es != 0.0f) {
-            const float2 ep = tps_noise(sh, (uint32_t)(un.k0 + s2), (uint32_t)t, I.ctr2, I.ctr3);
-            a0 = fmaf(es, ep.x, a0);
-            a1 = fmaf(es, ep.y, a1);
+            const float2 ep = tps_noise(sh, I.k_base + (uint32_t)(un.k0 + s2), (uint32_t)t, I.ctr2, I.ctr3);
+            a0.add_prod(es, ep.x);
+            a1.add_prod(es, ep.y);
           }
         }
       }
-#pragma unroll
-      for (int o = 1; o < G; o <<= 1) {
-        a0 += __shfl_xor_sync(FULL_MASK, a0, o);
-        a1 += __shfl_xor_sync(FULL_MASK, a1, o);
-      }
+      a0 = csum_lanes(a0, G);
+      a1 = csum_lanes(a1, G);
       if (valid && q == 0) {
-        rec[8 + 2 * t] = a0;
-        rec[8 + 2 * t + 1] = a1;
+        rec[8 + 2 * t] = a0.value();
+        rec[8 + 2 * t + 1] = a1.value();
       }
     }
   }
@@ -249,7 +262,7 @@ __global__ void __launch_bounds__(kMergeThreads) tps_merge_kernel(const __grid_c
   if (threadIdx.x == 0) mbar_init(&mbar, 1);
   __syncthreads();
   uint32_t phase = 0;
-  merge_records<kMergeThreads>(q, sh.partials + I.rec_off, I.n_units, nullptr, reinterpret_cast<float *>(smem),
+  merge_records<kMergeThreads>(q, sh.partials + I.rec_off, I.n_units, I.rec_out, reinterpret_cast<float *>(smem),
                                stage_floats, &mbar, phase);
 }
 

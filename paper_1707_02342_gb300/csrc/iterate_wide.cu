@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "itmpc_device.cuh"
+#include "itmpc_sum.cuh"
 #include "itmpc_units.cuh"
 
 namespace itmpc {
@@ -122,9 +123,10 @@ __global__ void __launch_bounds__(WideShape<H>::NT, WideShape<H>::MIN_CTAS)
     const int k = un.k0 + lane;
     const bool owner = warp == 0 && lane < S;
     const bool live = owner && k < K;
-    const bool imp = k < I.n_imp;
+    const bool imp = (long long)I.k_base + k < I.n_imp;  // global index (sharded iterations)
     const bool dbg = live && sh.states_out != nullptr && un.inst == 0 && k < sh.n_states;
-    float px = 0.f, py = 0.f, th = 0.f, xd0 = 0.f, xd1 = 0.f, xd2 = 0.f, xd3 = 0.f, Sacc = 0.f;
+    float px = 0.f, py = 0.f, th = 0.f, xd0 = 0.f, xd1 = 0.f, xd2 = 0.f, xd3 = 0.f;
+    CSum Sacc;  // running cost over t, compensated
     // the pending running-cost lookup (texels of x_t loaded one step ahead)
     float pa = 0.f, pb = 0.f, m00 = 0.f, m01 = 0.f, m10 = 0.f, m11 = 0.f, pvx = 0.f, pvy = 0.f;
     if (owner) {
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(WideShape<H>::NT, WideShape<H>::MIN_CTAS)
         __syncthreads();  // the previous block's noise has been used
         for (int item = tid; item < kChunk * S; item += NT) {
           const int s = item % S, tt = item / S;
-          eps_s[item] = (t + tt < T) ? tps_noise(sh, (uint32_t)(un.k0 + s), (uint32_t)(t + tt), I.ctr2, I.ctr3)
+          eps_s[item] = (t + tt < T) ? tps_noise(sh, I.k_base + (uint32_t)(un.k0 + s), (uint32_t)(t + tt), I.ctr2, I.ctr3)
                                      : make_float2(0.f, 0.f);
         }
         __syncthreads();
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(WideShape<H>::NT, WideShape<H>::MIN_CTAS)
         const float2 e = eps_s[tc * S + lane];
         const float u0 = U_s[2 * t], u1 = U_s[2 * t + 1];
         const float v0 = imp ? u0 + e.x : e.x, v1 = imp ? u1 + e.y : e.y;
-        if (sh.gamma != 0.0f) Sacc += sh.gamma * (u0 * v0 * sh.inv_sig2_0 + u1 * v1 * sh.inv_sig2_1);
+        if (sh.gamma != 0.0f) Sacc.add(sh.gamma * (u0 * v0 * sh.inv_sig2_0 + u1 * v1 * sh.inv_sig2_1));
         zT[0 * S + lane] = xd0;
         zT[1 * S + lane] = xd1;
         zT[2 * S + lane] = xd2;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(WideShape<H>::NT, WideShape<H>::MIN_CTAS)
         if (t > 0) {  // cost of x_t (loop index t) from the texels loaded last step
           float hh = (1.0f - pa) * (1.0f - pb) * m00 + pa * (1.0f - pb) * m01 + (1.0f - pa) * pb * m10 +
                      pa * pb * m11;
-          Sacc += tps_cost_from_h(sh, hh, pvx, pvy, t);
+          Sacc.add(tps_cost_from_h(sh, hh, pvx, pvy, t));
         }
         float sn, cs;
         sincosf(th, &sn, &cs);
@@ -290,18 +292,21 @@ __global__ void __launch_bounds__(WideShape<H>::NT, WideShape<H>::MIN_CTAS)
     if (owner) {
       const float hh = (1.0f - pa) * (1.0f - pb) * m00 + pa * (1.0f - pb) * m01 + (1.0f - pa) * pb * m10 +
                        pa * pb * m11;
-      Sacc += tps_cost_from_h(sh, hh, pvx, pvy, T);
-      if (live) I.costs[k] = Sacc;
+      Sacc.add(tps_cost_from_h(sh, hh, pvx, pvy, T));
+      if (live) I.costs[k] = Sacc.value();
     }
+    const float Sv = Sacc.value();
 
     // ---- this unit's partial record (Alg. 2 shifted by the unit's own minimum) ----
     if (warp == 0) {
-      const bool fin = live && isfinite(Sacc);
-      const float rho = warp_min(fin ? Sacc : INFINITY);
-      const float e = (fin && isfinite(rho)) ? expf(-(Sacc - rho) * sh.inv_lambda) : 0.0f;
+      const bool fin = live && isfinite(Sv);
+      const float rho = warp_min(fin ? Sv : INFINITY);
+      const float e = (fin && isfinite(rho)) ? expf(-(Sv - rho) * sh.inv_lambda) : 0.0f;
       if (lane < S) e_s[lane] = e;
-      const float eta = warp_sum(e), eta_imp = warp_sum(imp && live ? e : 0.0f);
-      const float sq = warp_sum(e * e), nf = warp_sum(fin ? 1.0f : 0.0f);
+      CSum cq;
+      cq.add_prod(e, e);
+      const float eta = warp_csum(e), eta_imp = warp_csum(imp && live ? e : 0.0f);
+      const float sq = csum_warp(cq).value(), nf = warp_sum(fin ? 1.0f : 0.0f);
       if (lane == 0) {
         red[0] = rho; red[1] = eta; red[2] = eta_imp; red[3] = sq; red[4] = nf;
       }
@@ -315,17 +320,17 @@ __global__ void __launch_bounds__(WideShape<H>::NT, WideShape<H>::MIN_CTAS)
     }
     // E_c[t] = sum_s e_s eps_s(t), the noise drawn again from its counter (e = 0 skipped)
     for (int t = tid; t < T; t += NT) {
-      float a0 = 0.f, a1 = 0.f;
+      CSum a0, a1;
       for (int s = 0; s < S; ++s) {
         const float es = e_s[s];
         if (es != 0.0f) {
-          const float2 ep = tps_noise(sh, (uint32_t)(un.k0 + s), (uint32_t)t, I.ctr2, I.ctr3);
-          a0 = fmaf(es, ep.x, a0);
-          a1 = fmaf(es, ep.y, a1);
+          const float2 ep = tps_noise(sh, I.k_base + (uint32_t)(un.k0 + s), (uint32_t)t, I.ctr2, I.ctr3);
+          a0.add_prod(es, ep.x);
+          a1.add_prod(es, ep.y);
         }
       }
-      rec[8 + 2 * t] = a0;
-      rec[8 + 2 * t + 1] = a1;
+      rec[8 + 2 * t] = a0.value();
+      rec[8 + 2 * t + 1] = a1.value();
     }
   }
 }

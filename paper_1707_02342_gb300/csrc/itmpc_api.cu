@@ -244,10 +244,19 @@ extern "C" itmpc_status itmpc_reserve_batch(itmpc_ctx *c, int32_t max_instances,
 
 namespace {
 
+// One shard of a sample-sharded iteration: the context's samples are global samples
+// k_base .. k_base + K - 1, the exploration split counts n_imp global samples, and the merged
+// partial record goes to rec_out instead of U', the weights and the stats.
+struct ShardSpec {
+  uint32_t k_base;
+  int n_imp;
+  float *rec_out;
+};
+
 itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
-                       int states_every = 1);
+                       int states_every = 1, const ShardSpec *shard = nullptr);
 itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
-                            TpsTile tile, int states_every = 1);
+                            TpsTile tile, int states_every = 1, const ShardSpec *shard = nullptr);
 itmpc_status build_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, int nt, TpsInstance *inst_h,
                          TpsUnit *units_h, int *n_units);
 TpsShared batch_shared(const itmpc_ctx *c, const TpsInstance *inst_d, const TpsUnit *units_d, int n, int n_units);
@@ -257,7 +266,7 @@ int batch_nt(const itmpc_ctx *c);
 
 itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, float *U_out,
                            float *weights, float *costs, float *states, int n_states, float *eps_out,
-                           int states_every = 1) {
+                           int states_every = 1, const ShardSpec *shard = nullptr) {
   const bool tc = c->cfg.precision != ITMPC_FP32;
   if (tc || (!eps_out && single_as_batch(c, states != nullptr))) {
     // the tensor-core kernels, or many samples: the thread-per-sample kernels, as a batch of one instance
@@ -274,7 +283,7 @@ itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64
     q.weights = weights;
     q.costs = costs ? costs : c->costs;
     q.stats = c->stats;
-    return run_batch(c, 1, &q, states, n_states, states_every);
+    return run_batch(c, 1, &q, states, n_states, states_every, shard);
   }
   IterParams p = make_params(c);
   set_iter(p, iter, c->cfg.instance);
@@ -288,6 +297,12 @@ itmpc_status run_iteration(itmpc_ctx *c, const float *x0, const float *U, uint64
   p.states_every = states_every;
   p.eps_out = eps_out;
   if (costs) p.costs = costs;  // write S_k straight into the caller's buffer
+  if (shard) {
+    p.k_base = shard->k_base;
+    p.n_imp = shard->n_imp;
+    p.rec_out = shard->rec_out;
+    p.weights = nullptr;
+  }
   const Fp32Tile tile = fp32_pick_tile(p.K, p.T, p.H, c->smem_optin);
   CK(c, fp32_launch_iterate(p, tile, c->stream), "fused FP32 iteration launch");
   if (weights && !p.weights_inline) CK(c, launch_finalize_weights(p, c->stream), "weights launch");
@@ -764,6 +779,8 @@ itmpc_status build_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, in
     d.weights = q.weights;
     d.costs = q.costs ? q.costs : c->batch_costs + cost_off;
     d.stats = q.stats ? q.stats : c->batch_stats + (size_t)ITMPC_STATS_LEN * i;
+    d.k_base = 0;
+    d.rec_out = nullptr;
     cost_off += q.K;
   }
   int u = 0;
@@ -853,7 +870,7 @@ itmpc_status batch_ready(itmpc_ctx *c) {
 }
 
 itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
-                            TpsTile tile, int states_every) {
+                            TpsTile tile, int states_every, const ShardSpec *shard) {
   itmpc_status st = batch_ready(c);
   if (st != ITMPC_OK) return st;
   const int nt = (c->cfg.precision == ITMPC_FP32 && (c->H == 32 || c->cfg.dynamics == ITMPC_DYN_BASIS))
@@ -863,6 +880,12 @@ itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst,
   int u = 0;
   st = build_batch(c, n, inst, nt, c->inst_h, c->units_h, &u);
   if (st != ITMPC_OK) return st;
+  if (shard) {  // a batch of one instance: the shard of a sample-sharded iteration
+    c->inst_h[0].k_base = shard->k_base;
+    c->inst_h[0].n_imp = shard->n_imp;
+    c->inst_h[0].rec_out = shard->rec_out;
+    c->inst_h[0].weights = nullptr;
+  }
   CK(c, cudaMemcpyAsync(c->inst_d, c->inst_h, sizeof(TpsInstance) * n, cudaMemcpyHostToDevice, c->stream), "copy");
   CK(c, cudaMemcpyAsync(c->units_d, c->units_h, sizeof(TpsUnit) * u, cudaMemcpyHostToDevice, c->stream), "copy");
   CK(c, cudaEventRecord(c->staged, c->stream), "event");
@@ -874,9 +897,9 @@ itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst,
 }
 
 itmpc_status run_batch(itmpc_ctx *c, int32_t n, const itmpc_instance *inst, float *states, int n_states,
-                       int states_every) {
+                       int states_every, const ShardSpec *shard) {
   if (!c) return ITMPC_ERR_ARG;
-  return run_batch_tile(c, n, inst, states, n_states, c->tps_tile, states_every);
+  return run_batch_tile(c, n, inst, states, n_states, c->tps_tile, states_every, shard);
 }
 
 }  // namespace
@@ -1071,11 +1094,47 @@ itmpc_status itmpc_merge_partials(int32_t n_shards, int32_t T, const float *part
   return ITMPC_OK;
 }
 
+itmpc_status itmpc_iterate_shard(itmpc_ctx *c, const float *x0, const float *U, uint64_t iter, int64_t k_base,
+                                 int64_t K_total, float *partial, float *costs) {
+  itmpc_status st = ready(c);
+  if (st != ITMPC_OK) return st;
+  if (!x0 || !U || !partial) return fail(c, ITMPC_ERR_ARG, "x0, U and partial must be non-NULL");
+  if ((reinterpret_cast<uintptr_t>(partial) & 3u) != 0) return fail(c, ITMPC_ERR_ARG, "partial must be 4-byte aligned");
+  const int64_t K = c->cfg.K;
+  if (k_base < 0 || K_total < k_base + K || K_total > (int64_t)INT32_MAX)
+    return fail(c, ITMPC_ERR_ARG, "need 0 <= k_base, k_base + K <= K_total <= 2^31 - 1 (k_base=%lld K=%lld K_total=%lld)",
+                (long long)k_base, (long long)K, (long long)K_total);
+  const double nimp = ceil((1.0 - (double)c->cfg.alpha_explore) * (double)K_total);
+  ShardSpec sp{};
+  sp.k_base = (uint32_t)k_base;
+  sp.n_imp = (int)(nimp < 0 ? 0 : (nimp > (double)K_total ? K_total : nimp));
+  sp.rec_out = partial;
+  return run_iteration(c, x0, U, iter, c->Uout_d, nullptr, costs, nullptr, 0, nullptr, 1, &sp);
+}
+
+itmpc_status itmpc_merge_shards(itmpc_ctx *c, int32_t n_shards, const float *partials, int64_t K_total,
+                                const float *U, float *U_out, const float *costs, float *weights) {
+  if (!c) return ITMPC_ERR_ARG;
+  if (n_shards < 1 || !partials || !U || !U_out) return fail(c, ITMPC_ERR_ARG, "n_shards >= 1, partials, U, U_out");
+  if (K_total < 1 || K_total > (int64_t)INT32_MAX) return fail(c, ITMPC_ERR_ARG, "K_total outside [1, 2^31 - 1]");
+  if (weights && !costs) return fail(c, ITMPC_ERR_ARG, "weights need this device's costs");
+  if ((reinterpret_cast<uintptr_t>(partials) & 15u) != 0)
+    return fail(c, ITMPC_ERR_ARG, "partials must be 16-byte aligned (records are copied in bulk)");
+  IterParams p = make_params(c);
+  p.K = (int)K_total;  // the free energy's normalisation
+  p.U = U;
+  p.U_out = U_out;
+  p.costs = const_cast<float *>(costs);
+  p.weights = weights;
+  p.n_states = costs ? c->cfg.K : 0;
+  CK(c, launch_merge_records(p, partials, n_shards, c->stream), "shard merge launch");
+  return ITMPC_OK;
+}
+
 itmpc_status itmpc_update_from_noise(itmpc_ctx *c, const float *eps, const float *weights, const float *U,
                                      float *U_out) {
   if (!c) return ITMPC_ERR_ARG;
   if (!eps || !weights || !U || !U_out) return fail(c, ITMPC_ERR_ARG, "eps, weights, U and U_out must be non-NULL");
-  if (U_out == U) return fail(c, ITMPC_ERR_ARG, "U_out may not alias U");
   if (reinterpret_cast<uintptr_t>(eps) & 7u) return fail(c, ITMPC_ERR_ARG, "eps must be 8-byte aligned");
   const IterParams p = make_params(c);
   CK(c, wsum_launch(p.K, p.T, p.n_imp, eps, weights, U, U_out, c->wsum_part, c->sms, c->stream),

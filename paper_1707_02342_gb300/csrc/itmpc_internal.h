@@ -64,6 +64,11 @@ struct IterParams {
   int states_every;    // 1: the whole trajectory; N: the adjoint form's checkpoints every N steps
   // device counter added to the iteration index (a replayed closed-loop graph advances it), or null
   const unsigned long long *iter_add;
+  // sample-sharded iteration: local sample k is global sample k_base + k (its Philox counter word 0
+  // and its place in the exploration split, n_imp counting global samples); when rec_out is set the
+  // final merge writes the merged partial record there instead of U', the weights and the stats
+  uint32_t k_base;
+  float *rec_out;
 };
 
 // Launch shape of the FP32 fused kernel: nwarps warps per CTA, spw samples per
@@ -82,10 +87,19 @@ struct Fp32Scratch {
 Fp32Scratch fp32_scratch(int K, int T_max, int H);
 
 Fp32Tile fp32_pick_tile(int K, int T, int H, size_t smem_limit);
+// The 32-wide network's fused kernel (iterate_h32.cu): nw warps (samples) per CTA.
+int h32_pick_warps(int K, int T, size_t smem_limit);
+size_t h32_smem_bytes(int T, int nw);
+size_t h32_max_ctas(int K);  // most CTAs h32_pick_warps can lead to for K samples
+cudaError_t h32_launch_iterate(const IterParams &p, int nw, int group, cudaStream_t s);
 size_t fp32_smem_bytes(int T, int H, Fp32Tile tile);
 int fp32_num_ctas(int K, Fp32Tile tile);
 cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t s);
 cudaError_t launch_finalize_weights(const IterParams &p, cudaStream_t s);
+// Merge n partial records (device, stride partial_len(p.T)) on one CTA: U' from p.U into p.U_out
+// and the stats (p.K = the samples of all records, for the free energy); then, when p.weights is
+// set, the weights of p.n_states local costs p.costs under the merged rho and eta.
+cudaError_t launch_merge_records(const IterParams &p, const float *recs, int n, cudaStream_t s);
 
 // ---- thread-per-sample path (many samples: large K, or many instances) ----
 constexpr int kTpsThreads = 128;  // samples per work unit of the tensor-core kernels (one MMA tile)
@@ -106,6 +120,10 @@ struct TpsInstance {
   int n_units;   // its work units = its records (stride partial_len(T))
   const float *x0, *U;
   float *U_out, *weights, *costs, *stats;
+  // sample-sharded iteration (as IterParams::k_base / rec_out): global index of sample 0, and the
+  // merged record's destination (null: write U', weights and stats)
+  uint32_t k_base;
+  float *rec_out;
 };
 
 // A work unit: nt consecutive samples of one instance (128 for the tensor-core kernels).

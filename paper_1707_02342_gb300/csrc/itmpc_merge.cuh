@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "itmpc_device.cuh"
+#include "itmpc_sum.cuh"
 
 namespace itmpc {
 
@@ -21,8 +22,9 @@ constexpr uint32_t kWaitPolls = 1u << 22;  // bounded mbarrier wait: ~0.3 s of 6
 // Records are staged into shared memory (`stage`, `cap` floats, 16-byte
 // aligned) by cp.async.bulk copies completed on `mbar`: all of them with one
 // copy when they fit, else chunk by chunk.  The E sums are split over
-// (output, record-slice) pairs.  Returns false (status ITMPC_ERR_TIMEOUT) if a
-// copy did not complete in time.
+// (output, record-slice) pairs.  Every sum over records (eta, the importance
+// part, the squares, E) is compensated (itmpc_sum.cuh).  Returns false (status
+// ITMPC_ERR_TIMEOUT) if a copy did not complete in time.
 template <int NT>
 __device__ bool merge_records(const IterParams &p, const float *recs, int n, float *out, float *stage, int cap,
                               uint64_t *mbar, uint32_t &phase) {
@@ -30,7 +32,7 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NWARP = NT / 32;
   constexpr int MAXO = (2 * ITMPC_MAX_T_DEV + NT - 1) / NT;
-  __shared__ float red[NWARP][5];
+  __shared__ float red[NWARP][8];
   __shared__ float tot[5];
 
   // stage layout: [per-record scale: CH floats, padded to 4][CH records]
@@ -77,38 +79,44 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
   __syncthreads();
   const float rho = tot[0];
   const bool ok = isfinite(rho);
-  float eta = 0.f, eta_imp = 0.f, sq = 0.f, nf = 0.f;
+  CSum eta, eta_imp, sq;
+  float nf = 0.f;  // a count: exact in FP32 up to 2^24 samples
   for (int c = tid; c < n; c += NT) {
     const float4 h = header(c);
     const float sc = (ok && isfinite(h.x)) ? expf(-(h.x - rho) * p.inv_lambda) : 0.0f;
     if (whole) scs[c] = sc;
-    eta += sc * h.y;
-    eta_imp += sc * h.z;
-    sq += sc * sc * h.w;
+    eta.add_prod(sc, h.y);
+    eta_imp.add_prod(sc, h.z);
+    sq.add_prod(__fmul_rn(sc, sc), h.w);
     nf += nfin(c);
   }
-  eta = warp_sum(eta);
-  eta_imp = warp_sum(eta_imp);
-  sq = warp_sum(sq);
+  eta = csum_warp(eta);
+  eta_imp = csum_warp(eta_imp);
+  sq = csum_warp(sq);
   nf = warp_sum(nf);
   __syncthreads();  // tot[0] consumed, scs written
   if (lane == 0) {
-    red[warp][0] = eta; red[warp][1] = eta_imp; red[warp][2] = sq; red[warp][3] = nf;
+    red[warp][0] = eta.s; red[warp][1] = eta.c; red[warp][2] = eta_imp.s; red[warp][3] = eta_imp.c;
+    red[warp][4] = sq.s; red[warp][5] = sq.c; red[warp][6] = nf;
   }
   __syncthreads();
   if (tid == 0) {
-    float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
-    for (int w = 0; w < NWARP; ++w) { a += red[w][0]; b += red[w][1]; c += red[w][2]; d += red[w][3]; }
-    tot[1] = a; tot[2] = b; tot[3] = c; tot[4] = d;
+    CSum a, b, c;
+    float d = 0.f;
+    for (int w = 0; w < NWARP; ++w) {
+      a.add(CSum{red[w][0], red[w][1]});
+      b.add(CSum{red[w][2], red[w][3]});
+      c.add(CSum{red[w][4], red[w][5]});
+      d += red[w][6];
+    }
+    tot[1] = a.value(); tot[2] = b.value(); tot[3] = c.value(); tot[4] = d;
   }
 
   // pass 3: E sums.  Thread -> (output o, record slice r) when 2T <= NT.
   const int S = T2 <= NT ? NT / T2 : 1;
   const int r = T2 <= NT ? tid / T2 : 0;
   const bool active = T2 <= NT ? (tid < S * T2) : true;
-  float acc[MAXO];
-#pragma unroll
-  for (int j = 0; j < MAXO; ++j) acc[j] = 0.f;
+  CSum acc[MAXO];
   for (int c0 = 0; c0 < n; c0 += CH) {
     const int cn = min(CH, n - c0);
     if (!whole) {
@@ -124,22 +132,26 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
       for (int j = 0; j < MAXO; ++j) {
         const int o = T2 <= NT ? tid % T2 : tid + j * NT;
         if ((j == 0 || T2 > NT) && o < T2) {
-          float a0 = 0.f, a1 = 0.f;
+          CSum a0, a1;
           int c = r;
           for (; c + S < cn; c += 2 * S) {
-            a0 = fmaf(scs[c], rs[(size_t)c * PL + 8 + o], a0);
-            a1 = fmaf(scs[c + S], rs[(size_t)(c + S) * PL + 8 + o], a1);
+            a0.add_prod(scs[c], rs[(size_t)c * PL + 8 + o]);
+            a1.add_prod(scs[c + S], rs[(size_t)(c + S) * PL + 8 + o]);
           }
-          if (c < cn) a0 = fmaf(scs[c], rs[(size_t)c * PL + 8 + o], a0);
-          acc[j] += a0 + a1;
+          if (c < cn) a0.add_prod(scs[c], rs[(size_t)c * PL + 8 + o]);
+          acc[j].add(a0);
+          acc[j].add(a1);
         }
       }
     }
   }
-  // combine the record slices through shared memory (reusing the stage)
+  // combine the record slices through shared memory (reusing the stage): (s, c) pairs
   __syncthreads();
   float *part = stage;
-  if (T2 <= NT && active) part[r * T2 + (tid % T2)] = acc[0];
+  if (T2 <= NT && active) {
+    part[2 * (r * T2 + (tid % T2))] = acc[0].s;
+    part[2 * (r * T2 + (tid % T2)) + 1] = acc[0].c;
+  }
   __syncthreads();
   const float eta_t = tot[1], eta_imp_t = tot[2], sq_t = tot[3], nf_t = tot[4];
   const float inv_eta = ok ? 1.0f / eta_t : 0.0f;
@@ -148,11 +160,13 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
   for (int j = 0; j < MAXO; ++j) {
     const int o = tid + j * NT;
     if (o < T2) {
-      float E = 0.f;
+      float E;
       if (T2 <= NT) {
-        for (int q = 0; q < S; ++q) E += part[q * T2 + o];
+        CSum Ec;
+        for (int q = 0; q < S; ++q) Ec.add(CSum{part[2 * (q * T2 + o)], part[2 * (q * T2 + o) + 1]});
+        E = Ec.value();
       } else {
-        E = acc[j];
+        E = acc[j].value();
       }
       if (out) {
         out[8 + o] = ok ? E : 0.0f;

@@ -68,6 +68,8 @@ SIGNATURES = {
     "itmpc_philox4x32_10": (C.c_int, [_vp, _vp, _vp, _i64, _vp]),
     "itmpc_tanh_f32": (C.c_int, [_vp, _vp, _i64, _vp]),
     "itmpc_merge_partials": (C.c_int, [_i32, _i32, _vp, _vp, _f, _vp]),
+    "itmpc_iterate_shard": (C.c_int, [_vp, _vp, _vp, _u64, _i64, _i64, _vp, _vp]),
+    "itmpc_merge_shards": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "itmpc_iterate_noalloc": (C.c_int, [C.POINTER(Config), _vp, _vp, _vp, _i32, _i32, _f, _f, _f, _vp, _vp, _u64,
                                         _vp, _vp, _vp]),
     "itmpc_autotune_batch": (C.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
@@ -346,6 +348,26 @@ class Controller:
         if st not in (OK, ERR_NONFINITE):
             self._check(st)
         return st
+
+    # -- sample-sharded iteration ------------------------------------------------
+    def iterate_shard(self, x0, U, it: int, k_base: int, K_total: int, partial, costs=None):
+        """This context's K samples as global samples k_base.. of a K_total-sample iteration:
+        writes the shard's partial record (device, partial_stride(T) floats) and its costs."""
+        K, T = self.cfg.K, self.cfg.T
+        self._check(self._L.itmpc_iterate_shard(self._h, _dptr(x0, 7), _dptr(U, 2 * T), it, k_base, K_total,
+                                                _dptr(partial, partial_stride(T)), _dptr(costs, K)))
+
+    def merge_shards(self, partials, K_total: int, U, U_out, costs=None, weights=None):
+        """Merge n shard records (device, n x partial_stride(T)) into U_out, the stats and,
+        given this context's costs, its samples' weights under the merged normaliser."""
+        K, T = self.cfg.K, self.cfg.T
+        if partials.dim() != 2 or partials.shape[1] != partial_stride(T):
+            raise ValueError(f"partials must be (n, {partial_stride(T)})")
+        if partials.data_ptr() % 16:
+            raise ValueError("partials must be 16-byte aligned")
+        self._check(self._L.itmpc_merge_shards(self._h, partials.shape[0], _dptr(partials, partials.numel()), K_total,
+                                               _dptr(U, 2 * T), _dptr(U_out, 2 * T), _dptr(costs, K),
+                                               _dptr(weights, K)))
 
     def read_status(self) -> int:
         return int(self._L.itmpc_read_status(self._h))
