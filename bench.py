@@ -10,6 +10,13 @@ A step is one full iteration (noise, rollouts, costs, weights, update) through
 as the next nominal sequence.  L2 is flushed (256 MiB write) before every timed
 step; only the iteration itself is inside each step's CUDA-event pair.
 
+With N > 1 ranks (torchrun, one GPU each) a step is ONE iteration of N x 2048
+samples, sharded over the ranks: rank r rolls out global samples
+2048 r .. 2048 (r + 1) - 1 (``itmpc_iterate_shard``), the ranks all-gather their
+partial records (NCCL; ``ITMPC_BENCH_BACKEND=gloo`` exchanges them through the
+host instead) and every rank merges them on its GPU (``itmpc_merge_shards``):
+weak scaling, 2048 samples per GPU.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
@@ -37,7 +44,9 @@ UNIT = "rollout-steps/s"
 K_WORK, T_WORK, H_WORK = 2048, 100, 32
 FLOP_PER_SAMPLE_STEP = 2 * (6 * H_WORK + H_WORK * H_WORK + H_WORK * 4)  # network MACs x 2 = 2688
 PROFILE = os.path.join(ROOT, "profiles", "iterate_fp32_K2048_T100.md")
-KERNEL_SOURCES = ["paper_1707_02342_gb300/csrc/iterate_fp32.cu", "paper_1707_02342_gb300/csrc/itmpc_device.cuh"]
+KERNEL_SOURCES = ["paper_1707_02342_gb300/csrc/iterate_fp32.cu", "paper_1707_02342_gb300/csrc/itmpc_device.cuh",
+                  "paper_1707_02342_gb300/csrc/itmpc_fused.cuh", "paper_1707_02342_gb300/csrc/itmpc_merge.cuh",
+                  "paper_1707_02342_gb300/csrc/itmpc_sum.cuh"]
 
 
 ADJ_PROFILE = os.path.join(ROOT, "profiles", "adj_backward_K4096_T100_H64.md")
@@ -537,7 +546,8 @@ def run_reference(args, rank, world):
 
     tmap, layers, x0, U, params = workload()
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    P = oracle.Problem(K=K_WORK, T=T_WORK, layers=layers, costmap=tmap.data, res=tmap.res, origin_x=tmap.origin_x,
+    K_total = world * K_WORK  # the same iteration as the GPU arm's (N x 2048 samples sharded over N GPUs)
+    P = oracle.Problem(K=K_total, T=T_WORK, layers=layers, costmap=tmap.data, res=tmap.res, origin_x=tmap.origin_x,
                        origin_y=tmap.origin_y, lam=params["lam"], sigma=params["sigma"], cost_w=params["cost_w"],
                        n_threads=cores)
     U64 = U.astype(np.float64)
@@ -553,17 +563,31 @@ def run_reference(args, rank, world):
             break
     dt = time.perf_counter() - t0
     per = dt / n
-    value = K_WORK * T_WORK / per
+    value = K_total * T_WORK / per
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"it-mpc iteration K={K_WORK} T={T_WORK} H={H_WORK} spline-1024 map",
-                       "K": K_WORK, "T": T_WORK, "hidden": H_WORK, "map": "1024x1024@0.1m"},
+            "config": {"workload": f"it-mpc iteration K={K_total} T={T_WORK} H={H_WORK} spline-1024 map",
+                       "K": K_total, "K_per_gpu": K_WORK, "T": T_WORK, "hidden": H_WORK, "map": "1024x1024@0.1m"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n} full iterations (FP64 C oracle, OpenMP over samples)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "control_updates_per_s": 1.0 / per}
     print(json.dumps(line), flush=True)
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest value of x over the ranks (x itself on one rank)."""
+    if world == 1:
+        return x
+    import torch
+
+    dist = torch.distributed
+    t = torch.tensor([x], dtype=torch.float64)
+    if dist.get_backend() != "gloo":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def run_ours(args, rank, world, local_rank):
@@ -573,14 +597,16 @@ def run_ours(args, rank, world, local_rank):
     from paper_1707_02342_gb300 import build as nbuild
     from paper_1707_02342_gb300 import itmpc
 
-    torch.cuda.set_device(local_rank)
+    dev = local_rank % torch.cuda.device_count()
+    torch.cuda.set_device(dev)
     if rank == 0:
         nbuild.build()
     if world > 1:
         torch.distributed.barrier()
     tmap, layers, x0, U, params = workload()
     stream = torch.cuda.current_stream()
-    ctl = itmpc.Controller(K_WORK, T_WORK, hidden=H_WORK, instance=rank, **params)
+    # N > 1: every rank holds a shard of one iteration (same noise stream, instance tag 0)
+    ctl = itmpc.Controller(K_WORK, T_WORK, hidden=H_WORK, instance=0, **params)
     ctl.set_dynamics([(torch.tensor(W, device="cuda"), torch.tensor(b, device="cuda")) for W, b in layers])
     ctl.set_costmap(torch.tensor(tmap.data, device="cuda"), tmap.res, tmap.origin_x, tmap.origin_y)
     x0_d = torch.tensor(x0, device="cuda")
@@ -590,9 +616,30 @@ def run_ours(args, rank, world, local_rank):
     S_d = torch.empty(K_WORK, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     launches_per_step = 1 if K_WORK <= 16384 else 2
+    K_total = world * K_WORK
+    if world > 1:
+        dist = torch.distributed
+        gloo = dist.get_backend() == "gloo"
+        stride = itmpc.partial_stride(T_WORK)
+        rec_me = torch.zeros(stride, device="cuda")
+        rec_all = torch.zeros((world, stride), device="cuda")
+        launches_per_step = 2  # the shard's iteration kernel and the record merge
 
-    def step(i):
-        ctl.iterate(x0_d, U_d, i, U_d, w_d, S_d)
+        def exchange():
+            if gloo:  # through the host (one GPU can carry several ranks this way)
+                parts = [torch.zeros(stride) for _ in range(world)]
+                dist.all_gather(parts, rec_me.cpu())
+                rec_all.copy_(torch.stack(parts))
+            else:
+                dist.all_gather_into_tensor(rec_all.view(-1), rec_me)
+
+        def step(i):
+            ctl.iterate_shard(x0_d, U_d, i, rank * K_WORK, K_total, rec_me, S_d)
+            exchange()
+            ctl.merge_shards(rec_all, K_total, U_d, U_d, S_d, w_d)
+    else:
+        def step(i):
+            ctl.iterate(x0_d, U_d, i, U_d, w_d, S_d)
 
     for i in range(args.warmup):
         flush.zero_()
@@ -604,7 +651,7 @@ def run_ours(args, rank, world, local_rank):
     n = args.steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
-    sampler = ClockSampler(local_rank)
+    sampler = ClockSampler(dev)
     with sampler:
         if world > 1:
             torch.distributed.barrier()
@@ -621,41 +668,61 @@ def run_ours(args, rank, world, local_rank):
         t_wall = time.perf_counter() - t_wall
     assert ctl.read_status() == itmpc.OK
     step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
-    mean_ms = float(step_ms.mean())
-    if world > 1:
-        t = torch.tensor([mean_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        mean_ms = float(t.item())
+    mean_ms = max_over_ranks(float(step_ms.mean()), world)
 
-    # end to end through the host-pointer entry point: h2d of x0 + U, d2h of U'
-    x0_h = torch.tensor(x0).pin_memory().numpy()
-    U_h = torch.tensor(U).pin_memory().numpy()
-    Uo_h = torch.empty((T_WORK, 2), dtype=torch.float32).pin_memory().numpy()
+    # end to end: h2d of x0 + U from pinned host memory, the step, d2h of U'
     e2e_n = min(n, 500)
-    # untimed warm-up calls: the first call captures the context's host graph (and every call after a
-    # parameter change would); the timed calls replay it
-    for i in range(max(10, args.warmup)):
-        st = ctl.iterate_host(x0_h, U_h, i, Uo_h)
-        assert st == itmpc.OK
-    e2e_s = []
-    for i in range(e2e_n):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st = ctl.iterate_host(x0_h, U_h, args.warmup + i, Uo_h)
-        e2e_s.append(time.perf_counter() - t0)
-        assert st == itmpc.OK
-        U_h[:] = Uo_h
-    e2e_mean = float(np.mean(e2e_s))
-    if world > 1:
-        t = torch.tensor([e2e_mean], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_mean = float(t.item())
+    e2e_warm = max(10, args.warmup)
+    if world == 1:
+        # through the host-pointer entry point; the first call captures the context's host graph
+        # (as every call after a parameter change would), so untimed calls come first
+        x0_h = torch.tensor(x0).pin_memory().numpy()
+        U_h = torch.tensor(U).pin_memory().numpy()
+        Uo_h = torch.empty((T_WORK, 2), dtype=torch.float32).pin_memory().numpy()
+        for i in range(e2e_warm):
+            st = ctl.iterate_host(x0_h, U_h, i, Uo_h)
+            assert st == itmpc.OK
+        e2e_s = []
+        for i in range(e2e_n):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ctl.iterate_host(x0_h, U_h, args.warmup + i, Uo_h)
+            e2e_s.append(time.perf_counter() - t0)
+            assert st == itmpc.OK
+            U_h[:] = Uo_h
+        e2e_entry = "itmpc_iterate_host (pinned host buffers; includes copies and stream sync)"
+    else:
+        x0_p = torch.tensor(x0).pin_memory()
+        U_p = torch.tensor(U).pin_memory()
+        Uo_p = torch.empty((T_WORK, 2), dtype=torch.float32).pin_memory()
+
+        def e2e_step(i):
+            x0_d.copy_(x0_p, non_blocking=True)
+            U_d.copy_(U_p, non_blocking=True)
+            step(i)
+            Uo_p.copy_(U_d, non_blocking=True)
+            torch.cuda.synchronize()
+            U_p.copy_(Uo_p)
+
+        for i in range(e2e_warm):
+            e2e_step(i)
+        e2e_s = []
+        for i in range(e2e_n):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step(args.warmup + i)
+            e2e_s.append(time.perf_counter() - t0)
+        e2e_entry = ("itmpc_iterate_shard + record all-gather + itmpc_merge_shards with pinned-host copies of "
+                     "x0, U in and U' out (torch.cuda copies; includes the stream sync)")
+    e2e_med = float(np.median(e2e_s))
+    e2e_mean = max_over_ranks(float(np.mean(e2e_s)), world)
 
     if rank != 0:
         return
     pk = peaks()
-    props = torch.cuda.get_device_properties(local_rank)
+    props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     sm_max = pk.get("sm_max_mhz", 2070.0)
     peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
@@ -667,21 +734,25 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": args.warmup,
         "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"it-mpc iteration K={K_WORK} T={T_WORK} H={H_WORK} spline-1024 map",
-                   "K": K_WORK, "T": T_WORK, "hidden": H_WORK, "map": "1024x1024@0.1m", "crash_cost": 1e4,
+        "config": {"workload": f"it-mpc iteration K={K_total} T={T_WORK} H={H_WORK} spline-1024 map",
+                   "K": K_total, "K_per_gpu": K_WORK, "T": T_WORK, "hidden": H_WORK, "map": "1024x1024@0.1m",
+                   "crash_cost": 1e4,
                    "l2": "flushed before every timed step (256 MiB write, outside the step's events)",
-                   "instances": "one independent instance per GPU (Philox instance = rank)"},
+                   "parallelism": ("one GPU" if world == 1 else
+                                   f"K-sharded: one iteration of {K_total} samples over {world} GPUs, "
+                                   f"{K_WORK} each; one all-gather of the {4 * itmpc.partial_stride(T_WORK)}-byte "
+                                   f"partial records per iteration, then the log-sum-exp merge on every GPU")},
         "control_updates_per_s": world / (mean_ms * 1e-3),
         "ms_per_step_median": float(np.median(step_ms)),
         "wall_s_timed_region_incl_flush": t_wall,
         "e2e": {"value": world * K_WORK * T_WORK / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": 4 * (7 + 2 * T_WORK),
-                "d2h_bytes_per_step": 4 * 2 * T_WORK, "steps": e2e_n, "warmup": max(10, args.warmup),
-                "us_per_call_mean": e2e_mean * 1e6, "us_per_call_median": float(np.median(e2e_s)) * 1e6,
-                "entry_point": "itmpc_iterate_host (pinned host buffers; includes copies and stream sync)"},
+                "d2h_bytes_per_step": 4 * 2 * T_WORK, "steps": e2e_n, "warmup": e2e_warm,
+                "us_per_call_mean": e2e_mean * 1e6, "us_per_call_median": e2e_med * 1e6,
+                "entry_point": e2e_entry},
         "gpu_launches": n * launches_per_step,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "iterate_fp32_kernel (fused noise, rollout, cost, weights, update)",
+                     "kernel": "iterate_fp32_kernel<32, 7, 2> (fused noise, rollout, cost, weights, update)",
                      "peak_derivation": f"{n_sm} SMs x 128 FP32 lanes x 2 FLOP x {sm_max:.0f} MHz (max SM clock)",
                      "algorithmic_flop_per_launch": FLOP_PER_SAMPLE_STEP * K_WORK * T_WORK},
         "clocks": clocks,
@@ -780,8 +851,8 @@ def main():
     if world > 1:
         import torch
 
-        torch.cuda.set_device(local_rank)
-        torch.distributed.init_process_group("nccl")
+        torch.cuda.set_device(local_rank % torch.cuda.device_count())
+        torch.distributed.init_process_group(os.environ.get("ITMPC_BENCH_BACKEND", "nccl"))
     try:
         run_ours(args, rank, world, local_rank)
     finally:

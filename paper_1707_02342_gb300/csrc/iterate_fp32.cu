@@ -1,17 +1,19 @@
-// iterate_fp32.cu -- fused FP32 IT-MPC control iteration for the wide networks
-// (6 -> 64 -> 64 -> 4 and 6 -> 128 -> 128 -> 4) on sm_103a; the paper's 32-wide
-// network has its own kernel (iterate_h32.cu).
+// iterate_fp32.cu -- fused FP32 IT-MPC control iteration for sm_103a.
 //
-// One launch performs the whole iteration of Alg. 1 / Alg. 2.  A warp owns one
-// sample; a CTA owns NW warps' consecutive samples.
+// One launch performs the whole iteration of Alg. 1 / Alg. 2.  A warp owns two
+// samples (H = 32) or one (H = 64, 128); a CTA owns NW warps' consecutive samples.
 //   phase 1  noise      eps and the clamped control g(v) for the CTA's samples x T
 //                       steps (Philox-4x32-10 + Box-Muller), kept in shared memory;
 //   phase 2  dynamics   the serial recurrence x_d(t+1) = x_d(t) + dt f(x_d(t), g(v_t))
 //                       of Sec. V-B.  Only x_d feeds the network, so this is the one
-//                       serial chain.  Lane j owns neurons j, j + 32, ...; layer 1 in
-//                       registers, h1 broadcast through a per-warp shared row, W2
-//                       transposed in shared memory, the 4 outputs of layer 3 reduced
-//                       across the warp with a register butterfly;
+//                       serial chain.  H = 32: a half-warp per sample, two neurons per
+//                       lane, the W2 and M rows in registers as packed pairs for
+//                       fma.rn.f32x2, the layer-1 pre-activation carried from step to
+//                       step (recurrence_half32).  H = 64, 128: lane j owns neurons j,
+//                       j + 32, ...; layer 1 in registers, h1 broadcast through a
+//                       per-warp shared row, W2 transposed in shared memory, the 4
+//                       outputs of layer 3 reduced across the warp with a register
+//                       butterfly;
 //   phase 3  kinematics heading and position are prefix sums over t of dt*theta_dot
 //            and cost   and dt*R(theta)v (warp scans, lane = time step); then the state
 //                       cost of Sec. V-C at t = 1..T plus the control-cost term of
@@ -49,7 +51,7 @@ __host__ __device__ inline SmemLayout fp32_layout(int T, int H, int nw, int spw)
   L.traj = off; off += align16(sizeof(float4) * (size_t)scta * (T + 1));
   L.pos = off;  off += align16(sizeof(float4) * (size_t)scta * T);
   L.W2T = off;  off += (H > 32) ? align16(sizeof(float) * (size_t)H * H) : 0;
-  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * 2 * H);
+  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * (spw == 2 ? 2 * 32 * 36 + 16 + 80 : 2 * H));
   L.W3b3 = off; off += align16(sizeof(float) * (4 * H + 4));
   L.S = off;    off += align16(sizeof(float) * scta);
   L.e = off;    off += align16(sizeof(float) * scta);
@@ -57,9 +59,167 @@ __host__ __device__ inline SmemLayout fp32_layout(int T, int H, int nw, int spw)
   return L;
 }
 
+// Phase 2 for H = 32.  Layers 3 and 1 are affine, so with M = dt W1x W3
+// (32 x 32), beta = dt W1x b3 and the Euler step x_d(t+1) = x_d(t) + dt d(t),
+// d(t) = W3 h2(t) + b3, the input-layer pre-activation obeys
+//   a1(t+1) = a1(t) + M h2(t) + beta + W1u (g(t+1) - g(t))
+// (W1x, W1u: the state and control columns of W1; g the clamped control).
+// The serial chain of a step is then two 32-term dot products with a tanh
+// each, and x_d is not needed inside the loop: a1 is carried as a compensated
+// (Kahan) sum, h2 rows go to a 32-step ring in shared memory (which is also the
+// broadcast row of the M h2 product), and every 32 steps the output layer
+// d = W3 h2 + b3 is applied to the whole block with lane = time step.  d(t) is
+// left in traj[t + 1]; phase 3 turns it into x_d by prefix sums.
+constexpr int kRingStride = 36;  // padded row: lanes reading rows t, t+1, .. hit distinct banks
+
+// Two samples per warp: half-warp h = lane / 16 owns sample s_first + h and
+// lane j = lane % 16 owns neurons j and j + 16 of it, so every activation
+// broadcast feeds two FMAs per lane (half the shared-memory -> register traffic
+// per sample-step of a one-neuron-per-lane layout).
+// Per-warp buffer: ring 0 at 0, ring 1 at 32 rows + 16 floats (the other 16
+// banks), then the two h1 rows at +0 and +48 floats: the halves' stores and
+// loads never share a bank.
+constexpr int kRing1 = 32 * kRingStride + 16;
+constexpr int kHrows = kRing1 + 32 * kRingStride;
+constexpr int kHalfWarpBuf = kHrows + 80;
+
+template <int ACT>
+__device__ __forceinline__ void recurrence_half32(const IterParams &p, const float *net, float *wbuf,
+                                                  const float *W3b3_s, const float2 *gv_s, float4 *traj_s,
+                                                  int s_first, int T, int lane) {
+  constexpr int H = 32;
+  const int h = lane >> 4, j = lane & 15;
+  const int s = s_first + h;
+  float *ring = wbuf + h * kRing1;
+  float *hB = wbuf + kHrows + h * 48;
+  const float4 *hB4 = reinterpret_cast<const float4 *>(hB);
+  const float2 *gvr = gv_s + (size_t)s * T;
+  float4 *traj = traj_s + (size_t)s * (T + 1);
+  const float dt = p.dt;
+  const int ja = j, jb = j + 16;
+  float w1xa[4], w1xb[4], b3[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    w1xa[o] = __ldg(net + net_off_W1(H) + ja * 6 + o);
+    w1xb[o] = __ldg(net + net_off_W1(H) + jb * 6 + o);
+    b3[o] = W3b3_s[4 * H + o];
+  }
+  const float w1ua0 = __ldg(net + net_off_W1(H) + ja * 6 + 4), w1ua1 = __ldg(net + net_off_W1(H) + ja * 6 + 5);
+  const float w1ub0 = __ldg(net + net_off_W1(H) + jb * 6 + 4), w1ub1 = __ldg(net + net_off_W1(H) + jb * 6 + 5);
+  const float b2a = __ldg(net + net_off_b2(H) + ja), b2b = __ldg(net + net_off_b2(H) + jb);
+  float beta_a = 0.f, beta_b = 0.f;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    beta_a = fmaf(dt * w1xa[o], b3[o], beta_a);
+    beta_b = fmaf(dt * w1xb[o], b3[o], beta_b);
+  }
+  // the lane's rows of M and W2 as packed pairs (w[i], w[i + 1]): one fma.rn.f32x2 multiplies
+  // two terms of a dot product, in the same chains (i mod 4) and order as four scalar FMAs
+  unsigned long long ma[H / 2], mb[H / 2], w2a[H / 2], w2b[H / 2];
+#pragma unroll
+  for (int i = 0; i < H; i += 2) {
+    float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      a0 = fmaf(w1xa[o], W3b3_s[o * H + i], a0);
+      b0 = fmaf(w1xb[o], W3b3_s[o * H + i], b0);
+      a1 = fmaf(w1xa[o], W3b3_s[o * H + i + 1], a1);
+      b1 = fmaf(w1xb[o], W3b3_s[o * H + i + 1], b1);
+    }
+    ma[i / 2] = f2pack(dt * a0, dt * a1);
+    mb[i / 2] = f2pack(dt * b0, dt * b1);
+    w2a[i / 2] = f2pack(__ldg(net + net_off_W2(H) + ja * H + i), __ldg(net + net_off_W2(H) + ja * H + i + 1));
+    w2b[i / 2] = f2pack(__ldg(net + net_off_W2(H) + jb * H + i), __ldg(net + net_off_W2(H) + jb * H + i + 1));
+  }
+  // a1(0) = b1 + W1x x_d(0) + W1u g(0)
+  float2 g = gvr[0];
+  float a1a = __ldg(net + net_off_b1(H) + ja), a1b = __ldg(net + net_off_b1(H) + jb);
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const float xo = __ldg(p.x0 + 3 + o);
+    a1a = fmaf(w1xa[o], xo, a1a);
+    a1b = fmaf(w1xb[o], xo, a1b);
+  }
+  a1a = fmaf(w1ua0, g.x, fmaf(w1ua1, g.y, a1a));
+  a1b = fmaf(w1ub0, g.x, fmaf(w1ub1, g.y, a1b));
+  float ca_c = 0.f, cb_c = 0.f;  // Kahan compensations
+  for (int t = 0; t < T; ++t) {
+    const float2 gn = gvr[t + 1 < T ? t + 1 : t];
+    hB[ja] = activation<ACT>(a1a);
+    hB[jb] = activation<ACT>(a1b);
+    __syncwarp();
+    // partial sums (i = 0 mod 4, i = 1 mod 4) and (i = 2 mod 4, i = 3 mod 4) as packed pairs
+    unsigned long long pa01 = f2pack(b2a, 0.f), pa23 = 0ull, pb01 = f2pack(b2b, 0.f), pb23 = 0ull;
+#pragma unroll
+    for (int kk = 0; kk < H; kk += 4) {
+      const ulonglong2 hv = reinterpret_cast<const ulonglong2 *>(hB4)[kk >> 2];
+      pa01 = ffma2(w2a[kk / 2], hv.x, pa01);
+      pa23 = ffma2(w2a[kk / 2 + 1], hv.y, pa23);
+      pb01 = ffma2(w2b[kk / 2], hv.x, pb01);
+      pb23 = ffma2(w2b[kk / 2 + 1], hv.y, pb23);
+    }
+    float *row = ring + (t & 31) * kRingStride;
+    const float2 qa01 = f2unpack(pa01), qa23 = f2unpack(pa23), qb01 = f2unpack(pb01), qb23 = f2unpack(pb23);
+    row[ja] = activation<ACT>((qa01.x + qa01.y) + (qa23.x + qa23.y));
+    row[jb] = activation<ACT>((qb01.x + qb01.y) + (qb23.x + qb23.y));
+    __syncwarp();
+    if (t + 1 < T) {
+      const ulonglong2 *row2 = reinterpret_cast<const ulonglong2 *>(row);
+      const float dgx = gn.x - g.x, dgy = gn.y - g.y;
+      unsigned long long ea01 = f2pack(fmaf(w1ua0, dgx, beta_a), w1ua1 * dgy), ea23 = 0ull;
+      unsigned long long eb01 = f2pack(fmaf(w1ub0, dgx, beta_b), w1ub1 * dgy), eb23 = 0ull;
+#pragma unroll
+      for (int kk = 0; kk < H; kk += 4) {
+        const ulonglong2 hv = row2[kk >> 2];
+        ea01 = ffma2(ma[kk / 2], hv.x, ea01);
+        ea23 = ffma2(ma[kk / 2 + 1], hv.y, ea23);
+        eb01 = ffma2(mb[kk / 2], hv.x, eb01);
+        eb23 = ffma2(mb[kk / 2 + 1], hv.y, eb23);
+      }
+      const float2 fa01 = f2unpack(ea01), fa23 = f2unpack(ea23), fb01 = f2unpack(eb01), fb23 = f2unpack(eb23);
+      const float ea0 = fa01.x, ea1 = fa01.y, ea2 = fa23.x, ea3 = fa23.y;
+      const float eb0 = fb01.x, eb1 = fb01.y, eb2 = fb23.x, eb3 = fb23.y;
+      const float ya = ((ea0 + ea1) + (ea2 + ea3)) - ca_c;
+      const float sa = a1a + ya;
+      ca_c = (sa - a1a) - ya;
+      a1a = sa;
+      const float yb = ((eb0 + eb1) + (eb2 + eb3)) - cb_c;
+      const float sb = a1b + yb;
+      cb_c = (sb - a1b) - yb;
+      a1b = sb;
+      g = gn;
+    }
+    if ((t & 31) == 31 || t + 1 == T) {
+      const int t0 = t & ~31;
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int r = j + 16 * rr;
+        if (t0 + r <= t) {
+          const float4 *r4 = reinterpret_cast<const float4 *>(ring + r * kRingStride);
+          float d0 = b3[0], d1 = b3[1], d2 = b3[2], d3 = b3[3];
+#pragma unroll
+          for (int kk = 0; kk < H; kk += 4) {
+            const float4 hv = r4[kk >> 2];
+            const float4 q0 = *reinterpret_cast<const float4 *>(W3b3_s + 0 * H + kk);
+            const float4 q1 = *reinterpret_cast<const float4 *>(W3b3_s + 1 * H + kk);
+            const float4 q2 = *reinterpret_cast<const float4 *>(W3b3_s + 2 * H + kk);
+            const float4 q3 = *reinterpret_cast<const float4 *>(W3b3_s + 3 * H + kk);
+            d0 = fmaf(q0.x, hv.x, fmaf(q0.y, hv.y, fmaf(q0.z, hv.z, fmaf(q0.w, hv.w, d0))));
+            d1 = fmaf(q1.x, hv.x, fmaf(q1.y, hv.y, fmaf(q1.z, hv.z, fmaf(q1.w, hv.w, d1))));
+            d2 = fmaf(q2.x, hv.x, fmaf(q2.y, hv.y, fmaf(q2.z, hv.z, fmaf(q2.w, hv.w, d2))));
+            d3 = fmaf(q3.x, hv.x, fmaf(q3.y, hv.y, fmaf(q3.z, hv.z, fmaf(q3.w, hv.w, d3))));
+          }
+          traj[t0 + r + 1] = make_float4(d0, d1, d2, d3);
+        }
+      }
+      __syncwarp();  // the ring is reused by the next block
+    }
+  }
+}
+
 template <int H, int NW, int SPW, int ACT>
 __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_constant__ IterParams p) {
-  static_assert(SPW == 1 && H > 32, "one sample per warp; the 32-wide network has its own kernel (iterate_h32.cu)");
+  static_assert((SPW == 2) == (H == 32), "H = 32 runs two samples per warp, H = 64 / 128 one");
   constexpr int NT = NW * 32;
   constexpr int SCTA = NW * SPW;  // samples per CTA
   constexpr int NPL = H / 32;  // hidden neurons per lane
@@ -151,8 +311,15 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
   const float x0px = __ldg(p.x0 + 0), x0py = __ldg(p.x0 + 1), x0th = __ldg(p.x0 + 2);
 
   // ---- phase 2: the serial network recurrence ----
-  if (k0 + warp < p.K) {
-    // one warp per sample
+  if constexpr (SPW == 2) {
+    float *wbuf = reinterpret_cast<float *>(smem + L.hbuf) + warp * kHalfWarpBuf;
+    if ((lane & 15) == 0)
+      traj_s[(warp * 2 + (lane >> 4)) * (T + 1)] =
+          make_float4(__ldg(p.x0 + 3), __ldg(p.x0 + 4), __ldg(p.x0 + 5), __ldg(p.x0 + 6));
+    recurrence_half32<ACT>(p, net, wbuf, W3b3_s, gv_s, traj_s, warp * 2, T, lane);
+    __syncwarp();
+  } else if (k0 + warp < p.K) {
+    // H = 64 / 128: one warp per sample
     const int s = warp;
     float xd0 = __ldg(p.x0 + 3), xd1 = __ldg(p.x0 + 4), xd2 = __ldg(p.x0 + 5), xd3 = __ldg(p.x0 + 6);
     float *hrow = reinterpret_cast<float *>(smem + L.hbuf) + s * 2 * H;
@@ -233,13 +400,15 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
   // ---- phase 3: kinematics and running costs, this warp's samples side by side ----
   {
     float th_c[SPW], px_c[SPW], py_c[SPW];
+    float4 xd_c[SPW];
 #pragma unroll
     for (int q = 0; q < SPW; ++q) {
       th_c[q] = x0th;
       px_c[q] = x0px;
       py_c[q] = x0py;
+      xd_c[q] = traj_s[(warp * SPW + q) * (T + 1)];
     }
-    // 3a: heading and position by prefix sums over t
+    // 3a: x_d (H = 32: from the stored d), heading and position by prefix sums over t
     for (int base = 0; base < T; base += 32) {
       const int tau = base + lane;
       const bool valid = tau < T;
@@ -247,7 +416,27 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
       for (int q = 0; q < SPW; ++q) {
         const int s = warp * SPW + q;
         float4 *traj = traj_s + s * (T + 1);
-        float4 xo = traj[valid ? tau : T - 1];
+        float4 xo;
+        if constexpr (H == 32) {
+          // traj[tau + 1] holds d(tau): x_d(tau + 1) = x_d(0) + dt sum_{s <= tau} d(s)
+          float4 dd = traj[valid ? tau + 1 : T];
+          if (!valid) dd = make_float4(0.f, 0.f, 0.f, 0.f);
+          const float i0 = warp_incl_scan(dt * dd.x, lane), i1 = warp_incl_scan(dt * dd.y, lane);
+          const float i2 = warp_incl_scan(dt * dd.z, lane), i3 = warp_incl_scan(dt * dd.w, lane);
+          // every lane takes part in each shuffle; lane 0 then drops the value
+          float e0 = __shfl_up_sync(FULL_MASK, i0, 1), e1 = __shfl_up_sync(FULL_MASK, i1, 1);
+          float e2 = __shfl_up_sync(FULL_MASK, i2, 1), e3 = __shfl_up_sync(FULL_MASK, i3, 1);
+          if (lane == 0) e0 = e1 = e2 = e3 = 0.f;
+          xo = make_float4(xd_c[q].x + e0, xd_c[q].y + e1, xd_c[q].z + e2, xd_c[q].w + e3);
+          __syncwarp();  // every lane has read its d before any x_d overwrites it
+          if (valid) traj[tau + 1] = make_float4(xd_c[q].x + i0, xd_c[q].y + i1, xd_c[q].z + i2, xd_c[q].w + i3);
+          xd_c[q].x += __shfl_sync(FULL_MASK, i0, 31);
+          xd_c[q].y += __shfl_sync(FULL_MASK, i1, 31);
+          xd_c[q].z += __shfl_sync(FULL_MASK, i2, 31);
+          xd_c[q].w += __shfl_sync(FULL_MASK, i3, 31);
+        } else {
+          xo = traj[valid ? tau : T - 1];
+        }
         if (!valid) xo = make_float4(0.f, 0.f, 0.f, 0.f);
         const float dth = dt * xo.w;
         const float incl_th = warp_incl_scan(dth, lane);
@@ -431,10 +620,16 @@ int group_for(int nC) { return nC <= kSingleLevel ? nC : kGroup; }
 }  // namespace
 
 Fp32Tile fp32_pick_tile(int K, int T, int H, size_t smem_limit) {
-  if (H == 32) {  // one sample per warp, a CTA per SM (iterate_h32.cu)
-    const int nw = h32_pick_warps(K, T, smem_limit);
-    const int nC = (K + nw - 1) / nw;
-    return {nw, group_for(nC), 1};
+  if (H == 32) {
+    // Two samples per warp; spread the samples evenly over the SMs, at most 8
+    // warps (the register file holds one such CTA per SM).
+    DeviceInfo di;
+    const int sms = device_info(di) == cudaSuccess && di.sms > 0 ? di.sms : 148;
+    const int want = (K + 2 * sms - 1) / (2 * sms);
+    int nw = want <= 2 ? 2 : (want <= 4 ? 4 : (want <= 7 ? 7 : 8));
+    while (nw > 2 && fp32_layout(T, H, nw, 2).total > smem_limit) nw = nw > 4 ? 4 : 2;
+    const int nC = (K + 2 * nw - 1) / (2 * nw);
+    return {nw, group_for(nC), 2};
   }
   // One warp per sample.  Large CTAs give few partial records (a short merge).
   int nw = K >= 2048 ? 16 : (K >= 1024 ? 8 : 4);
@@ -445,24 +640,25 @@ Fp32Tile fp32_pick_tile(int K, int T, int H, size_t smem_limit) {
 
 Fp32Scratch fp32_scratch(int K, int T_max, int H) {
   const size_t PL = (size_t)partial_len(T_max);
-  const size_t nC = H == 32 ? h32_max_ctas(K) : (size_t)(K + kMinWarps - 1) / kMinWarps;
+  const size_t nC = (size_t)(K + kMinWarps - 1) / kMinWarps;
   const size_t G = (size_t)group_for((int)nC);
   const size_t nG = (nC + G - 1) / G;
   return {PL * nC, PL * nG, nC > nG ? nC : nG, 1 + nG + 2};  // + grid barrier (arrivals, generation)
 }
 
-size_t fp32_smem_bytes(int T, int H, Fp32Tile t) {
-  return H == 32 ? h32_smem_bytes(T, t.nwarps) : fp32_layout(T, H, t.nwarps, t.spw).total;
-}
+size_t fp32_smem_bytes(int T, int H, Fp32Tile t) { return fp32_layout(T, H, t.nwarps, t.spw).total; }
 
 int fp32_num_ctas(int K, Fp32Tile t) { return (K + t.nwarps * t.spw - 1) / (t.nwarps * t.spw); }
 
 cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t s) {
-  if (p.H == 32) return h32_launch_iterate(p, tile.nwarps, tile.group, s);
 #define ITMPC_TILE(HH, WW, SS)                                                                          \
   if (p.H == HH && tile.nwarps == WW && tile.spw == SS)                                                 \
     return p.activation == 1 ? launch_tile<HH, WW, SS, 1>(p, tile.group, s)                             \
                              : launch_tile<HH, WW, SS, 0>(p, tile.group, s);
+  ITMPC_TILE(32, 2, 2)
+  ITMPC_TILE(32, 4, 2)
+  ITMPC_TILE(32, 7, 2)
+  ITMPC_TILE(32, 8, 2)
   ITMPC_TILE(64, 4, 1)
   ITMPC_TILE(64, 8, 1)
   ITMPC_TILE(64, 16, 1)

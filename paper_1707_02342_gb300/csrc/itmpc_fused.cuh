@@ -124,19 +124,23 @@ __device__ void coop_tail(const IterParams &p, const float *S_s, int k0) {
     acc[2].add_prod(__fmul_rn(sc, sc), h.w);
     acc[3].s += nfr[j];  // a count: exact
 #pragma unroll
-    for (int q = 0; q < MAXS; ++q) acc[5 + q].add_prod(sc, evr[j][q]);
+    for (int q = 0; q < MAXS; ++q)
+      if (q < on) acc[5 + q].add_prod(sc, evr[j][q]);
   }
   __syncthreads();  // tot[0] consumed
+  // only the sums this CTA uses: eta, the importance part, the squares, the count (4 is unused)
+  // and its `on` outputs of U'
 #pragma unroll
   for (int q = 0; q < 5 + MAXS; ++q) {
-    const CSum v = csum_warp(acc[q]);
+    if (q == 4 || q >= 5 + on) continue;  // block-uniform
+    const CSum v = q == 3 ? CSum{warp_sum(acc[3].s), 0.f} : csum_warp(acc[q]);
     if (lane == 0) {
       red[warp][2 * q] = v.s;
       red[warp][2 * q + 1] = v.c;
     }
   }
   __syncthreads();
-  if (tid < 5 + MAXS) {
+  if (tid < 5 + on && tid != 4) {
     CSum a;
     for (int w = 0; w < NWARP; ++w) a.add(CSum{red[w][2 * tid], red[w][2 * tid + 1]});
     tot[tid] = a.value();
@@ -171,11 +175,13 @@ __device__ void coop_tail(const IterParams &p, const float *S_s, int k0) {
 
 // Phase 4 + 5 of a fused iteration, called by every thread of the CTA after the
 // costs of its SCTA samples are in S_s (samples k0 .. k0 + SCTA - 1):
-//   eps        the CTA's noise, sample q's eps[t][i] at eps[q * eps_stride + 2 t + i];
+//   eps        the CTA's noise: sample q's eps[t][i] at
+//              eps[(q / EG) * eps_stride + (q % EG) * 2 T + 2 t + i] (groups of EG samples
+//              with contiguous rows, eps_stride floats apart);
 //   e_s        SCTA floats of shared scratch;
 //   gen0       the grid-barrier generation read before this launch's barrier;
 //   stage      shared memory for the merge (p.stage_floats floats; the rollout's buffers).
-template <int NT, int SCTA>
+template <int NT, int SCTA, int EG = 1>
 __device__ void record_and_merge(const IterParams &p, const float *S_s, float *e_s, const float *eps,
                                  size_t eps_stride, int k0, unsigned gen0, float *stage) {
   const int T = p.T;
@@ -209,7 +215,7 @@ __device__ void record_and_merge(const IterParams &p, const float *S_s, float *e
   for (int o = tid; o < 2 * T; o += NT) {
     CSum acc;
 #pragma unroll
-    for (int q = 0; q < SCTA; ++q) acc.add_prod(e_s[q], eps[(size_t)q * eps_stride + o]);
+    for (int q = 0; q < SCTA; ++q) acc.add_prod(e_s[q], eps[(size_t)(q / EG) * eps_stride + (q % EG) * 2 * T + o]);
     rec[8 + o] = acc.value();
   }
 

@@ -87,11 +87,6 @@ struct Fp32Scratch {
 Fp32Scratch fp32_scratch(int K, int T_max, int H);
 
 Fp32Tile fp32_pick_tile(int K, int T, int H, size_t smem_limit);
-// The 32-wide network's fused kernel (iterate_h32.cu): nw warps (samples) per CTA.
-int h32_pick_warps(int K, int T, size_t smem_limit);
-size_t h32_smem_bytes(int T, int nw);
-size_t h32_max_ctas(int K);  // most CTAs h32_pick_warps can lead to for K samples
-cudaError_t h32_launch_iterate(const IterParams &p, int nw, int group, cudaStream_t s);
 size_t fp32_smem_bytes(int T, int H, Fp32Tile tile);
 int fp32_num_ctas(int K, Fp32Tile tile);
 cudaError_t fp32_launch_iterate(const IterParams &p, Fp32Tile tile, cudaStream_t s);

@@ -26,7 +26,8 @@ def test_reference_arm_line_on_rank_zero():
 
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["n_gpus"] == 2 and d["steps"] == 1 and d["warmup"] >= 3 and d["value"] > 0
-    assert d["higher_is_better"] is True and d["config"]["K"] == bench.K_WORK and d["config"]["T"] == bench.T_WORK
+    assert d["higher_is_better"] is True and d["config"]["K"] == 2 * bench.K_WORK and d["config"]["T"] == bench.T_WORK
+    assert d["config"]["K_per_gpu"] == bench.K_WORK  # one iteration of 2 x 2048 samples, as the GPU arm shards it
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
