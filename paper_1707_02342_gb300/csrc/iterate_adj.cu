@@ -16,16 +16,19 @@
 //                          Sbar_k = w_k (gJ (1 - (S_k - J)/lambda) - (a_k - c0)/lambda),
 //                          a_k = sum_t gU_t . v_{k,t}
 //                        (dw_k/dS_j = -(1/lambda) w_k (delta_kj - w_j)).  The horizon is
-//                        walked backwards in segments of `every` steps: the segment is
-//                        re-run forward from its checkpoint x_{t0} (written by the
-//                        forward launch), keeping states, controls and both hidden
-//                        layers in shared memory; then each step is reversed: cost
-//                        slope at x_t, the Euler kinematics, the network (lane j owns
-//                        neurons j, j+32, ...; W2 is read from shared memory in both
-//                        orientations), the clamp g and the control-cost term.  The
-//                        W2 gradient, an outer product summed over samples and steps,
-//                        is accumulated by the whole CTA as a small GEMM over the
-//                        segment's rows (a2bar x h1) after every segment;
+//                        walked backwards in segments of `every` steps, each in sub-segments
+//                        short enough that a CTA's footprint lets 4 CTAs share an SM: the
+//                        segment is re-run forward from its checkpoint x_{t0} (written by
+//                        the forward launch), keeping its states and controls and the last
+//                        sub-segment's hidden-layer rows in shared memory; each earlier
+//                        sub-segment is re-run from its stored start state.  Each step is
+//                        then reversed: cost slope at x_t, the Euler kinematics, the network
+//                        (lane j owns neurons j, j+32, ...; one copy of W2 with padded rows
+//                        serves both orientations without bank conflicts), the clamp g and
+//                        the control-cost term.  The W2 gradient, an outer product summed
+//                        over samples and steps, is accumulated by the whole CTA as a small
+//                        GEMM over the sub-segment's rows (a2bar x h1) and added to the
+//                        CTA's record in place;
 //   adj_reduce_kernel    sums the per-CTA records in a fixed order (deterministic)
 //                        and adds the direct term dU'_t/du_t = sum_{importance} w_k.
 #include <cuda_runtime.h>
@@ -38,23 +41,51 @@ namespace itmpc {
 
 namespace {
 
-constexpr int kAdjWarps = 4;                     // warps per CTA
+constexpr int kAdjWarps = 8;                     // warps per CTA
 constexpr int kAdjSPW = 2;                       // samples per warp, side by side
 constexpr int kAdjSamples = kAdjWarps * kAdjSPW; // samples per CTA
+constexpr int kAdjCtasPerSm = 2;                 // the shared-memory and register budget aims at 2 CTAs per SM
+constexpr size_t kAdjSmemTarget = 113 * 1024;    // 228 KB per SM / 2, less the 1 KB the SM keeps per CTA
 
 __host__ __device__ inline int adj_rec_floats(int H, int T) { return (net_floats(H) + 4 + 2 * T + 3) & ~3; }
+// A CTA's slot in the record buffer: its record, then one dL/dU row (2T) per warp.
+__host__ __device__ inline size_t adj_cta_floats(int H, int T) {
+  return (size_t)adj_rec_floats(H, T) + (size_t)kAdjWarps * 2 * T;
+}
+__host__ __device__ inline int adj_w2_stride(int H) { return H + 4; }
 
-// Per-sample shared floats for a segment of `every` steps.
-__host__ __device__ inline size_t adj_sample_floats(int H, int every) {
-  return 8 * (size_t)(every + 1)      // states x_{t0..t0+every}, 8 floats each
-         + 4 * (size_t)every          // (v0, v1, g0, g1) per step
-         + 4 * (size_t)every          // cost slope (px, py, vx, vy) at x_{t0+1+i}
-         + 2 * (size_t)H * every;     // h1 rows, h2 rows (then a2bar rows)
+// Per-sample shared floats for a segment of `every` steps walked in sub-segments of `sub`
+// steps: states and controls for the whole segment, hidden-layer rows for one sub-segment.
+__host__ __device__ inline size_t adj_sample_floats(int H, int every, int sub) {
+  return 8 * (size_t)(every + 1)    // states x_{t0..t0+every}, 8 floats each
+         + 4 * (size_t)every        // (v0, v1, g0, g1) per step
+         + 4 * (size_t)every        // cost slope (px, py, vx, vy) at x_{t0+1+i}
+         + 2 * (size_t)H * sub;     // h1 rows, h2 rows (then a2bar rows) of the sub-segment
 }
 
-__host__ __device__ inline size_t adj_smem_floats(int H, int every, int T) {
-  return 2 * (size_t)H * H + kAdjSamples * adj_sample_floats(H, every) + (size_t)kAdjWarps * 2 * T +
-         (size_t)adj_rec_floats(H, T);
+// W2 (rows padded), the per-warp dL/dU rows, then the per-sample regions; the CTA's
+// record reuses the per-sample regions once the last segment is done.
+__host__ __device__ inline size_t adj_region_floats(int H, int every, int sub, int T) {
+  const size_t s = kAdjSamples * adj_sample_floats(H, every, sub);
+  const size_t r = (size_t)adj_rec_floats(H, T);
+  return s > r ? s : r;
+}
+
+// W3 by neuron (4 floats each), b1, b2, and 8 per-warp sums (b3 gradient, cost components)
+__host__ __device__ inline int adj_small_floats(int H) { return 6 * H + 8 * kAdjWarps; }
+
+__host__ __device__ inline size_t adj_smem_floats(int H, int every, int sub, int T) {
+  return (size_t)H * adj_w2_stride(H) + adj_small_floats(H) + adj_region_floats(H, every, sub, T);
+}
+
+// The longest sub-segment (every, every/2, every/3, ...) whose footprint fits the target;
+// a sub-segment other than the segment's last is re-run from its stored start state.
+inline int adj_sub_len(int H, int every, int T) {
+  for (int n = 1; n <= every; ++n) {
+    const int sub = (every + n - 1) / n;
+    if (sizeof(float) * adj_smem_floats(H, every, sub, T) <= kAdjSmemTarget) return sub;
+  }
+  return 1;
 }
 
 // Slope of the state cost c(x, t) of Sec. V-C with respect to (p_x, p_y, v_x, v_y),
@@ -160,23 +191,24 @@ __global__ void __launch_bounds__(1024) adj_scalars_kernel(int K, int T, int n_i
 }
 
 template <int H, int ACT>
-__global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __grid_constant__ AdjParams a) {
+__global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_kernel(const __grid_constant__ AdjParams a) {
   constexpr int NW = kAdjWarps, SPW = kAdjSPW, SC = kAdjSamples;
   constexpr int M = H / 32;
+  constexpr int WS = H + 4;             // padded W2 row: conflict-free in both orientations
   constexpr int E = H * H / (NW * 32);  // W2-gradient entries per thread
-  constexpr int TJ = 4, TI = E / 4, NIB = H / TI;
+  constexpr int TJ = E >= 8 ? 4 : 2, TI = E / TJ, NIB = H / TI;
   static_assert(E % 4 == 0 && (TI == 2 || TI % 4 == 0), "tile");
   const IterParams &p = a.p;
-  const int T = p.T, K = p.K, every = a.every;
+  const int T = p.T, K = p.K, every = a.every, sub = a.sub;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const size_t sf = adj_sample_floats(H, every);
+  const size_t sf = adj_sample_floats(H, every, sub);
 
   extern __shared__ __align__(16) float sm[];
-  float *W2T_s = sm;             // [i][j] = W2[j][i]
-  float *W2_s = sm + H * H;      // [j][i] = W2[j][i]
-  float *sreg = sm + 2 * H * H;  // SC per-sample regions
-  float *ub_s = sreg + SC * sf;  // NW x 2T: per-warp dL/dU of its samples
-  float *rec_s = ub_s + NW * 2 * T;
+  float *W2_s = sm;                    // [j][i] = W2[j][i], rows WS floats apart
+  float *W3_s = sm + H * WS;           // [j][o] = W3[o][j]
+  float *b1_s = W3_s + 4 * H, *b2_s = b1_s + H;
+  float *wsum_s = b2_s + H;            // NW x 8: per-warp b3 gradient (4), cost components (4)
+  float *sreg = wsum_s + 8 * NW;       // SC per-sample regions; the CTA's record at the end
   float *xs[SPW], *vg[SPW], *gc[SPW], *hs1[SPW], *hs2[SPW];
 #pragma unroll
   for (int q = 0; q < SPW; ++q) {
@@ -184,35 +216,39 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
     vg[q] = xs[q] + 8 * (every + 1);
     gc[q] = vg[q] + 4 * every;
     hs1[q] = gc[q] + 4 * every;
-    hs2[q] = hs1[q] + H * every;
+    hs2[q] = hs1[q] + H * sub;
   }
 
   const float *net = p.net;
-  for (int e = threadIdx.x; e < H * H; e += NW * 32) {
-    const float v = __ldg(net + net_off_W2(H) + e);
-    W2_s[e] = v;
-    W2T_s[(e % H) * H + e / H] = v;
+  for (int e = threadIdx.x; e < H * H; e += NW * 32) W2_s[(e / H) * WS + e % H] = __ldg(net + net_off_W2(H) + e);
+  for (int e = threadIdx.x; e < 4 * H; e += NW * 32) W3_s[e] = __ldg(net + net_off_W3(H) + (e & 3) * H + (e >> 2));
+  for (int e = threadIdx.x; e < H; e += NW * 32) {
+    b1_s[e] = __ldg(net + net_off_b1(H) + e);
+    b2_s[e] = __ldg(net + net_off_b2(H) + e);
   }
-  for (int e = threadIdx.x; e < NW * 2 * T; e += NW * 32) ub_s[e] = 0.0f;
+  for (int e = threadIdx.x; e < 8 * NW; e += NW * 32) wsum_s[e] = 0.0f;
   const int nrec = adj_rec_floats(H, T);
-  for (int e = threadIdx.x; e < nrec; e += NW * 32) rec_s[e] = 0.0f;
+  float *rec = a.part + (size_t)blockIdx.x * adj_cta_floats(H, T);
+  float *ub_w = rec + nrec + (size_t)warp * 2 * T;  // this warp's dL/dU row (written while it runs)
 
-  float W1r[M][6], b1r[M], b2r[M], W3c[M][4], b3u[4];
+  // Register tiles of the two matrix-vector products (H/16 rows or columns per lane, half of
+  // the other dimension; one shuffle exchange finishes the sums):
+  //   W2 h1:     lane (r4, ch) sums rows r4 + 16 rr over columns [H/2 ch, H/2 ch + H/2) and
+  //              keeps rows lane + 32 m (layer-2 neuron j = lane + 32 m);
+  //   W2^T a2b:  lane (r4, ch) sums columns CW r4 .. + CW-1 over rows [H/2 ch, ...) and keeps
+  //              columns CW r4 + M ch + m (layer-1 neuron i1(m)).
+  constexpr int R = H / 16, CW = H / 16, HH = H / 2;
+  const int r4 = lane & 15, ch = lane >> 4;
+  const int i1 = CW * r4 + M * ch;  // first layer-1 neuron of this lane (i1 + m, m < M)
+  float W1r[M][6];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const int j = lane + 32 * m;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) W1r[m][c] = __ldg(net + net_off_W1(H) + j * 6 + c);
-    b1r[m] = __ldg(net + net_off_b1(H) + j);
-    b2r[m] = __ldg(net + net_off_b2(H) + j);
-#pragma unroll
-    for (int o = 0; o < 4; ++o) W3c[m][o] = __ldg(net + net_off_W3(H) + o * H + j);
+    for (int c = 0; c < 6; ++c) W1r[m][c] = __ldg(net + net_off_W1(H) + (i1 + m) * 6 + c);
   }
-#pragma unroll
-  for (int o = 0; o < 4; ++o) b3u[o] = __ldg(net + net_off_b3(H) + o);
 
   // gradient accumulators: both samples of the warp add into the same registers
-  float gW1[M][6], gb1[M], gb2[M], gW3[M][4], gb3[4], gcw[4];
+  float gW1[M][6], gb1[M], gb2[M], gW3[M][4];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
 #pragma unroll
@@ -221,14 +257,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
 #pragma unroll
     for (int o = 0; o < 4; ++o) gW3[m][o] = 0.0f;
   }
-#pragma unroll
-  for (int o = 0; o < 4; ++o) gb3[o] = gcw[o] = 0.0f;
+  // this thread's W2-gradient tile: rows TJ*jb .. +3; columns in groups of 4 (TI = 2: one pair),
+  // group g at 4*ib + 4*NIB*g, so that a quarter-warp's 16-byte loads are contiguous
   const int jb = threadIdx.x / NIB, ib = threadIdx.x % NIB;
-  float gW2[TJ][TI];
-#pragma unroll
-  for (int r = 0; r < TJ; ++r)
-#pragma unroll
-    for (int c = 0; c < TI; ++c) gW2[r][c] = 0.0f;
+  bool first_tile = true;
 
   // this warp's samples and their cost cotangents; an inactive sample (k >= K or w_k = 0)
   // runs from the zero state with Sbar = 0, so that everything it adds is zero
@@ -273,14 +305,12 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int t0 = seg * every;
     const int nst = min(every, T - t0);
+    const int nsub = (nst + sub - 1) / sub;
     if (warp_active) {
-      // (a) re-run the segment forward from its checkpoints, both samples side by side
-      float x[SPW][7];
+      // the segment's checkpoint and controls
 #pragma unroll
       for (int q = 0; q < SPW; ++q) {
-        const float *ck = a.ckpt + ((size_t)kq[q] * n_ck + seg) * 7;
-#pragma unroll
-        for (int c = 0; c < 7; ++c) x[q][c] = act[q] ? __ldg(ck + c) : 0.0f;
+        if (lane < 7) xs[q][lane] = act[q] ? __ldg(a.ckpt + ((size_t)kq[q] * n_ck + seg) * 7 + lane) : 0.0f;
         if (lane < nst) {
           const int t = t0 + lane;
           const float2 e = noise_at(p, (uint32_t)kq[q], (uint32_t)t);
@@ -289,267 +319,377 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adj_backward_kernel(const __gr
           *reinterpret_cast<float4 *>(vg[q] + 4 * lane) =
               make_float4(v0, v1, fminf(fmaxf(v0, p.umin0), p.umax0), fminf(fmaxf(v1, p.umin1), p.umax1));
         }
-        if (lane < 7) xs[q][lane] = x[q][lane];
       }
       __syncwarp();
-      for (int i = 0; i < nst; ++i) {
-#pragma unroll
-        for (int q = 0; q < SPW; ++q) {
-          const float z[6] = {x[q][3], x[q][4], x[q][5], x[q][6], vg[q][4 * i + 2], vg[q][4 * i + 3]};
-#pragma unroll
-          for (int m = 0; m < M; ++m) {
-            float acc = b1r[m];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) acc = fmaf(W1r[m][c], z[c], acc);
-            hs1[q][i * H + lane + 32 * m] = activation<ACT>(acc);
-          }
-        }
-        __syncwarp();
-        float acc2[SPW][M];
+    }
+    for (int b = nsub - 1; b >= 0; --b) {
+      const int ib0 = b * sub, ie = min(ib0 + sub, nst);
+      if (warp_active) {
+        // (a) forward: the first pass runs the whole segment from the checkpoint (all states
+        // kept); later passes re-run one sub-segment from its stored start state.  Rows of
+        // h1 and h2 are kept for the sub-segment's steps only.
+        const int i_start = b == nsub - 1 ? 0 : ib0;
+        float x[SPW][7];
 #pragma unroll
         for (int q = 0; q < SPW; ++q)
 #pragma unroll
-          for (int m = 0; m < M; ++m) acc2[q][m] = b2r[m];
-#pragma unroll 4
-        for (int ii = 0; ii < H; ii += 4) {
-          float4 hv[SPW];
+          for (int c = 0; c < 7; ++c) x[q][c] = xs[q][8 * i_start + c];
+        for (int i = i_start; i < ie; ++i) {
+          const int r = i >= ib0 ? i - ib0 : 0;  // row slot (rows before the sub-segment are scratch)
 #pragma unroll
-          for (int q = 0; q < SPW; ++q) hv[q] = *reinterpret_cast<const float4 *>(hs1[q] + i * H + ii);
+          for (int q = 0; q < SPW; ++q) {
+            const float z[6] = {x[q][3], x[q][4], x[q][5], x[q][6], vg[q][4 * i + 2], vg[q][4 * i + 3]};
+            float h1v[M];
 #pragma unroll
-          for (int m = 0; m < M; ++m) {
-            const float *w = W2T_s + ii * H + lane + 32 * m;
-            const float w0 = w[0], w1 = w[H], w2 = w[2 * H], w3 = w[3 * H];
+            for (int m = 0; m < M; ++m) {
+              float acc = b1_s[i1 + m];
 #pragma unroll
-            for (int q = 0; q < SPW; ++q) {
-              acc2[q][m] = fmaf(w0, hv[q].x, acc2[q][m]);
-              acc2[q][m] = fmaf(w1, hv[q].y, acc2[q][m]);
-              acc2[q][m] = fmaf(w2, hv[q].z, acc2[q][m]);
-              acc2[q][m] = fmaf(w3, hv[q].w, acc2[q][m]);
+              for (int c = 0; c < 6; ++c) acc = fmaf(W1r[m][c], z[c], acc);
+              h1v[m] = activation<ACT>(acc);
+            }
+            if constexpr (M == 2) {
+              *reinterpret_cast<float2 *>(hs1[q] + r * H + i1) = make_float2(h1v[0], h1v[1]);
+            } else {
+              hs1[q][r * H + i1] = h1v[0];
             }
           }
-        }
+          __syncwarp();
+          float pa[R][SPW];
 #pragma unroll
-        for (int q = 0; q < SPW; ++q) {
-          float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          for (int rr = 0; rr < R; ++rr)
 #pragma unroll
-          for (int m = 0; m < M; ++m) {
-            const float h2 = activation<ACT>(acc2[q][m]);
-            hs2[q][i * H + lane + 32 * m] = h2;
+            for (int q = 0; q < SPW; ++q) pa[rr][q] = 0.0f;
+#pragma unroll 4
+          for (int ii = 0; ii < HH; ii += 4) {
+            float4 hv[SPW];
 #pragma unroll
-            for (int o = 0; o < 4; ++o) d[o] = fmaf(W3c[m][o], h2, d[o]);
+            for (int q = 0; q < SPW; ++q) hv[q] = *reinterpret_cast<const float4 *>(hs1[q] + r * H + HH * ch + ii);
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+              const float4 w = *reinterpret_cast<const float4 *>(W2_s + (r4 + 16 * rr) * WS + HH * ch + ii);
+#pragma unroll
+              for (int q = 0; q < SPW; ++q) {
+                pa[rr][q] = fmaf(w.x, hv[q].x, pa[rr][q]);
+                pa[rr][q] = fmaf(w.y, hv[q].y, pa[rr][q]);
+                pa[rr][q] = fmaf(w.z, hv[q].z, pa[rr][q]);
+                pa[rr][q] = fmaf(w.w, hv[q].w, pa[rr][q]);
+              }
+            }
           }
+          // rows r4 + 16 (ch + 2 m) = lane + 32 m stay; the partner's half arrives by shuffle
+          float acc2[SPW][M];
 #pragma unroll
-          for (int o = 0; o < 4; ++o) d[o] = warp_sum(d[o]) + b3u[o];
-          float sn, cs;
-          sincosf(x[q][2], &sn, &cs);
-          const float nx0 = x[q][0] + (cs * x[q][4] - sn * x[q][5]) * dt;
-          const float nx1 = x[q][1] + (sn * x[q][4] + cs * x[q][5]) * dt;
-          const float nx2 = x[q][2] + x[q][6] * dt;
-          x[q][0] = nx0;
-          x[q][1] = nx1;
-          x[q][2] = nx2;
+          for (int m = 0; m < M; ++m)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) x[q][3 + c] = x[q][3 + c] + d[c] * dt;
-          if (lane < 7) xs[q][8 * (i + 1) + lane] = x[q][lane];
+            for (int q = 0; q < SPW; ++q) {
+              const float mine = ch ? pa[2 * m + 1][q] : pa[2 * m][q];
+              const float send = ch ? pa[2 * m][q] : pa[2 * m + 1][q];
+              acc2[q][m] = b2_s[lane + 32 * m] + (mine + __shfl_xor_sync(FULL_MASK, send, 16));
+            }
+          __syncwarp();  // the row slot is rewritten by the next step when r is the scratch slot
+#pragma unroll
+          for (int q = 0; q < SPW; ++q) {
+            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              const float h2 = activation<ACT>(acc2[q][m]);
+              hs2[q][r * H + lane + 32 * m] = h2;
+              const float4 w3 = *reinterpret_cast<const float4 *>(W3_s + 4 * (lane + 32 * m));
+              d[0] = fmaf(w3.x, h2, d[0]);
+              d[1] = fmaf(w3.y, h2, d[1]);
+              d[2] = fmaf(w3.z, h2, d[2]);
+              d[3] = fmaf(w3.w, h2, d[3]);
+            }
+#pragma unroll
+            for (int o = 0; o < 4; ++o) d[o] = warp_sum(d[o]) + __ldg(net + net_off_b3(H) + o);
+            float sn, cs;
+            sincosf(x[q][2], &sn, &cs);
+            const float nx0 = x[q][0] + (cs * x[q][4] - sn * x[q][5]) * dt;
+            const float nx1 = x[q][1] + (sn * x[q][4] + cs * x[q][5]) * dt;
+            const float nx2 = x[q][2] + x[q][6] * dt;
+            x[q][0] = nx0;
+            x[q][1] = nx1;
+            x[q][2] = nx2;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) x[q][3 + c] = x[q][3 + c] + d[c] * dt;
+            float xl = x[q][0];
+#pragma unroll
+            for (int c = 1; c < 7; ++c) xl = lane == c ? x[q][c] : xl;
+            if (lane < 7) xs[q][8 * (i + 1) + lane] = xl;
+          }
         }
-      }
-      __syncwarp();
-      // (b) cost slopes at x_{t0+1 .. t0+nst}, one step per lane; Sbar-weighted components
-      if (lane < nst) {
+        __syncwarp();
+        // (b) on the first pass: cost slopes at x_{t0+1 .. t0+nst}, one step per lane, and the
+        // Sbar-weighted components
+        if (b == nsub - 1) {
+          float gcw[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          if (lane < nst) {
 #pragma unroll
-        for (int q = 0; q < SPW; ++q) {
-          const float *xt = xs[q] + 8 * (lane + 1);
-          float g4[4], c4[4];
-          state_cost_slope(p, xt[0], xt[1], xt[4], xt[5], t0 + lane + 1, g4, c4);
-          *reinterpret_cast<float4 *>(gc[q] + 4 * lane) = make_float4(g4[0], g4[1], g4[2], g4[3]);
+            for (int q = 0; q < SPW; ++q) {
+              const float *xt = xs[q] + 8 * (lane + 1);
+              float g4[4], c4[4];
+              state_cost_slope(p, xt[0], xt[1], xt[4], xt[5], t0 + lane + 1, g4, c4);
+              *reinterpret_cast<float4 *>(gc[q] + 4 * lane) = make_float4(g4[0], g4[1], g4[2], g4[3]);
 #pragma unroll
-          for (int o = 0; o < 4; ++o) gcw[o] = fmaf(Sbar[q], c4[o], gcw[o]);
-        }
-      }
-      __syncwarp();
-      // (c) reverse the segment's steps
-      for (int i = nst - 1; i >= 0; --i) {
-        const int t = t0 + i;  // step t -> t + 1 used v_t
-        float xbp[SPW][7], db[SPW][4];
-#pragma unroll
-        for (int q = 0; q < SPW; ++q) {
-          const float4 gci = *reinterpret_cast<const float4 *>(gc[q] + 4 * i);
-          xb[q][0] = fmaf(Sbar[q], gci.x, xb[q][0]);
-          xb[q][1] = fmaf(Sbar[q], gci.y, xb[q][1]);
-          xb[q][4] = fmaf(Sbar[q], gci.z, xb[q][4]);
-          xb[q][5] = fmaf(Sbar[q], gci.w, xb[q][5]);
-          const float *xp = xs[q] + 8 * i;
-          const float th = xp[2], vx = xp[4], vy = xp[5];
-          float sn, cs;
-          sincosf(th, &sn, &cs);
-#pragma unroll
-          for (int c = 0; c < 7; ++c) xbp[q][c] = xb[q][c];
-          xbp[q][2] += dt * (xb[q][0] * (-sn * vx - cs * vy) + xb[q][1] * (cs * vx - sn * vy));
-          xbp[q][4] += dt * (xb[q][0] * cs + xb[q][1] * sn);
-          xbp[q][5] += dt * (-xb[q][0] * sn + xb[q][1] * cs);
-          xbp[q][6] += dt * xb[q][2];
+              for (int o = 0; o < 4; ++o) gcw[o] = fmaf(Sbar[q], c4[o], gcw[o]);
+            }
+          }
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
-            db[q][o] = dt * xb[q][3 + o];
-            gb3[o] += db[q][o];
-          }
-#pragma unroll
-          for (int m = 0; m < M; ++m) {
-            const float h2 = hs2[q][i * H + lane + 32 * m];
-            float hb = 0.0f;
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-              hb = fmaf(W3c[m][o], db[q][o], hb);
-              gW3[m][o] = fmaf(db[q][o], h2, gW3[m][o]);
-            }
-            const float a2b = ACT == 1 ? hb : hb * (1.0f - h2 * h2);
-            gb2[m] += a2b;
-            hs2[q][i * H + lane + 32 * m] = a2b;
+            const float c = warp_sum(gcw[o]);
+            if (lane == 0) wsum_s[8 * warp + 4 + o] += c;
           }
         }
         __syncwarp();
-        float h1b[SPW][M];
+        // (c) reverse the sub-segment's steps
+        for (int i = ie - 1; i >= ib0; --i) {
+          const int t = t0 + i;  // step t -> t + 1 used v_t
+          const int r = i - ib0;
+          float xbp[SPW][7], db[SPW][4];
 #pragma unroll
-        for (int q = 0; q < SPW; ++q)
+          for (int q = 0; q < SPW; ++q) {
+            const float4 gci = *reinterpret_cast<const float4 *>(gc[q] + 4 * i);
+            xb[q][0] = fmaf(Sbar[q], gci.x, xb[q][0]);
+            xb[q][1] = fmaf(Sbar[q], gci.y, xb[q][1]);
+            xb[q][4] = fmaf(Sbar[q], gci.z, xb[q][4]);
+            xb[q][5] = fmaf(Sbar[q], gci.w, xb[q][5]);
+            const float *xp = xs[q] + 8 * i;
+            const float th = xp[2], vx = xp[4], vy = xp[5];
+            float sn, cs;
+            sincosf(th, &sn, &cs);
 #pragma unroll
-          for (int m = 0; m < M; ++m) h1b[q][m] = 0.0f;
-#pragma unroll 4
-        for (int jj = 0; jj < H; jj += 4) {
-          float4 av[SPW];
+            for (int c = 0; c < 7; ++c) xbp[q][c] = xb[q][c];
+            xbp[q][2] += dt * (xb[q][0] * (-sn * vx - cs * vy) + xb[q][1] * (cs * vx - sn * vy));
+            xbp[q][4] += dt * (xb[q][0] * cs + xb[q][1] * sn);
+            xbp[q][5] += dt * (-xb[q][0] * sn + xb[q][1] * cs);
+            xbp[q][6] += dt * xb[q][2];
 #pragma unroll
-          for (int q = 0; q < SPW; ++q) av[q] = *reinterpret_cast<const float4 *>(hs2[q] + i * H + jj);
+            for (int o = 0; o < 4; ++o) db[q][o] = dt * xb[q][3 + o];
 #pragma unroll
-          for (int m = 0; m < M; ++m) {
-            const float *w = W2_s + jj * H + lane + 32 * m;
-            const float w0 = w[0], w1 = w[H], w2 = w[2 * H], w3 = w[3 * H];
+            for (int m = 0; m < M; ++m) {
+              const float h2 = hs2[q][r * H + lane + 32 * m];
+              const float4 w3 = *reinterpret_cast<const float4 *>(W3_s + 4 * (lane + 32 * m));
+              float hb = w3.x * db[q][0];
+              hb = fmaf(w3.y, db[q][1], hb);
+              hb = fmaf(w3.z, db[q][2], hb);
+              hb = fmaf(w3.w, db[q][3], hb);
+#pragma unroll
+              for (int o = 0; o < 4; ++o) gW3[m][o] = fmaf(db[q][o], h2, gW3[m][o]);
+              const float a2b = ACT == 1 ? hb : hb * (1.0f - h2 * h2);
+              gb2[m] += a2b;
+              hs2[q][r * H + lane + 32 * m] = a2b;
+            }
+          }
+          if (lane == 0) {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) wsum_s[8 * warp + o] += db[0][o] + db[1][o];
+          }
+          __syncwarp();
+          float pb[CW][SPW];
+#pragma unroll
+          for (int cc = 0; cc < CW; ++cc)
+#pragma unroll
+            for (int q = 0; q < SPW; ++q) pb[cc][q] = 0.0f;
+#pragma unroll 2
+          for (int jj = 0; jj < HH; jj += 4) {
+            float4 av[SPW];
+#pragma unroll
+            for (int q = 0; q < SPW; ++q) av[q] = *reinterpret_cast<const float4 *>(hs2[q] + r * H + HH * ch + jj);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const float *wrow = W2_s + (HH * ch + jj + kk) * WS + CW * r4;
+              float wv[CW];
+              if constexpr (CW == 4) {
+                const float4 w = *reinterpret_cast<const float4 *>(wrow);
+                wv[0] = w.x; wv[1] = w.y; wv[2] = w.z; wv[3] = w.w;
+              } else {
+                const float2 w = *reinterpret_cast<const float2 *>(wrow);
+                wv[0] = w.x; wv[1] = w.y;
+              }
+#pragma unroll
+              for (int q = 0; q < SPW; ++q) {
+                const float a = kk == 0 ? av[q].x : kk == 1 ? av[q].y : kk == 2 ? av[q].z : av[q].w;
+#pragma unroll
+                for (int cc = 0; cc < CW; ++cc) pb[cc][q] = fmaf(wv[cc], a, pb[cc][q]);
+              }
+            }
+          }
+          // columns CW r4 + M ch + m stay; the partner's half arrives by shuffle
+          float h1b[SPW][M];
+#pragma unroll
+          for (int m = 0; m < M; ++m)
 #pragma unroll
             for (int q = 0; q < SPW; ++q) {
-              h1b[q][m] = fmaf(w0, av[q].x, h1b[q][m]);
-              h1b[q][m] = fmaf(w1, av[q].y, h1b[q][m]);
-              h1b[q][m] = fmaf(w2, av[q].z, h1b[q][m]);
-              h1b[q][m] = fmaf(w3, av[q].w, h1b[q][m]);
+              const float mine = ch ? pb[M + m][q] : pb[m][q];
+              const float send = ch ? pb[m][q] : pb[M + m][q];
+              h1b[q][m] = mine + __shfl_xor_sync(FULL_MASK, send, 16);
             }
-          }
-        }
-        float ub[2] = {0.0f, 0.0f};
+          float ub[2] = {0.0f, 0.0f};
 #pragma unroll
-        for (int q = 0; q < SPW; ++q) {
-          const float *xp = xs[q] + 8 * i;
-          const float4 vgi = *reinterpret_cast<const float4 *>(vg[q] + 4 * i);
-          const float z[6] = {xp[3], xp[4], xp[5], xp[6], vgi.z, vgi.w};
-          float zb[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          for (int q = 0; q < SPW; ++q) {
+            const float *xp = xs[q] + 8 * i;
+            const float4 vgi = *reinterpret_cast<const float4 *>(vg[q] + 4 * i);
+            const float z[6] = {xp[3], xp[4], xp[5], xp[6], vgi.z, vgi.w};
+            float zb[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-          for (int m = 0; m < M; ++m) {
-            const float h1 = hs1[q][i * H + lane + 32 * m];
-            const float a1b = ACT == 1 ? h1b[q][m] : h1b[q][m] * (1.0f - h1 * h1);
-            gb1[m] += a1b;
+            for (int m = 0; m < M; ++m) {
+              const float h1 = hs1[q][r * H + i1 + m];
+              const float a1b = ACT == 1 ? h1b[q][m] : h1b[q][m] * (1.0f - h1 * h1);
+              gb1[m] += a1b;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-              gW1[m][c] = fmaf(a1b, z[c], gW1[m][c]);
-              zb[c] = fmaf(W1r[m][c], a1b, zb[c]);
+              for (int c = 0; c < 6; ++c) {
+                gW1[m][c] = fmaf(a1b, z[c], gW1[m][c]);
+                zb[c] = fmaf(W1r[m][c], a1b, zb[c]);
+              }
             }
-          }
 #pragma unroll
-          for (int c = 0; c < 6; ++c) zb[c] = warp_sum(zb[c]);
+            for (int c = 0; c < 6; ++c) zb[c] = warp_sum(zb[c]);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) xbp[q][3 + c] += zb[c];
-          // the clamp g passes the slope inside [u_min, u_max]; the control-cost term
-          // gamma u' Sigma^-1 v adds gamma u/sigma^2 to dL/dv and gamma v/sigma^2 to dL/du
-          float vb0 = (vgi.x >= p.umin0 && vgi.x <= p.umax0) ? zb[4] : 0.0f;
-          float vb1 = (vgi.y >= p.umin1 && vgi.y <= p.umax1) ? zb[5] : 0.0f;
-          float ub0 = 0.0f, ub1 = 0.0f;
-          if (p.gamma != 0.0f) {
-            const float u0 = __ldg(p.U + 2 * t), u1 = __ldg(p.U + 2 * t + 1);
-            const float sg = Sbar[q] * p.gamma;
-            vb0 = fmaf(sg * u0, p.inv_sig2_0, vb0);
-            vb1 = fmaf(sg * u1, p.inv_sig2_1, vb1);
-            ub0 = sg * vgi.x * p.inv_sig2_0;
-            ub1 = sg * vgi.y * p.inv_sig2_1;
-          }
-          if (impq[q]) {
-            ub0 += vb0;
-            ub1 += vb1;
-          }
-          ub[0] += ub0;
-          ub[1] += ub1;
+            for (int c = 0; c < 4; ++c) xbp[q][3 + c] += zb[c];
+            // the clamp g passes the slope inside [u_min, u_max]; the control-cost term
+            // gamma u' Sigma^-1 v adds gamma u/sigma^2 to dL/dv and gamma v/sigma^2 to dL/du
+            float vb0 = (vgi.x >= p.umin0 && vgi.x <= p.umax0) ? zb[4] : 0.0f;
+            float vb1 = (vgi.y >= p.umin1 && vgi.y <= p.umax1) ? zb[5] : 0.0f;
+            float ub0 = 0.0f, ub1 = 0.0f;
+            if (p.gamma != 0.0f) {
+              const float u0 = __ldg(p.U + 2 * t), u1 = __ldg(p.U + 2 * t + 1);
+              const float sg = Sbar[q] * p.gamma;
+              vb0 = fmaf(sg * u0, p.inv_sig2_0, vb0);
+              vb1 = fmaf(sg * u1, p.inv_sig2_1, vb1);
+              ub0 = sg * vgi.x * p.inv_sig2_0;
+              ub1 = sg * vgi.y * p.inv_sig2_1;
+            }
+            if (impq[q]) {
+              ub0 += vb0;
+              ub1 += vb1;
+            }
+            ub[0] += ub0;
+            ub[1] += ub1;
 #pragma unroll
-          for (int c = 0; c < 7; ++c) xb[q][c] = xbp[q][c];
-        }
-        if (lane == 0) {
-          ub_s[warp * 2 * T + 2 * t] = ub[0];
-          ub_s[warp * 2 * T + 2 * t + 1] = ub[1];
+            for (int c = 0; c < 7; ++c) xb[q][c] = xbp[q][c];
+          }
+          if (lane == 0) {
+            *reinterpret_cast<float2 *>(ub_w + 2 * t) = make_float2(ub[0], ub[1]);
+          }
         }
       }
-    }
-    __syncthreads();
-    // (d) W2 gradient: sum over this CTA's active samples and the segment's steps of a2bar h1^T
-    for (int sidx = 0; sidx < SC; ++sidx) {
-      const int ks = blockIdx.x * SC + sidx;
-      if (ks >= K || __ldg(a.w + ks) == 0.0f) continue;
-      const float *h1w = sreg + sidx * sf + 8 * (every + 1) + 8 * every;
-      const float *a2w = h1w + H * every;
-      for (int i = 0; i < nst; ++i) {
-        const float4 av = *reinterpret_cast<const float4 *>(a2w + i * H + TJ * jb);
-        const float ar[4] = {av.x, av.y, av.z, av.w};
-        float hr[TI];
+      __syncthreads();
+      // (d) W2 gradient: sum over this CTA's active samples and the sub-segment's steps of
+      // a2bar h1^T, added to the thread's tile of the record (first tile: stored)
+      float gW2[TJ][TI];
+#pragma unroll
+      for (int rr = 0; rr < TJ; ++rr)
+#pragma unroll
+        for (int c = 0; c < TI; ++c) gW2[rr][c] = 0.0f;
+      const int nrow = ie - ib0;
+      for (int sidx = 0; sidx < SC; ++sidx) {
+        const int ks = blockIdx.x * SC + sidx;
+        if (ks >= K || __ldg(a.w + ks) == 0.0f) continue;
+        const float *h1w = sreg + sidx * sf + 8 * (every + 1) + 8 * every;
+        const float *a2w = h1w + H * sub;
+        for (int i = 0; i < nrow; ++i) {
+          float ar[TJ];
+          if constexpr (TJ == 4) {
+            const float4 av = *reinterpret_cast<const float4 *>(a2w + i * H + TJ * jb);
+            ar[0] = av.x; ar[1] = av.y; ar[2] = av.z; ar[3] = av.w;
+          } else {
+            const float2 av = *reinterpret_cast<const float2 *>(a2w + i * H + TJ * jb);
+            ar[0] = av.x; ar[1] = av.y;
+          }
+          float hr[TI];
+          if constexpr (TI == 2) {
+            const float2 hv = *reinterpret_cast<const float2 *>(h1w + i * H + TI * ib);
+            hr[0] = hv.x; hr[1] = hv.y;
+          } else {
+#pragma unroll
+            for (int g = 0; g < TI / 4; ++g) {
+              const float4 hv = *reinterpret_cast<const float4 *>(h1w + i * H + 4 * ib + 4 * NIB * g);
+              hr[4 * g] = hv.x; hr[4 * g + 1] = hv.y; hr[4 * g + 2] = hv.z; hr[4 * g + 3] = hv.w;
+            }
+          }
+#pragma unroll
+          for (int rr = 0; rr < TJ; ++rr)
+#pragma unroll
+            for (int c = 0; c < TI; ++c) gW2[rr][c] = fmaf(ar[rr], hr[c], gW2[rr][c]);
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < TJ; ++rr) {
+        float *dst = rec + net_off_W2(H) + (TJ * jb + rr) * H;
         if constexpr (TI == 2) {
-          const float2 hv = *reinterpret_cast<const float2 *>(h1w + i * H + TI * ib);
-          hr[0] = hv.x; hr[1] = hv.y;
+          float2 *d2 = reinterpret_cast<float2 *>(dst + TI * ib);
+          float2 v = make_float2(gW2[rr][0], gW2[rr][1]);
+          if (!first_tile) {
+            const float2 o = *d2;
+            v.x += o.x;
+            v.y += o.y;
+          }
+          *d2 = v;
         } else {
 #pragma unroll
-          for (int c4 = 0; c4 < TI; c4 += 4) {
-            const float4 hv = *reinterpret_cast<const float4 *>(h1w + i * H + TI * ib + c4);
-            hr[c4] = hv.x; hr[c4 + 1] = hv.y; hr[c4 + 2] = hv.z; hr[c4 + 3] = hv.w;
+          for (int g = 0; g < TI / 4; ++g) {
+            float4 *d4 = reinterpret_cast<float4 *>(dst + 4 * ib + 4 * NIB * g);
+            float4 v = make_float4(gW2[rr][4 * g], gW2[rr][4 * g + 1], gW2[rr][4 * g + 2], gW2[rr][4 * g + 3]);
+            if (!first_tile) {
+              const float4 o = *d4;
+              v.x += o.x;
+              v.y += o.y;
+              v.z += o.z;
+              v.w += o.w;
+            }
+            *d4 = v;
           }
         }
-#pragma unroll
-        for (int r = 0; r < TJ; ++r)
-#pragma unroll
-          for (int c = 0; c < TI; ++c) gW2[r][c] = fmaf(ar[r], hr[c], gW2[r][c]);
       }
+      first_tile = false;
+      __syncthreads();
     }
-    __syncthreads();
   }
 
-  // ---- this CTA's record: per-warp accumulators summed in warp order ----
+  // ---- this CTA's record (the per-sample regions are free now): per-warp accumulators
+  // summed in warp order; the W2 part is already in place ----
+  float *rec_s = sreg;
   const int nf = net_floats(H);
+  for (int e = threadIdx.x; e < nrec; e += NW * 32) rec_s[e] = 0.0f;
+  __syncthreads();
   for (int w = 0; w < NW; ++w) {
     if (warp == w) {
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         const int j = lane + 32 * m;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) rec_s[net_off_W1(H) + j * 6 + c] += gW1[m][c];
-        rec_s[net_off_b1(H) + j] += gb1[m];
+        for (int c = 0; c < 6; ++c) rec_s[net_off_W1(H) + (i1 + m) * 6 + c] += gW1[m][c];
+        rec_s[net_off_b1(H) + i1 + m] += gb1[m];
         rec_s[net_off_b2(H) + j] += gb2[m];
 #pragma unroll
         for (int o = 0; o < 4; ++o) rec_s[net_off_W3(H) + o * H + j] += gW3[m][o];
       }
-      if (lane == 0) {
-#pragma unroll
-        for (int o = 0; o < 4; ++o) rec_s[net_off_b3(H) + o] += gb3[o];
-      }
-      // cost multipliers: the Sbar-weighted components, summed over the lanes' steps
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        const float c = warp_sum(gcw[o]);
-        if (lane == 0) rec_s[nf + o] += c;
+      // b3 and the cost multipliers (the Sbar-weighted components)
+      if (lane < 4) {
+        rec_s[net_off_b3(H) + lane] += wsum_s[8 * w + lane];
+        rec_s[nf + lane] += wsum_s[8 * w + 4 + lane];
       }
     }
     __syncthreads();
   }
+  // warps with an active sample wrote their dL/dU rows
+  unsigned wmask = 0;
+  for (int w = 0; w < NW; ++w)
 #pragma unroll
-  for (int r = 0; r < TJ; ++r)
-#pragma unroll
-    for (int c = 0; c < TI; ++c) rec_s[net_off_W2(H) + (TJ * jb + r) * H + TI * ib + c] = gW2[r][c];
+    for (int q = 0; q < SPW; ++q) {
+      const int k = blockIdx.x * SC + w * SPW + q;
+      if (k < K && __ldg(a.w + k) != 0.0f) wmask |= 1u << w;
+    }
   for (int e = threadIdx.x; e < 2 * T; e += NW * 32) {
     float sum = 0.0f;
-    for (int w = 0; w < NW; ++w) sum += ub_s[w * 2 * T + e];
+    for (int w = 0; w < NW; ++w)
+      if (wmask >> w & 1u) sum += rec[nrec + (size_t)w * 2 * T + e];
     rec_s[nf + 4 + e] = sum;
   }
   __syncthreads();
-  float *rec = a.part + (size_t)blockIdx.x * nrec;
-  for (int e = threadIdx.x; e < nrec; e += NW * 32) rec[e] = rec_s[e];
+  const int w2_lo = net_off_W2(H), w2_hi = w2_lo + H * H;
+  for (int e = threadIdx.x; e < nrec; e += NW * 32)
+    if (e < w2_lo || e >= w2_hi) rec[e] = rec_s[e];
 }
 
 // Sum the per-CTA records in CTA order; warp w of a block takes records w, w + 8, ...
@@ -600,8 +740,10 @@ cudaError_t launch_bwd(const AdjParams &a, int n_cta, size_t smem, cudaStream_t 
 }  // namespace
 
 int adj_num_ctas(int K) { return (K + kAdjSamples - 1) / kAdjSamples; }
-size_t adj_part_floats(int K, int H, int T_max) { return (size_t)adj_num_ctas(K) * adj_rec_floats(H, T_max); }
-size_t adj_smem_bytes(int H, int every, int T) { return sizeof(float) * adj_smem_floats(H, every, T); }
+size_t adj_part_floats(int K, int H, int T_max) { return (size_t)adj_num_ctas(K) * adj_cta_floats(H, T_max); }
+size_t adj_smem_bytes(int H, int every, int T) {
+  return sizeof(float) * adj_smem_floats(H, every, adj_sub_len(H, every, T), T);
+}
 
 cudaError_t adj_launch_scalars(int K, int T, int n_imp, const float *w, const float *S, const float *Uo,
                                const float *gUo, const float *gJ, float *scal, float *J_out, cudaStream_t s) {
@@ -609,10 +751,12 @@ cudaError_t adj_launch_scalars(int K, int T, int n_imp, const float *w, const fl
   return cudaGetLastError();
 }
 
-cudaError_t adj_launch_backward(const AdjParams &a, float *g_cost_w, float *g_U, float *g_net, cudaStream_t s) {
+cudaError_t adj_launch_backward(const AdjParams &a_in, float *g_cost_w, float *g_U, float *g_net, cudaStream_t s) {
+  AdjParams a = a_in;
   const int H = a.p.H, T = a.p.T;
   const int n_cta = adj_num_ctas(a.p.K);
-  const size_t smem = adj_smem_bytes(H, a.every, T);
+  a.sub = adj_sub_len(H, a.every, T);
+  const size_t smem = sizeof(float) * adj_smem_floats(H, a.every, a.sub, T);
   cudaError_t e;
   if (H == 32) e = a.p.activation == 1 ? launch_bwd<32, 1>(a, n_cta, smem, s) : launch_bwd<32, 0>(a, n_cta, smem, s);
   else if (H == 64) e = a.p.activation == 1 ? launch_bwd<64, 1>(a, n_cta, smem, s) : launch_bwd<64, 0>(a, n_cta, smem, s);
@@ -620,7 +764,7 @@ cudaError_t adj_launch_backward(const AdjParams &a, float *g_cost_w, float *g_U,
   if (e != cudaSuccess) return e;
   const int nf = net_floats(H);
   const int n_out = nf + 4 + 2 * T;
-  adj_reduce_kernel<<<(n_out + 31) / 32, 256, 0, s>>>(n_cta, adj_rec_floats(H, T), nf, T, a.part, a.gUo, a.scal,
+  adj_reduce_kernel<<<(n_out + 31) / 32, 256, 0, s>>>(n_cta, (int)adj_cta_floats(H, T), nf, T, a.part, a.gUo, a.scal,
                                                       g_net, g_cost_w, g_U);
   return cudaGetLastError();
 }

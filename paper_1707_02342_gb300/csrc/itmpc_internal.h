@@ -217,6 +217,7 @@ struct AdjParams {
   IterParams p;        // dynamics, costs, noise counters, map, network, U
   const float *ckpt;   // K x (T / every + 1) x 7: x_t at t = 0, every, 2 every, ... (forward launch)
   int every;           // checkpoint interval, 1..32
+  int sub;             // sub-segment length (set by adj_launch_backward)
   const float *w, *S;  // forward weights and costs (K)
   const float *gUo;    // dL/dU' (T x 2) or null
   const float *scal;   // [J, c0 = gU . U', sum of importance weights, gJ] (adj_launch_scalars)
