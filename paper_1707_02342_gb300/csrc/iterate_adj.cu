@@ -41,16 +41,21 @@ namespace itmpc {
 
 namespace {
 
-constexpr int kAdjWarps = 8;                     // warps per CTA
 constexpr int kAdjSPW = 2;                       // samples per warp, side by side
-constexpr int kAdjSamples = kAdjWarps * kAdjSPW; // samples per CTA
-constexpr int kAdjCtasPerSm = 2;                 // the shared-memory and register budget aims at 2 CTAs per SM
-constexpr size_t kAdjSmemTarget = 113 * 1024;    // 228 KB per SM / 2, less the 1 KB the SM keeps per CTA
+constexpr int kAdjMinWarps = 8, kAdjMaxWarps = 16; // warps per CTA: one CTA per SM
+constexpr int kAdjDThreads = 128;                // threads per group in the W2-gradient GEMM (two groups)
+
+// Warps per CTA: the samples spread over one CTA per SM (two per warp), 8..16 warps.
+inline int adj_warps(int K, int n_sm) {
+  const int per_sm = (K + n_sm - 1) / n_sm;
+  const int nw = (per_sm + kAdjSPW - 1) / kAdjSPW;
+  return nw < kAdjMinWarps ? kAdjMinWarps : (nw > kAdjMaxWarps ? kAdjMaxWarps : nw);
+}
 
 __host__ __device__ inline int adj_rec_floats(int H, int T) { return (net_floats(H) + 4 + 2 * T + 3) & ~3; }
 // A CTA's slot in the record buffer: its record, then one dL/dU row (2T) per warp.
-__host__ __device__ inline size_t adj_cta_floats(int H, int T) {
-  return (size_t)adj_rec_floats(H, T) + (size_t)kAdjWarps * 2 * T;
+__host__ __device__ inline size_t adj_cta_floats(int H, int T, int nw) {
+  return (size_t)adj_rec_floats(H, T) + (size_t)nw * 2 * T;
 }
 __host__ __device__ inline int adj_w2_stride(int H) { return H + 4; }
 
@@ -63,27 +68,27 @@ __host__ __device__ inline size_t adj_sample_floats(int H, int every, int sub) {
          + 2 * (size_t)H * sub;     // h1 rows, h2 rows (then a2bar rows) of the sub-segment
 }
 
-// W2 (rows padded), the per-warp dL/dU rows, then the per-sample regions; the CTA's
-// record reuses the per-sample regions once the last segment is done.
-__host__ __device__ inline size_t adj_region_floats(int H, int every, int sub, int T) {
-  const size_t s = kAdjSamples * adj_sample_floats(H, every, sub);
+// The per-sample regions; the CTA's record reuses them once the last segment is done.
+__host__ __device__ inline size_t adj_region_floats(int H, int every, int sub, int T, int nw) {
+  const size_t s = (size_t)kAdjSPW * nw * adj_sample_floats(H, every, sub);
   const size_t r = (size_t)adj_rec_floats(H, T);
   return s > r ? s : r;
 }
 
 // W3 by neuron (4 floats each), b1, b2, and 8 per-warp sums (b3 gradient, cost components)
-__host__ __device__ inline int adj_small_floats(int H) { return 6 * H + 8 * kAdjWarps; }
+__host__ __device__ inline int adj_small_floats(int H, int nw) { return 6 * H + 8 * nw; }
 
-__host__ __device__ inline size_t adj_smem_floats(int H, int every, int sub, int T) {
-  return (size_t)H * adj_w2_stride(H) + adj_small_floats(H) + adj_region_floats(H, every, sub, T);
+// W2 (rows padded), the small tables, then the per-sample regions.
+__host__ __device__ inline size_t adj_smem_floats(int H, int every, int sub, int T, int nw) {
+  return (size_t)H * adj_w2_stride(H) + adj_small_floats(H, nw) + adj_region_floats(H, every, sub, T, nw);
 }
 
-// The longest sub-segment (every, every/2, every/3, ...) whose footprint fits the target;
+// The longest sub-segment (every, every/2, every/3, ...) whose footprint fits a CTA;
 // a sub-segment other than the segment's last is re-run from its stored start state.
-inline int adj_sub_len(int H, int every, int T) {
+inline int adj_sub_len(int H, int every, int T, int nw, size_t smem_max) {
   for (int n = 1; n <= every; ++n) {
     const int sub = (every + n - 1) / n;
-    if (sizeof(float) * adj_smem_floats(H, every, sub, T) <= kAdjSmemTarget) return sub;
+    if (sizeof(float) * adj_smem_floats(H, every, sub, T, nw) <= smem_max) return sub;
   }
   return 1;
 }
@@ -191,16 +196,18 @@ __global__ void __launch_bounds__(1024) adj_scalars_kernel(int K, int T, int n_i
 }
 
 template <int H, int ACT>
-__global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_kernel(const __grid_constant__ AdjParams a) {
-  constexpr int NW = kAdjWarps, SPW = kAdjSPW, SC = kAdjSamples;
+__global__ void __launch_bounds__(kAdjMaxWarps * 32, 1) adj_backward_kernel(const __grid_constant__ AdjParams a) {
+  constexpr int SPW = kAdjSPW;
   constexpr int M = H / 32;
   constexpr int WS = H + 4;             // padded W2 row: conflict-free in both orientations
-  constexpr int E = H * H / (NW * 32);  // W2-gradient entries per thread
+  constexpr int NTD = kAdjDThreads;
+  constexpr int E = H * H / NTD;         // W2-gradient entries per thread
   constexpr int TJ = E >= 8 ? 4 : 2, TI = E / TJ, NIB = H / TI;
   static_assert(E % 4 == 0 && (TI == 2 || TI % 4 == 0), "tile");
   const IterParams &p = a.p;
   const int T = p.T, K = p.K, every = a.every, sub = a.sub;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NW = blockDim.x >> 5, SC = SPW * NW, NT = blockDim.x;
   const size_t sf = adj_sample_floats(H, every, sub);
 
   extern __shared__ __align__(16) float sm[];
@@ -208,6 +215,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_ke
   float *W3_s = sm + H * WS;           // [j][o] = W3[o][j]
   float *b1_s = W3_s + 4 * H, *b2_s = b1_s + H;
   float *wsum_s = b2_s + H;            // NW x 8: per-warp b3 gradient (4), cost components (4)
+  // (b2_s + H and wsum_s + 8 NW are 16-byte aligned: H and 8 NW are multiples of 4)
   float *sreg = wsum_s + 8 * NW;       // SC per-sample regions; the CTA's record at the end
   float *xs[SPW], *vg[SPW], *gc[SPW], *hs1[SPW], *hs2[SPW];
 #pragma unroll
@@ -220,15 +228,15 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_ke
   }
 
   const float *net = p.net;
-  for (int e = threadIdx.x; e < H * H; e += NW * 32) W2_s[(e / H) * WS + e % H] = __ldg(net + net_off_W2(H) + e);
-  for (int e = threadIdx.x; e < 4 * H; e += NW * 32) W3_s[e] = __ldg(net + net_off_W3(H) + (e & 3) * H + (e >> 2));
-  for (int e = threadIdx.x; e < H; e += NW * 32) {
+  for (int e = threadIdx.x; e < H * H; e += NT) W2_s[(e / H) * WS + e % H] = __ldg(net + net_off_W2(H) + e);
+  for (int e = threadIdx.x; e < 4 * H; e += NT) W3_s[e] = __ldg(net + net_off_W3(H) + (e & 3) * H + (e >> 2));
+  for (int e = threadIdx.x; e < H; e += NT) {
     b1_s[e] = __ldg(net + net_off_b1(H) + e);
     b2_s[e] = __ldg(net + net_off_b2(H) + e);
   }
-  for (int e = threadIdx.x; e < 8 * NW; e += NW * 32) wsum_s[e] = 0.0f;
+  for (int e = threadIdx.x; e < 8 * NW; e += NT) wsum_s[e] = 0.0f;
   const int nrec = adj_rec_floats(H, T);
-  float *rec = a.part + (size_t)blockIdx.x * adj_cta_floats(H, T);
+  float *rec = a.part + (size_t)blockIdx.x * adj_cta_floats(H, T, NW);
   float *ub_w = rec + nrec + (size_t)warp * 2 * T;  // this warp's dL/dU row (written while it runs)
 
   // Register tiles of the two matrix-vector products (H/16 rows or columns per lane, half of
@@ -259,7 +267,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_ke
   }
   // this thread's W2-gradient tile: rows TJ*jb .. +3; columns in groups of 4 (TI = 2: one pair),
   // group g at 4*ib + 4*NIB*g, so that a quarter-warp's 16-byte loads are contiguous
-  const int jb = threadIdx.x / NIB, ib = threadIdx.x % NIB;
+  // Two groups of NTD threads (warps 0..7) take half of the CTA's samples each and add into
+  // the record in turn; the other warps wait at the barriers.
+  const int dhalf = threadIdx.x < 2 * NTD ? threadIdx.x / NTD : 2, dtid = threadIdx.x % NTD;
+  const int jb = dtid / NIB, ib = dtid % NIB;
   bool first_tile = true;
 
   // this warp's samples and their cost cotangents; an inactive sample (k >= K or w_k = 0)
@@ -582,7 +593,8 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_ke
 #pragma unroll
         for (int c = 0; c < TI; ++c) gW2[rr][c] = 0.0f;
       const int nrow = ie - ib0;
-      for (int sidx = 0; sidx < SC; ++sidx) {
+      const int s_lo = dhalf < 2 ? dhalf * NW : SC, s_hi = dhalf == 0 ? NW : SC;
+      for (int sidx = s_lo; sidx < s_hi; ++sidx) {
         const int ks = blockIdx.x * SC + sidx;
         if (ks >= K || __ldg(a.w + ks) == 0.0f) continue;
         const float *h1w = sreg + sidx * sf + 8 * (every + 1) + 8 * every;
@@ -613,31 +625,36 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_ke
             for (int c = 0; c < TI; ++c) gW2[rr][c] = fmaf(ar[rr], hr[c], gW2[rr][c]);
         }
       }
+      for (int turn = 0; turn < 2; ++turn) {
+        if (turn == 1) __syncthreads();
+        if (dhalf != turn) continue;
+        const bool store = first_tile && turn == 0;
 #pragma unroll
-      for (int rr = 0; rr < TJ; ++rr) {
-        float *dst = rec + net_off_W2(H) + (TJ * jb + rr) * H;
-        if constexpr (TI == 2) {
-          float2 *d2 = reinterpret_cast<float2 *>(dst + TI * ib);
-          float2 v = make_float2(gW2[rr][0], gW2[rr][1]);
-          if (!first_tile) {
-            const float2 o = *d2;
-            v.x += o.x;
-            v.y += o.y;
-          }
-          *d2 = v;
-        } else {
-#pragma unroll
-          for (int g = 0; g < TI / 4; ++g) {
-            float4 *d4 = reinterpret_cast<float4 *>(dst + 4 * ib + 4 * NIB * g);
-            float4 v = make_float4(gW2[rr][4 * g], gW2[rr][4 * g + 1], gW2[rr][4 * g + 2], gW2[rr][4 * g + 3]);
-            if (!first_tile) {
-              const float4 o = *d4;
+        for (int rr = 0; rr < TJ; ++rr) {
+          float *dst = rec + net_off_W2(H) + (TJ * jb + rr) * H;
+          if constexpr (TI == 2) {
+            float2 *d2 = reinterpret_cast<float2 *>(dst + TI * ib);
+            float2 v = make_float2(gW2[rr][0], gW2[rr][1]);
+            if (!store) {
+              const float2 o = *d2;
               v.x += o.x;
               v.y += o.y;
-              v.z += o.z;
-              v.w += o.w;
             }
-            *d4 = v;
+            *d2 = v;
+          } else {
+#pragma unroll
+            for (int g = 0; g < TI / 4; ++g) {
+              float4 *d4 = reinterpret_cast<float4 *>(dst + 4 * ib + 4 * NIB * g);
+              float4 v = make_float4(gW2[rr][4 * g], gW2[rr][4 * g + 1], gW2[rr][4 * g + 2], gW2[rr][4 * g + 3]);
+              if (!store) {
+                const float4 o = *d4;
+                v.x += o.x;
+                v.y += o.y;
+                v.z += o.z;
+                v.w += o.w;
+              }
+              *d4 = v;
+            }
           }
         }
       }
@@ -650,7 +667,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_ke
   // summed in warp order; the W2 part is already in place ----
   float *rec_s = sreg;
   const int nf = net_floats(H);
-  for (int e = threadIdx.x; e < nrec; e += NW * 32) rec_s[e] = 0.0f;
+  for (int e = threadIdx.x; e < nrec; e += NT) rec_s[e] = 0.0f;
   __syncthreads();
   for (int w = 0; w < NW; ++w) {
     if (warp == w) {
@@ -680,7 +697,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_ke
       const int k = blockIdx.x * SC + w * SPW + q;
       if (k < K && __ldg(a.w + k) != 0.0f) wmask |= 1u << w;
     }
-  for (int e = threadIdx.x; e < 2 * T; e += NW * 32) {
+  for (int e = threadIdx.x; e < 2 * T; e += NT) {
     float sum = 0.0f;
     for (int w = 0; w < NW; ++w)
       if (wmask >> w & 1u) sum += rec[nrec + (size_t)w * 2 * T + e];
@@ -688,7 +705,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm) adj_backward_ke
   }
   __syncthreads();
   const int w2_lo = net_off_W2(H), w2_hi = w2_lo + H * H;
-  for (int e = threadIdx.x; e < nrec; e += NW * 32)
+  for (int e = threadIdx.x; e < nrec; e += NT)
     if (e < w2_lo || e >= w2_hi) rec[e] = rec_s[e];
 }
 
@@ -729,20 +746,30 @@ __global__ void __launch_bounds__(256) adj_reduce_kernel(int n_cta, int nrec, in
 }
 
 template <int H, int ACT>
-cudaError_t launch_bwd(const AdjParams &a, int n_cta, size_t smem, cudaStream_t s) {
+cudaError_t launch_bwd(const AdjParams &a, const AdjPlan &pl, cudaStream_t s) {
   auto kern = adj_backward_kernel<H, ACT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_cta, kAdjWarps * 32, smem, s>>>(a);
+  kern<<<pl.n_cta, pl.nw * 32, pl.smem, s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int adj_num_ctas(int K) { return (K + kAdjSamples - 1) / kAdjSamples; }
-size_t adj_part_floats(int K, int H, int T_max) { return (size_t)adj_num_ctas(K) * adj_cta_floats(H, T_max); }
-size_t adj_smem_bytes(int H, int every, int T) {
-  return sizeof(float) * adj_smem_floats(H, every, adj_sub_len(H, every, T), T);
+AdjPlan adj_plan(int K, int H, int every, int T, int n_sm, size_t smem_max) {
+  AdjPlan pl;
+  pl.nw = adj_warps(K, n_sm > 0 ? n_sm : 1);
+  pl.n_cta = (K + kAdjSPW * pl.nw - 1) / (kAdjSPW * pl.nw);
+  pl.sub = adj_sub_len(H, every, T, pl.nw, smem_max);
+  pl.smem = sizeof(float) * adj_smem_floats(H, every, pl.sub, T, pl.nw);
+  return pl;
+}
+
+// Any plan for K <= K_cap: at most ceil(K_cap / 16) CTAs (8 warps or more each), and
+// n_cta * nw <= K_cap / 2 + 16 dL/dU rows.
+size_t adj_part_floats(int K_cap, int H, int T_max) {
+  const size_t n_cta = (K_cap + 2 * kAdjMinWarps - 1) / (2 * kAdjMinWarps);
+  return n_cta * adj_rec_floats(H, T_max) + ((size_t)K_cap / 2 + kAdjMaxWarps) * 2 * T_max;
 }
 
 cudaError_t adj_launch_scalars(int K, int T, int n_imp, const float *w, const float *S, const float *Uo,
@@ -751,21 +778,20 @@ cudaError_t adj_launch_scalars(int K, int T, int n_imp, const float *w, const fl
   return cudaGetLastError();
 }
 
-cudaError_t adj_launch_backward(const AdjParams &a_in, float *g_cost_w, float *g_U, float *g_net, cudaStream_t s) {
+cudaError_t adj_launch_backward(const AdjParams &a_in, const AdjPlan &pl, float *g_cost_w, float *g_U, float *g_net,
+                                cudaStream_t s) {
   AdjParams a = a_in;
   const int H = a.p.H, T = a.p.T;
-  const int n_cta = adj_num_ctas(a.p.K);
-  a.sub = adj_sub_len(H, a.every, T);
-  const size_t smem = sizeof(float) * adj_smem_floats(H, a.every, a.sub, T);
+  a.sub = pl.sub;
   cudaError_t e;
-  if (H == 32) e = a.p.activation == 1 ? launch_bwd<32, 1>(a, n_cta, smem, s) : launch_bwd<32, 0>(a, n_cta, smem, s);
-  else if (H == 64) e = a.p.activation == 1 ? launch_bwd<64, 1>(a, n_cta, smem, s) : launch_bwd<64, 0>(a, n_cta, smem, s);
+  if (H == 32) e = a.p.activation == 1 ? launch_bwd<32, 1>(a, pl, s) : launch_bwd<32, 0>(a, pl, s);
+  else if (H == 64) e = a.p.activation == 1 ? launch_bwd<64, 1>(a, pl, s) : launch_bwd<64, 0>(a, pl, s);
   else return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
   const int nf = net_floats(H);
   const int n_out = nf + 4 + 2 * T;
-  adj_reduce_kernel<<<(n_out + 31) / 32, 256, 0, s>>>(n_cta, (int)adj_cta_floats(H, T), nf, T, a.part, a.gUo, a.scal,
-                                                      g_net, g_cost_w, g_U);
+  adj_reduce_kernel<<<(n_out + 31) / 32, 256, 0, s>>>(pl.n_cta, (int)adj_cta_floats(H, T, pl.nw), nf, T, a.part,
+                                                      a.gUo, a.scal, g_net, g_cost_w, g_U);
   return cudaGetLastError();
 }
 

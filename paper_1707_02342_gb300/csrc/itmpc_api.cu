@@ -1265,7 +1265,7 @@ itmpc_status adj_check(itmpc_ctx *c, int32_t every) {
   if (c->cfg.dynamics != ITMPC_DYN_NETWORK) return fail(c, ITMPC_ERR_ARG, "the adjoint form needs the network model");
   if (every < 1 || every > ITMPC_ADJ_MAX_EVERY)
     return fail(c, ITMPC_ERR_ARG, "checkpoint interval %d outside [1, %d]", every, ITMPC_ADJ_MAX_EVERY);
-  if (adj_smem_bytes(c->H, every, c->cfg.T) > c->smem_optin)
+  if (adj_plan(c->cfg.K, c->H, every, c->cfg.T, c->sms, c->smem_optin).smem > c->smem_optin)
     return fail(c, ITMPC_ERR_ARG, "checkpoint interval %d with T=%d needs more shared memory than a CTA has", every,
                 c->cfg.T);
   return ITMPC_OK;
@@ -1308,7 +1308,8 @@ itmpc_status itmpc_iterate_bwd(itmpc_ctx *c, const float *U, uint64_t iter, int3
   CK(c, adj_launch_scalars(a.p.K, a.p.T, a.p.n_imp, weights, costs, U_out, gU_out, gJ, c->adj_scal, nullptr,
                            c->stream),
      "adjoint scalars launch");
-  CK(c, adj_launch_backward(a, g_cost_w, g_U, g_net, c->stream), "adjoint backward launch");
+  const AdjPlan pl = adj_plan(a.p.K, c->H, every, a.p.T, c->sms, c->smem_optin);
+  CK(c, adj_launch_backward(a, pl, g_cost_w, g_U, g_net, c->stream), "adjoint backward launch");
   return ITMPC_OK;
 }
 

@@ -217,18 +217,24 @@ struct AdjParams {
   IterParams p;        // dynamics, costs, noise counters, map, network, U
   const float *ckpt;   // K x (T / every + 1) x 7: x_t at t = 0, every, 2 every, ... (forward launch)
   int every;           // checkpoint interval, 1..32
-  int sub;             // sub-segment length (set by adj_launch_backward)
+  int sub;             // sub-segment length (from the launch plan)
   const float *w, *S;  // forward weights and costs (K)
   const float *gUo;    // dL/dU' (T x 2) or null
   const float *scal;   // [J, c0 = gU . U', sum of importance weights, gJ] (adj_launch_scalars)
   float *part;         // per-CTA gradient records
 };
-int adj_num_ctas(int K);
-size_t adj_part_floats(int K, int H, int T_max);
-size_t adj_smem_bytes(int H, int every, int T);
+// Launch shape of the adjoint backward: warps per CTA (one CTA per SM), CTAs, sub-segment
+// length and dynamic shared memory.
+struct AdjPlan {
+  int nw, n_cta, sub;
+  size_t smem;
+};
+AdjPlan adj_plan(int K, int H, int every, int T, int n_sm, size_t smem_max);
+size_t adj_part_floats(int K_cap, int H, int T_max);
 cudaError_t adj_launch_scalars(int K, int T, int n_imp, const float *w, const float *S, const float *Uo,
                                const float *gUo, const float *gJ, float *scal, float *J_out, cudaStream_t s);
-cudaError_t adj_launch_backward(const AdjParams &a, float *g_cost_w, float *g_U, float *g_net, cudaStream_t s);
+cudaError_t adj_launch_backward(const AdjParams &a, const AdjPlan &pl, float *g_cost_w, float *g_U, float *g_net,
+                                cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);
 cudaError_t launch_tanh(const float *x, float *y, int64_t n, cudaStream_t s);
 
