@@ -115,10 +115,13 @@ __device__ __forceinline__ void nbar_arrive(int id, int n) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// Activation of epilogue column i (of 32): 3 of every 8 columns take the FMA-pipe tanh,
+// the rest the MUFU tanh, so that both pipes work on a layer's 16 K activations at once.
+// (i is a constant once the epilogue's loop is unrolled.)
 template <int ACT>
-__device__ __forceinline__ float act_tc(float x) {
+__device__ __forceinline__ float act_tc(float x, int i) {
   if constexpr (ACT == 1) return x;
-  else return tanh_mufu(x);
+  else return (i & 7) < 3 ? tanh_poly(x) : tanh_mufu(x);
 }
 
 // Wait for a phase of an MMA / copy barrier; gives up after kWaitPolls polls
@@ -171,7 +174,7 @@ __device__ __forceinline__ void epilogue(uint32_t t_lane, uint32_t col0, uint32_
   for (int i = 0; i < 32; ++i) {
     float a = __uint_as_float(r[i]);
     if (SCALE) a *= scale;
-    v[i] = act_tc<ACT>(a);
+    v[i] = act_tc<ACT>(a, i);
   }
   if constexpr (OUT_E4M3) {
     const uint4 lo = make_uint4(

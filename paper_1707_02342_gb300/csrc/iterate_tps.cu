@@ -241,12 +241,16 @@ __global__ void __maxnreg__(96) tps_rollout_kernel(const __grid_constant__ TpsPa
 
 constexpr int kMergeThreads = 256;
 
+// CTA i < n_inst merges instance i.  With one instance and n_wcta > 0, CTAs n_inst ..
+// n_inst + n_wcta - 1 write its K weights (each from the records' rho and eta) and CTA 0
+// writes U', the stats and the status only.
 __global__ void __launch_bounds__(kMergeThreads) tps_merge_kernel(const __grid_constant__ TpsShared sh,
-                                                                  int stage_floats) {
+                                                                  int stage_floats, int n_wcta) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   if (blockIdx.x == 0 && threadIdx.x == 0) *sh.unit_counter = 0u;  // the rollout kernel has finished
-  const TpsInstance &I = sh.inst[blockIdx.x];
+  const bool wcta = (int)blockIdx.x >= sh.n_inst;
+  const TpsInstance &I = sh.inst[wcta ? 0 : blockIdx.x];
   IterParams q{};
   q.K = I.K;
   q.T = I.T;
@@ -259,6 +263,11 @@ __global__ void __launch_bounds__(kMergeThreads) tps_merge_kernel(const __grid_c
   q.costs = I.costs;
   q.stats = I.stats;
   q.status = sh.status;
+  if (wcta) {
+    merge_weights<kMergeThreads>(q, sh.partials + I.rec_off, I.n_units, (int)blockIdx.x - sh.n_inst, n_wcta);
+    return;
+  }
+  if (n_wcta > 0) q.weights = nullptr;
   if (threadIdx.x == 0) mbar_init(&mbar, 1);
   __syncthreads();
   uint32_t phase = 0;
@@ -319,7 +328,11 @@ cudaError_t tps_merge(const TpsShared &sh, cudaStream_t s) {
       return e;
     configured[dev] = smem;
   }
-  tps_merge_kernel<<<sh.n_inst, kMergeThreads, smem, s>>>(sh, (int)(smem / sizeof(float)));
+  // one instance: its weights are spread over CTAs of 2 x 256 samples each
+  const int n_wcta = sh.n_inst == 1 && sh.single_K > 0 && sh.single_weights
+                         ? std::min((sh.single_K + 2 * kMergeThreads - 1) / (2 * kMergeThreads), 148)
+                         : 0;
+  tps_merge_kernel<<<sh.n_inst + n_wcta, kMergeThreads, smem, s>>>(sh, (int)(smem / sizeof(float)), n_wcta);
   return cudaGetLastError();
 }
 

@@ -890,6 +890,10 @@ itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst,
   CK(c, cudaMemcpyAsync(c->units_d, c->units_h, sizeof(TpsUnit) * u, cudaMemcpyHostToDevice, c->stream), "copy");
   CK(c, cudaEventRecord(c->staged, c->stream), "event");
   TpsShared sh = batch_shared(c, c->inst_d, c->units_d, n, u);
+  if (n == 1) {
+    sh.single_K = c->inst_h[0].K;
+    sh.single_weights = c->inst_h[0].weights != nullptr;
+  }
   sh.states_out = states;
   sh.n_states = states ? n_states : 0;
   sh.states_every = states_every;

@@ -148,6 +148,9 @@ struct TpsShared {
   // (n_states x (T/e + 1) x 7: the adjoint form's checkpoints)
   float *states_out;
   int n_states, states_every;
+  // a batch of one instance: its K and whether it writes weights (the merge then spreads the
+  // weights over several CTAs); 0 otherwise
+  int single_K, single_weights;
 };
 
 // Network values in kernel parameter space (constant bank): FMA operands read
