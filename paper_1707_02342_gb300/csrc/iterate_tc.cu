@@ -76,6 +76,8 @@ constexpr int kBarH1 = 2;     // epilogue -> MMA warp: h1 stored                
 constexpr int kBarH2 = 3;     // epilogue -> MMA warp: h2 stored                       (512 + 32)
 constexpr int kBarState = 7;  // state warps -> cost warps: x(t) in shared memory      (128 + 128)
 constexpr int kBarNoise = 8;  // epilogue warps: a block of noise written              (512)
+constexpr int kBarLead = 9;   // warps 4-7 -> state warps: noise drawn ahead (one step later) (128 + 128)
+constexpr int kNoiseLead = 2; // steps of noise drawn before the loop when the horizon is resident
 
 // Operand image (bytes): every block K-major, no swizzle (itmpc_tcgen05.cuh).
 constexpr int kOffB1 = 0;       // 128 x 16 BF16: [W1 | W1 | b1_hi b1_lo 0 0]
@@ -397,9 +399,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         CostFetch cf{};
         float cc_prev = 0.f;
+        // Noise: when the whole horizon fits the block (Tc >= T), steps 0 .. kNoiseLead - 1 are drawn
+        // here and step t + kNoiseLead by warps 4-7 (one thread per sample) while layer 2 of step t
+        // runs; the state warps take step t's after a barrier with those warps' arrival at step t - 1.
+        // Otherwise blocks of Tc steps are drawn by all warps.
+        const bool lead = Tc >= T;
+        const int P = min(kNoiseLead, T);
         for (int t = 0; t < T; ++t) {
-          if (t % Tc == 0) {  // noise eps_{k, t .. t + Tc - 1} of the unit's samples
-            const int nst = min(Tc, T - t);
+          if (lead ? t == 0 : t % Tc == 0) {  // noise eps_{k, t .. t + nst - 1} of the unit's samples
+            const int nst = lead ? P : min(Tc, T - t);
             for (int it = tid; it < nst * kRows; it += kEpiThreads) {
               const int tt = it / kRows, s2 = it % kRows;
               eps_s[it] = tps_noise(sh, I.k_base + (uint32_t)(un.k0 + s2), (uint32_t)(t + tt), I.ctr2, I.ctr3);
@@ -407,6 +415,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             nbar_sync(kBarNoise, kEpiThreads);
           }
           if (state) {
+            if (lead && t > 0) nbar_sync(kBarLead, 256);
             if (t > 0) step_velocities();  // x_d(t)
             const float2 e = eps_s[(t % Tc) * kRows + s];
             const float u0 = U_s[2 * t], u1 = U_s[2 * t + 1];
@@ -436,6 +445,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tc_fence_after();
           epilogue<ACT, FP8, false>(t_lane, 0, kColH1, sub, 1.0f);
           nbar_arrive(kBarH1, kTcThreads);
+          if (lead && sub == 1) {  // noise of step t + P while layer 2 runs
+            if (t + P < T)
+              eps_s[(t + P) * kRows + s] = tps_noise(sh, I.k_base + (uint32_t)k, (uint32_t)(t + P), I.ctr2, I.ctr3);
+            if (t + 1 < T) nbar_arrive(kBarLead, 256);
+          }
           if (coster && t > 0) S.add(cost_finish(sh, cf, t) + cc_prev);  // running cost of x(t) (Alg. 1)
           // layer-2 epilogue: h2 = tanh(D2)
           tc_wait(&bars[2], ph, abort_v);
@@ -517,7 +531,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int t = item >> 2, qq = item & 3;
         CSum a0, a1;
         if (valid) {
-          for (int s2 = qq * 32; s2 < qq * 32 + 32; ++s2) {
+          // lane l starts at sample l of the quarter: the 32 lanes (8 steps x 4 quarters) read
+          // 32 different banks of the noise block instead of one
+          for (int i = 0; i < 32; ++i) {
+            const int s2 = qq * 32 + ((i + lane) & 31);
             const float es = e_s[s2];
             if (es != 0.0f) {
               const float2 ep = resident ? eps_s[t * kRows + s2]
