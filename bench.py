@@ -287,6 +287,8 @@ def measure_precision(params, flush, steps: int = 50, warmup: int = 10):
 
     from paper_1707_02342_gb300 import inputs, itmpc
 
+    import numpy as np
+
     K, T, H = 16384, 100, 128
     tmap = inputs.track_costmap(inputs.spline_centerline(1), 1024, 0.1, 2.5)
     layers = inputs.mlp_xavier((6, H, H, 4), seed=42)
@@ -306,6 +308,17 @@ def measure_precision(params, flush, steps: int = 50, warmup: int = 10):
         med, mean = _timed(lambda: ctl.iterate(x0_d, U_d, it, Uo, w, S), steps, warmup, flush)
         assert ctl.read_status() == itmpc.OK
         gpu[name] = tuple(t.double().cpu().numpy() for t in (S, w, Uo))
+        if name == "fp32":
+            # the U' error budget: the Monte-Carlo spread of U' over 16 other noise draws (iteration
+            # indices) of the same iteration, per element, from the FP32 form
+            draws = []
+            for j in range(16):
+                ctl.iterate(x0_d, U_d, it + 1 + j, Uo, w, S)
+                draws.append(Uo.double().cpu().numpy())
+            mc_std = np.std(np.array(draws), axis=0, ddof=1)
+            Uo.zero_()
+            ctl.iterate(x0_d, U_d, it, Uo, w, S)  # leave this draw's outputs as measured above
+            out["U_out_mc_std_l2"] = float(np.linalg.norm(mc_std))
         base_ms = base_ms or mean
         out[name] = {"ms_per_step": mean, "ms_median": med, "value": K * T / (mean * 1e-3), "unit": UNIT,
                      "speedup_vs_fp32": base_ms / mean, "algorithmic_tflops": flop / (mean * 1e-3) / 1e12,
@@ -388,7 +401,9 @@ def fp64_error_reports(forms, cases, params, cores):
         forms["precision"][name]["err_vs_fp64"] = {
             "cost_rel_median": float(np.median(rel)), "cost_rel_p99": float(np.quantile(rel, 0.99)),
             "cost_rel_max": float(rel.max()), "expected_cost_rel": abs(Jg - J64) / abs(J64),
-            "U_out_err_over_update": float(np.abs(Ug - U64).max() / np.abs(U64 - c["U"]).max())}
+            "U_out_err_over_update": float(np.abs(Ug - U64).max() / np.abs(U64 - c["U"]).max()),
+            # the budget: ||U'_form - U'_FP64||_2 <= the Monte-Carlo spread of U' (||std over draws||_2)
+            "U_out_err_over_mc_std": float(np.linalg.norm(Ug - U64) / forms["precision"]["U_out_mc_std_l2"])}
     c = cases["adjoint"]
     ref = oracle.iterate_vjp(problem(c), c["x0"], c["U"], c["it"], 1.0, c["gU"].astype(np.float64), S_use=c["S"])
     want = {"cost_w": ref["g_cost_w"], "U": ref["g_U"], "net": ref["g_net"]}

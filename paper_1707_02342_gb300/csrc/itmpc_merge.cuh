@@ -15,22 +15,19 @@ constexpr int kDevErrNonfinite = -3;  // ITMPC_ERR_NONFINITE
 constexpr int kDevErrTimeout = -4;    // ITMPC_ERR_TIMEOUT
 constexpr uint32_t kWaitPolls = 1u << 22;  // bounded mbarrier wait: ~0.3 s of 64 ns sleeps
 
-// Pass 1 + 2 of the merge (whole CTA): tot = {rho = min rho_c, eta, the importance part of
-// eta, the sum of squares, the finite count}, each record rescaled by exp(-(rho_c - rho)/lambda)
-// (written to scs when non-null).  Headers come from the staged copy rs when non-null, else from
-// global memory; either way the same values are summed in the same order, so every CTA that
-// calls it on the same records gets the same bits.
+// Pass 1 + 2 of merge_records (whole CTA), from the records in global memory: tot = {rho =
+// min rho_c, eta, the importance part of eta, the sum of squares, the finite count}.  The same
+// operations in the same order as merge_records' passes 1 + 2, so a CTA that calls it on the
+// same records gets the same bits.  tot[1..4] are written by thread 0 after the last barrier:
+// the caller synchronises before reading them.  (merge_records keeps its own copy of these
+// passes: folding them into a shared function changed the fused kernel's code generation.)
 template <int NT>
-__device__ void merge_scalars(const IterParams &p, const float *recs, const float *rs, int n, float *scs,
-                              float (*red)[8], float *tot) {
+__device__ void merge_scalars(const IterParams &p, const float *recs, int n, float (*red)[8], float *tot) {
   const int PL = partial_len(p.T);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NWARP = NT / 32;
-  auto header = [&](int c) -> float4 {
-    return rs ? *reinterpret_cast<const float4 *>(rs + (size_t)c * PL)
-              : __ldcg(reinterpret_cast<const float4 *>(recs + (size_t)c * PL));
-  };
-  auto nfin = [&](int c) -> float { return rs ? rs[(size_t)c * PL + 4] : __ldcg(recs + (size_t)c * PL + 4); };
+  auto header = [&](int c) -> float4 { return __ldcg(reinterpret_cast<const float4 *>(recs + (size_t)c * PL)); };
+  auto nfin = [&](int c) -> float { return __ldcg(recs + (size_t)c * PL + 4); };
   float m = INFINITY;
   for (int c = tid; c < n; c += NT) m = fminf(m, header(c).x);
   m = warp_min(m);
@@ -49,7 +46,6 @@ __device__ void merge_scalars(const IterParams &p, const float *recs, const floa
   for (int c = tid; c < n; c += NT) {
     const float4 h = header(c);
     const float sc = (ok && isfinite(h.x)) ? expf(-(h.x - rho) * p.inv_lambda) : 0.0f;
-    if (scs) scs[c] = sc;
     eta.add_prod(sc, h.y);
     eta_imp.add_prod(sc, h.z);
     sq.add_prod(__fmul_rn(sc, sc), h.w);
@@ -76,7 +72,6 @@ __device__ void merge_scalars(const IterParams &p, const float *recs, const floa
     }
     tot[1] = a.value(); tot[2] = b.value(); tot[3] = c.value(); tot[4] = d;
   }
-  __syncthreads();
 }
 
 // The weights w_k = exp(-(S_k - rho)/lambda) / eta of samples k = part * 8 NT + ... (every
@@ -86,7 +81,8 @@ template <int NT>
 __device__ void merge_weights(const IterParams &p, const float *recs, int n, int part, int nparts) {
   __shared__ float red[NT / 32][8];
   __shared__ float tot[5];
-  merge_scalars<NT>(p, recs, nullptr, n, nullptr, red, tot);
+  merge_scalars<NT>(p, recs, n, red, tot);
+  __syncthreads();  // tot[1] written by thread 0
   const float rho = tot[0];
   const bool ok = isfinite(rho);
   const float inv_eta = ok ? 1.0f / tot[1] : 0.0f;
@@ -152,9 +148,56 @@ __device__ bool merge_records(const IterParams &p, const float *recs, int n, flo
 
   // pass 1 + 2: rho and the scalar sums, from the staged records when they all fit
   if (whole && !copy_chunk(0, n)) return false;
-  merge_scalars<NT>(p, recs, whole ? rs : nullptr, n, whole ? scs : nullptr, red, tot);
+  auto header = [&](int c) -> float4 {
+    return whole ? *reinterpret_cast<const float4 *>(rs + (size_t)c * PL)
+                 : __ldcg(reinterpret_cast<const float4 *>(recs + (size_t)c * PL));
+  };
+  auto nfin = [&](int c) -> float { return whole ? rs[(size_t)c * PL + 4] : __ldcg(recs + (size_t)c * PL + 4); };
+  float m = INFINITY;
+  for (int c = tid; c < n; c += NT) m = fminf(m, header(c).x);
+  m = warp_min(m);
+  if (lane == 0) red[warp][0] = m;
+  __syncthreads();
+  if (tid == 0) {
+    float r = INFINITY;
+    for (int w = 0; w < NWARP; ++w) r = fminf(r, red[w][0]);
+    tot[0] = r;
+  }
+  __syncthreads();
   const float rho = tot[0];
   const bool ok = isfinite(rho);
+  CSum eta, eta_imp, sq;
+  float nf = 0.f;  // a count: exact in FP32 up to 2^24 samples
+  for (int c = tid; c < n; c += NT) {
+    const float4 h = header(c);
+    const float sc = (ok && isfinite(h.x)) ? expf(-(h.x - rho) * p.inv_lambda) : 0.0f;
+    if (whole) scs[c] = sc;
+    eta.add_prod(sc, h.y);
+    eta_imp.add_prod(sc, h.z);
+    sq.add_prod(__fmul_rn(sc, sc), h.w);
+    nf += nfin(c);
+  }
+  eta = csum_warp(eta);
+  eta_imp = csum_warp(eta_imp);
+  sq = csum_warp(sq);
+  nf = warp_sum(nf);
+  __syncthreads();  // tot[0] consumed, scs written
+  if (lane == 0) {
+    red[warp][0] = eta.s; red[warp][1] = eta.c; red[warp][2] = eta_imp.s; red[warp][3] = eta_imp.c;
+    red[warp][4] = sq.s; red[warp][5] = sq.c; red[warp][6] = nf;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    CSum a, b, c;
+    float d = 0.f;
+    for (int w = 0; w < NWARP; ++w) {
+      a.add(CSum{red[w][0], red[w][1]});
+      b.add(CSum{red[w][2], red[w][3]});
+      c.add(CSum{red[w][4], red[w][5]});
+      d += red[w][6];
+    }
+    tot[1] = a.value(); tot[2] = b.value(); tot[3] = c.value(); tot[4] = d;
+  }
 
   // pass 3: E sums.  Thread -> (output o, record slice r) when 2T <= NT.
   const int S = T2 <= NT ? NT / T2 : 1;

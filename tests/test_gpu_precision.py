@@ -9,8 +9,12 @@ What is exact and what is bounded:
     rounding, with B_f the a-priori bound of ``network_bound`` (rounding of
     weights and activations to BF16 / E4M3, hardware tanh error, FP32
     accumulation), evaluated on the GPU's own state;
-  * end to end (errors compound along T steps): reported, and held to the
-    envelopes stated in ``E2E`` -- measured values sit well inside them.
+  * end to end (errors compound along T steps): U' is held to the error
+    budget of the form -- ||U'_form - U'_FP64||_2 no larger than the
+    Monte-Carlo spread of U' itself (the 2-norm of its standard deviation over
+    16 other noise draws of the same iteration): reduced precision may not move
+    U' by more than resampling the noise does.  The cost errors are held to the
+    regression envelopes of ``E2E`` (measured values sit well inside them).
 """
 import numpy as np
 import pytest
@@ -173,10 +177,22 @@ def test_one_step_identity_and_gamma(precision):
     ctl.close()
 
 
-# End-to-end envelopes (small ellipse workload, K = 256, T = 50, no impulses):
-# median relative cost error, 99th percentile, and ||U'_gpu - U'_64||_inf relative
-# to ||U'_64 - U||_inf (the size of the update).
-E2E = {BF16: (2e-3, 2e-2, 0.25), FP8: (2e-2, 1e-1, 0.6)}
+# End-to-end regression envelopes of the costs (small ellipse workload, K = 256, T = 50, no
+# impulses): median relative cost error and its 99th percentile.
+E2E = {BF16: (2e-3, 2e-2), FP8: (2e-2, 1e-1)}
+
+
+def mc_spread(params, tmap, layers, x0, U, it, n=16):
+    """The Monte-Carlo spread of U': per-element standard deviation over n other noise draws
+    (iteration indices it + 1 .. it + n) of the FP32 iteration with the same inputs."""
+    ctl = G.controller(dict(params, precision=0), tmap, layers)
+    draws = []
+    for j in range(n):
+        Uo, _, _, st = G.run(ctl, x0, U, it + 1 + j)
+        assert st == 0
+        draws.append(Uo)
+    ctl.close()
+    return np.std(np.array(draws), axis=0, ddof=1)
 
 
 @pytest.mark.parametrize("precision", [BF16, FP8])
@@ -193,10 +209,13 @@ def test_end_to_end_error_vs_fp64(precision):
     assert rc == 0
     rel = np.abs(S - S_ref) / np.maximum(np.abs(S_ref), 1.0)
     upd = np.abs(Uo - U_ref).max() / np.abs(U_ref - U).max()
+    budget = np.linalg.norm(mc_spread(params, tmap, layers, x0, U, 0))
+    used = np.linalg.norm(Uo - U_ref) / budget
     print(f"precision {precision}: median rel cost err {np.median(rel):.3g}, p99 {np.quantile(rel, 0.99):.3g}, "
-          f"max {rel.max():.3g}; U' err / update {upd:.3g}")
-    med, p99, u_env = E2E[precision]
-    assert np.median(rel) <= med and np.quantile(rel, 0.99) <= p99 and upd <= u_env
+          f"max {rel.max():.3g}; U' err / update {upd:.3g}, / Monte-Carlo spread {used:.3g}")
+    med, p99 = E2E[precision]
+    assert np.median(rel) <= med and np.quantile(rel, 0.99) <= p99
+    assert used <= 1.0, used
     # the FP32 reduction itself is exact to 1e-5 given the GPU's costs
     check_stagewise(P, 0, U, Uo, w, S, params["sigma"])
     assert abs(w.sum() - 1) < 1e-5 and np.all(w >= 0)
