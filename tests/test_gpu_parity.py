@@ -303,7 +303,7 @@ def test_maximum_samples_sampled():
 
 def test_host_graph_path_follows_iteration_and_parameters():
     """itmpc_iterate_host without weights / costs replays one captured graph (upload, iteration,
-    download): each call's iteration index and the current parameters must be the ones used."""
+    download): each call's iteration index, inputs and the current parameters must be the ones used."""
     torch = G.torch_cuda()
     ctl, P, params, x0, U, Uo, w, S, st = small_case(K=200, T=30, it=11)
     x0f, Uf = x0.astype(np.float32), U.astype(np.float32)
@@ -311,6 +311,15 @@ def test_host_graph_path_follows_iteration_and_parameters():
         Uo_h = np.empty((30, 2), np.float32)
         assert ctl.iterate_host(x0f, Uf, it, Uo_h) == 0
         Uo_d, _, _, _ = G.run(ctl, x0, U, it)
+        np.testing.assert_allclose(Uo_h, Uo_d, rtol=0, atol=1e-6)
+    # new x0 and U on every call reach the iteration (the inputs travel through the pinned block)
+    for j, scale in enumerate((0.5, -1.0, 2.0)):
+        Uj = (U * scale).astype(np.float32)
+        x0j = x0.astype(np.float32).copy()
+        x0j[3] += 0.25 * j
+        Uo_h = np.empty((30, 2), np.float32)
+        assert ctl.iterate_host(x0j, Uj, 11, Uo_h) == 0
+        Uo_d, _, _, _ = G.run(ctl, x0j.astype(np.float64), Uj.astype(np.float64), 11)
         np.testing.assert_allclose(Uo_h, Uo_d, rtol=0, atol=1e-6)
     ctl.set_config(lam=7.0)  # a parameter change must reach the captured iteration
     Uo_h = np.empty((30, 2), np.float32)
