@@ -15,20 +15,20 @@
 //                        skips.  The cost cotangent of sample k is
 //                          Sbar_k = w_k (gJ (1 - (S_k - J)/lambda) - (a_k - c0)/lambda),
 //                          a_k = sum_t gU_t . v_{k,t}
-//                        (dw_k/dS_j = -(1/lambda) w_k (delta_kj - w_j)).  The horizon is
-//                        walked backwards in segments of `every` steps, each in sub-segments
-//                        short enough that a CTA's footprint lets 4 CTAs share an SM: the
-//                        segment is re-run forward from its checkpoint x_{t0} (written by
-//                        the forward launch), keeping its states and controls and the last
-//                        sub-segment's hidden-layer rows in shared memory; each earlier
-//                        sub-segment is re-run from its stored start state.  Each step is
-//                        then reversed: cost slope at x_t, the Euler kinematics, the network
-//                        (lane j owns neurons j, j+32, ...; one copy of W2 with padded rows
-//                        serves both orientations without bank conflicts), the clamp g and
-//                        the control-cost term.  The W2 gradient, an outer product summed
-//                        over samples and steps, is accumulated by the whole CTA as a small
-//                        GEMM over the sub-segment's rows (a2bar x h1) and added to the
-//                        CTA's record in place;
+//                        (dw_k/dS_j = -(1/lambda) w_k (delta_kj - w_j)).  One CTA per SM,
+//                        its warp count (8-16) spreading K over the SMs.  The horizon is
+//                        walked backwards in segments of `every` steps: the segment is re-run
+//                        forward from its checkpoint x_{t0} (written by the forward launch),
+//                        keeping its states, controls and hidden-layer rows in shared memory
+//                        (in sub-segments, each re-run from its stored start state, when the
+//                        rows do not fit).  Each step is then reversed: cost slope at x_t, the
+//                        Euler kinematics, the network (both matrix-vector products on 4 x 32
+//                        register tiles; one copy of W2 with padded rows serves both
+//                        orientations without bank conflicts), the clamp g and the
+//                        control-cost term.  The W2 gradient, an outer product summed over
+//                        samples and steps, is a small GEMM over the segment's rows
+//                        (a2bar x h1) by two 128-thread groups, added to the CTA's record
+//                        in place;
 //   adj_reduce_kernel    sums the per-CTA records in a fixed order (deterministic)
 //                        and adds the direct term dU'_t/du_t = sum_{importance} w_k.
 #include <cuda_runtime.h>
