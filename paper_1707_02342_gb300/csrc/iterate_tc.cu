@@ -19,7 +19,8 @@
 // Warp roles (one CTA per SM, persistent over 128-sample units):
 //   * 16 epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (its
 //     samples), columns 32 (w / 4) .. +31 of a layer's accumulator, applies
-//     the hardware tanh and stores the result as the next layer's A operand.
+//     tanh (the MUFU tanh for 5 of every 8 columns, an FMA-pipe polynomial for
+//     the other 3) and stores the result as the next layer's A operand.
 //     Warps 0-3 also own the sample state (Euler step of Sec. V-B, next
 //     layer-1 operand first, kinematics after); warps 8-11 add the running
 //     cost of Sec. V-C, fetching the costmap texels one layer ahead.
@@ -31,7 +32,9 @@
 //     (a relay through it costs about 15 % of the step).
 // Layers do not overlap: an MMA accumulating in tensor memory while the
 // epilogue warps read and write it slows the epilogue by more than the MMA
-// takes alone.  Noise is drawn in blocks of steps into shared memory.
+// takes alone.  Noise goes to shared memory: when the horizon fits, two steps
+// are drawn before the loop and warps 4-7 draw step t + 2 while layer 2 of step
+// t runs; otherwise blocks of steps are drawn by all epilogue warps.
 // Each unit leaves one partial record (Alg. 2 shifted by the unit's minimum),
 // merged per instance by tps_merge -- the same records as the FP32
 // thread-per-sample kernels, so single and batched iterations share it.
