@@ -161,6 +161,30 @@ def test_one_step_within_bound(precision, K, T):
 
 
 @pytest.mark.parametrize("precision", [BF16, FP8])
+def test_long_horizon_noise_in_blocks(precision):
+    """T = 300: the horizon's noise does not fit the shared-memory block (about 174 steps), so it
+    is drawn in blocks by all epilogue warps and the record's E sums draw it again from the
+    counter.  Every step of sampled trajectories within the bound, their costs, and U' and the
+    weights from the iteration's records (stage-wise) against the oracle."""
+    K, T = 130, 300
+    params, tmap, layers = G.small_workload(K=K, T=T, H=128)
+    ctl = tc_controller(params, tmap, layers, precision)
+    P = oracle_for(params, tmap, layers)
+    x0 = problems.x0_for(tmap, speed=2.5)
+    U = inputs.nominal_controls(T, seed=3)
+    n = 6
+    states, S_states = rollout(ctl, x0, U, 4, n)
+    g = controls(P, U, 4, n, T)
+    assert check_steps(P, layers, states, g, precision) < 1.0
+    check_costs_along(P, states, S_states, 4, U, g)
+    Uo, w, S, st = G.run(ctl, x0, U, 4)
+    assert st == 0
+    assert np.array_equal(S, S_states)  # the debug outputs do not change the rollout
+    check_stagewise(P, 4, U, Uo, w, S, params["sigma"])
+    ctl.close()
+
+
+@pytest.mark.parametrize("precision", [BF16, FP8])
 def test_one_step_identity_and_gamma(precision):
     """Affine network (no tanh), gamma term, alpha exploration and active clamps."""
     K, T = 64, 12
