@@ -159,6 +159,22 @@ def test_adjoint_full_size():
         ctl.close()
 
 
+def test_adjoint_sixteen_warps_per_cta():
+    """K = 8192: the backward launch's largest CTAs (16 warps, 32 samples; 256 CTAs, more than one
+    per SM over the launch) against the oracle's gradient."""
+    params = problems.params_small(K=8192, T=30, lam=20.0, gamma=0.05, alpha_explore=0.1)
+    tmap = problems.ellipse_map()
+    layers = problems.network(64, bias_scale=0.1)
+    x0 = problems.x0_for(tmap, 3.0)
+    U = inputs.nominal_controls(30, seed=4, scale=0.3)
+    gJ, gU = 0.5, np.random.default_rng(2).standard_normal((30, 2))
+    ctl = setup(params, tmap, layers)
+    gpu = gpu_fwd_bwd(ctl, x0, U, 6, 10, gJ, gU)
+    ref = oracle_ref(params, tmap, layers, x0, U, 6, gJ, gU, gpu["S"])
+    compare(gpu, ref, 64)
+    ctl.close()
+
+
 def test_adjoint_rejects_bad_arguments():
     torch = G.torch_cuda()
     from paper_1707_02342_gb300 import itmpc
