@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -159,15 +160,28 @@ def _dptr(t, n: int = 0, words: bool = False) -> int:
     return t.data_ptr()
 
 
+_HPTR_CACHE: dict = {}  # id(array) -> (weak reference, data address): a control loop passes the same buffers
+
+
 def _hptr(a, n: int = 0) -> int:
     """Address of a C-contiguous float32 numpy array of at least n elements, or None for None."""
     if a is None:
         return None
+    hit = _HPTR_CACHE.get(id(a))
+    if hit is not None and hit[0]() is a and a.dtype.char == "f" and a.size >= n:
+        return hit[1]  # an array's data address and contiguity are fixed for its lifetime
     if not isinstance(a, np.ndarray) or a.dtype.char != "f" or not a.flags.c_contiguous:
         raise ValueError("expected a C-contiguous float32 numpy array")
     if a.size < n:
         raise ValueError(f"array of {a.size} elements where at least {n} are needed")
-    return a.ctypes.data
+    addr = a.ctypes.data
+    try:
+        if len(_HPTR_CACHE) >= 64:
+            _HPTR_CACHE.clear()
+        _HPTR_CACHE[id(a)] = (weakref.ref(a), addr)
+    except TypeError:  # an ndarray subclass without weak references: no caching
+        pass
+    return addr
 
 
 def _stream_handle(stream) -> int:
