@@ -51,6 +51,19 @@ KERNEL_SOURCES = ["paper_1707_02342_gb300/csrc/iterate_fp32.cu", "paper_1707_023
 
 ADJ_PROFILE = os.path.join(ROOT, "profiles", "adj_backward_K4096_T100_H64.md")
 ADJ_SOURCES = ["paper_1707_02342_gb300/csrc/iterate_adj.cu"]
+# the forms' dominant kernels: (profile, the sources its hash covers)
+FORM_PROFILES = {
+    "batched": ("tps_rollout_batched256.md", ["iterate_tps.cu", "itmpc_units.cuh", "itmpc_sum.cuh"]),
+    "fp32_h128": ("wide_rollout_H128_K16384.md", ["iterate_wide.cu"]),
+    "bf16": ("tc_rollout_bf16_K16384.md", ["iterate_tc.cu", "itmpc_tcgen05.cuh"]),
+    "update_from_noise": ("wsum_partial4_K776192_T100.md", ["wsum.cu"]),
+}
+
+
+def form_traffic(name: str):
+    """DRAM bytes per launch of a form's dominant kernel from its committed ncu summary, or None."""
+    prof, srcs = FORM_PROFILES[name]
+    return profiled_traffic(os.path.join(ROOT, "profiles", prof), [f"paper_1707_02342_gb300/csrc/{f}" for f in srcs])
 
 
 def kernel_source_hash(sources=None) -> str:
@@ -777,6 +790,7 @@ def run_ours(args, rank, world, local_rank):
         bt["roofline"] = {"bound": "alu", "achieved": bt.pop("achieved_tflops"), "peak": peak_tflops,
                           "unit": "TFLOP/s"}
         bt["roofline"]["frac"] = bt["roofline"]["achieved"] / peak_tflops
+        bt["roofline"]["traffic"] = form_traffic("batched")
         line["forms"] = {"batched": bt}
         pr, pr_case = measure_precision(params, flush)
         bf_peak = pk.get("bf16_tflops", 1900.0)
@@ -784,9 +798,11 @@ def run_ours(args, rank, world, local_rank):
             pr[name]["roofline"] = {"bound": "tensor", "achieved": pr[name]["algorithmic_tflops"], "peak": pkv,
                                     "unit": "TFLOP/s", "frac": pr[name]["algorithmic_tflops"] / pkv,
                                     "peak_note": "measured bf16 burst" + (" x 2 (nominal fp8/bf16 ratio)"
-                                                                           if name == "fp8" else "")}
+                                                                           if name == "fp8" else ""),
+                                    "traffic": form_traffic("bf16") if name == "bf16" else None}
         pr["fp32"]["roofline"] = {"bound": "alu", "achieved": pr["fp32"]["algorithmic_tflops"], "peak": peak_tflops,
-                                  "unit": "TFLOP/s", "frac": pr["fp32"]["algorithmic_tflops"] / peak_tflops}
+                                  "unit": "TFLOP/s", "frac": pr["fp32"]["algorithmic_tflops"] / peak_tflops,
+                                  "traffic": form_traffic("fp32_h128")}
         line["forms"]["precision"] = pr
         line["forms"]["closed_loop"] = measure_closed_loop(tmap, layers, x0, U, params, flush)
         line["forms"]["cem"] = measure_cem(tmap, layers, x0, U, params, flush)
@@ -794,7 +810,8 @@ def run_ours(args, rank, world, local_rank):
         uh = measure_update_hbm(params, layers, flush)
         hbm = pk.get("hbm_gbs", 6800.0)
         uh["roofline"] = {"bound": "hbm", "achieved": uh["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                          "frac": uh["achieved_gbs"] / hbm, "peak_note": "measured copy bandwidth"}
+                          "frac": uh["achieved_gbs"] / hbm, "peak_note": "measured copy bandwidth",
+                          "traffic": form_traffic("update_from_noise")}
         line["forms"]["update_from_noise"] = uh
         ad, ad_case = measure_adjoint(params, flush)
         ad["bwd_roofline"]["peak"] = peak_tflops
