@@ -56,6 +56,7 @@ FORM_PROFILES = {
     "batched": ("tps_rollout_batched256.md", ["iterate_tps.cu", "itmpc_units.cuh", "itmpc_sum.cuh"]),
     "fp32_h128": ("wide_rollout_H128_K16384.md", ["iterate_wide.cu"]),
     "bf16": ("tc_rollout_bf16_K16384.md", ["iterate_tc.cu", "itmpc_tcgen05.cuh"]),
+    "fp8": ("tc_rollout_bf16_K16384.md", ["iterate_tc.cu", "itmpc_tcgen05.cuh"]),
     "update_from_noise": ("wsum_partial4_K776192_T100.md", ["wsum.cu"]),
 }
 
@@ -63,7 +64,9 @@ FORM_PROFILES = {
 def form_traffic(name: str):
     """DRAM bytes per launch of a form's dominant kernel from its committed ncu summary, or None."""
     prof, srcs = FORM_PROFILES[name]
-    return profiled_traffic(os.path.join(ROOT, "profiles", prof), [f"paper_1707_02342_gb300/csrc/{f}" for f in srcs])
+    key = "traffic_bytes_per_launch_fp8" if name == "fp8" else "traffic_bytes_per_launch"
+    return profiled_traffic(os.path.join(ROOT, "profiles", prof), [f"paper_1707_02342_gb300/csrc/{f}" for f in srcs],
+                            key)
 
 
 def kernel_source_hash(sources=None) -> str:
@@ -73,13 +76,13 @@ def kernel_source_hash(sources=None) -> str:
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(profile=PROFILE, sources=None):
+def profiled_traffic(profile=PROFILE, sources=None, key="traffic_bytes_per_launch"):
     """DRAM bytes per launch from a committed ncu summary, if it matches the current kernel source."""
     if not os.path.exists(profile):
         return None
     text = open(profile).read()
     m_src = re.search(r"kernel_source_sha1[^:]*:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_b = re.search(key + r":\s*([0-9.eE+]+)", text)
     if not m_src or not m_b or m_src.group(1) != kernel_source_hash(sources):
         return None
     return float(m_b.group(1))
@@ -799,7 +802,7 @@ def run_ours(args, rank, world, local_rank):
                                     "unit": "TFLOP/s", "frac": pr[name]["algorithmic_tflops"] / pkv,
                                     "peak_note": "measured bf16 burst" + (" x 2 (nominal fp8/bf16 ratio)"
                                                                            if name == "fp8" else ""),
-                                    "traffic": form_traffic("bf16") if name == "bf16" else None}
+                                    "traffic": form_traffic(name)}
         pr["fp32"]["roofline"] = {"bound": "alu", "achieved": pr["fp32"]["algorithmic_tflops"], "peak": peak_tflops,
                                   "unit": "TFLOP/s", "frac": pr["fp32"]["algorithmic_tflops"] / peak_tflops,
                                   "traffic": form_traffic("fp32_h128")}
