@@ -326,8 +326,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       __syncthreads();
       const int u = unit_s;
       if (u >= sh.n_units) break;
-      const TpsUnit un = sh.units[u];
-      const TpsInstance &I = sh.inst[un.inst];
+      const TpsUnit un = sh.inline_inst ? TpsUnit{0, u * kRows, u, 0} : sh.units[u];
+      const TpsInstance &I = sh.inline_inst ? sh.inst0 : sh.inst[un.inst];
       const int K = I.K, T = I.T;
       for (int i = tid; i < 2 * T; i += kTcThreads) U_s[i] = __ldg(I.U + i);
       __syncthreads();

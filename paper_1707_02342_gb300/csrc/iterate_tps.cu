@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kMergeThreads) tps_merge_kernel(const __grid_c
   __shared__ __align__(8) uint64_t mbar;
   if (blockIdx.x == 0 && threadIdx.x == 0) *sh.unit_counter = 0u;  // the rollout kernel has finished
   const bool wcta = (int)blockIdx.x >= sh.n_inst;
-  const TpsInstance &I = sh.inst[wcta ? 0 : blockIdx.x];
+  const TpsInstance &I = sh.inline_inst ? sh.inst0 : sh.inst[wcta ? 0 : blockIdx.x];
   IterParams q{};
   q.K = I.K;
   q.T = I.T;

@@ -886,10 +886,19 @@ itmpc_status run_batch_tile(itmpc_ctx *c, int32_t n, const itmpc_instance *inst,
     c->inst_h[0].rec_out = shard->rec_out;
     c->inst_h[0].weights = nullptr;
   }
-  CK(c, cudaMemcpyAsync(c->inst_d, c->inst_h, sizeof(TpsInstance) * n, cudaMemcpyHostToDevice, c->stream), "copy");
-  CK(c, cudaMemcpyAsync(c->units_d, c->units_h, sizeof(TpsUnit) * u, cudaMemcpyHostToDevice, c->stream), "copy");
-  CK(c, cudaEventRecord(c->staged, c->stream), "event");
+  // one instance on the tensor-core kernels: it travels in the launch's parameters and its
+  // units follow from K (no table upload); otherwise the tables are copied to the device
+  const bool inline1 = n == 1 && c->cfg.precision != ITMPC_FP32;
+  if (!inline1) {
+    CK(c, cudaMemcpyAsync(c->inst_d, c->inst_h, sizeof(TpsInstance) * n, cudaMemcpyHostToDevice, c->stream), "copy");
+    CK(c, cudaMemcpyAsync(c->units_d, c->units_h, sizeof(TpsUnit) * u, cudaMemcpyHostToDevice, c->stream), "copy");
+    CK(c, cudaEventRecord(c->staged, c->stream), "event");
+  }
   TpsShared sh = batch_shared(c, c->inst_d, c->units_d, n, u);
+  if (inline1) {
+    sh.inline_inst = 1;
+    sh.inst0 = c->inst_h[0];
+  }
   if (n == 1) {
     sh.single_K = c->inst_h[0].K;
     sh.single_weights = c->inst_h[0].weights != nullptr;

@@ -151,6 +151,10 @@ struct TpsShared {
   // a batch of one instance: its K and whether it writes weights (the merge then spreads the
   // weights over several CTAs); 0 otherwise
   int single_K, single_weights;
+  // inline_inst = 1: the one instance is inst0 (in the launch's parameters, no table upload) and
+  // unit u is its samples 128 u .. 128 u + 127 (the tensor-core kernels and their merge)
+  int inline_inst;
+  TpsInstance inst0;
 };
 
 // Network values in kernel parameter space (constant bank): FMA operands read
