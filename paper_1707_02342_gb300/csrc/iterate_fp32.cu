@@ -7,9 +7,9 @@
 //   phase 2  dynamics   the serial recurrence x_d(t+1) = x_d(t) + dt f(x_d(t), g(v_t))
 //                       of Sec. V-B.  Only x_d feeds the network, so this is the one
 //                       serial chain.  H = 32: a half-warp per sample, two neurons per
-//                       lane, the W2 and M rows in registers as packed pairs for
-//                       fma.rn.f32x2, the layer-1 pre-activation carried from step to
-//                       step (recurrence_half32).  H = 64, 128: lane j owns neurons j,
+//                       lane, the W2 rows in registers as packed pairs for
+//                       fma.rn.f32x2, layer 3 reduced across the half-warp with a
+//                       register butterfly (recurrence_half32).  H = 64, 128: lane j owns neurons j,
 //                       j + 32, ...; layer 1 in registers, h1 broadcast through a
 //                       per-warp shared row, W2 transposed in shared memory, the 4
 //                       outputs of layer 3 reduced across the warp with a register
@@ -51,7 +51,7 @@ __host__ __device__ inline SmemLayout fp32_layout(int T, int H, int nw, int spw)
   L.traj = off; off += align16(sizeof(float4) * (size_t)scta * (T + 1));
   L.pos = off;  off += align16(sizeof(float4) * (size_t)scta * T);
   L.W2T = off;  off += (H > 32) ? align16(sizeof(float) * (size_t)H * H) : 0;
-  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * (spw == 2 ? 2 * 32 * 36 + 16 + 80 : 2 * H));
+  L.hbuf = off; off += align16(sizeof(float) * (size_t)nw * (spw == 2 ? 96 : 2 * H));
   L.W3b3 = off; off += align16(sizeof(float) * (4 * H + 4));
   L.S = off;    off += align16(sizeof(float) * scta);
   L.e = off;    off += align16(sizeof(float) * scta);
@@ -59,92 +59,67 @@ __host__ __device__ inline SmemLayout fp32_layout(int T, int H, int nw, int spw)
   return L;
 }
 
-// Phase 2 for H = 32.  Layers 3 and 1 are affine, so with M = dt W1x W3
-// (32 x 32), beta = dt W1x b3 and the Euler step x_d(t+1) = x_d(t) + dt d(t),
-// d(t) = W3 h2(t) + b3, the input-layer pre-activation obeys
-//   a1(t+1) = a1(t) + M h2(t) + beta + W1u (g(t+1) - g(t))
-// (W1x, W1u: the state and control columns of W1; g the clamped control).
-// The serial chain of a step is then two 32-term dot products with a tanh
-// each, and x_d is not needed inside the loop: a1 is carried as a compensated
-// (Kahan) sum, h2 rows go to a 32-step ring in shared memory (which is also the
-// broadcast row of the M h2 product), and every 32 steps the output layer
-// d = W3 h2 + b3 is applied to the whole block with lane = time step.  d(t) is
-// left in traj[t + 1]; phase 3 turns it into x_d by prefix sums.
-constexpr int kRingStride = 36;  // padded row: lanes reading rows t, t+1, .. hit distinct banks
+// Phase 2 for H = 32: two samples per warp.  Half-warp h = lane / 16 owns sample
+// s_first + h and lane j = lane % 16 owns neurons j and j + 16 of it, so every
+// activation broadcast feeds two FMAs per lane (half the shared-memory -> register
+// traffic per sample-step of a one-neuron-per-lane layout).  The halves' h1 rows sit
+// 48 floats apart, so their stores and loads never share a bank.
+constexpr int kHrowHalf = 48;
+constexpr int kHalfWarpBuf = 2 * kHrowHalf;
 
-// Two samples per warp: half-warp h = lane / 16 owns sample s_first + h and
-// lane j = lane % 16 owns neurons j and j + 16 of it, so every activation
-// broadcast feeds two FMAs per lane (half the shared-memory -> register traffic
-// per sample-step of a one-neuron-per-lane layout).
-// Per-warp buffer: ring 0 at 0, ring 1 at 32 rows + 16 floats (the other 16
-// banks), then the two h1 rows at +0 and +48 floats: the halves' stores and
-// loads never share a bank.
-constexpr int kRing1 = 32 * kRingStride + 16;
-constexpr int kHrows = kRing1 + 32 * kRingStride;
-constexpr int kHalfWarpBuf = kHrows + 80;
-
+// Each step forms a1 = b1 + W1x x_d + W1u g from the carried state (the Sec. V-B
+// network's first layer), one 32-term dot W2 h1 per neuron from the broadcast h1 row, and
+// layer 3 by a register butterfly over the half-warp; x_d(t + 1) = x_d(t) + dt d(t)
+// is left in traj[t + 1].
 template <int ACT>
 __device__ __forceinline__ void recurrence_half32(const IterParams &p, const float *net, float *wbuf,
-                                                  const float *W3b3_s, const float2 *gv_s, float4 *traj_s,
-                                                  int s_first, int T, int lane) {
+                                                         const float *W3b3_s, const float2 *gv_s, float4 *traj_s,
+                                                         int s_first, int T, int lane) {
   constexpr int H = 32;
   const int h = lane >> 4, j = lane & 15;
   const int s = s_first + h;
-  float *ring = wbuf + h * kRing1;
-  float *hB = wbuf + kHrows + h * 48;
+  float *hB = wbuf + h * kHrowHalf;
   const float4 *hB4 = reinterpret_cast<const float4 *>(hB);
   const float2 *gvr = gv_s + (size_t)s * T;
   float4 *traj = traj_s + (size_t)s * (T + 1);
   const float dt = p.dt;
   const int ja = j, jb = j + 16;
-  float w1xa[4], w1xb[4], b3[4];
+  float w1a[6], w1b[6], w3a[4], w3b[4], b3[4];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    w1a[q] = __ldg(net + net_off_W1(H) + ja * 6 + q);
+    w1b[q] = __ldg(net + net_off_W1(H) + jb * 6 + q);
+  }
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
-    w1xa[o] = __ldg(net + net_off_W1(H) + ja * 6 + o);
-    w1xb[o] = __ldg(net + net_off_W1(H) + jb * 6 + o);
+    w3a[o] = W3b3_s[o * H + ja];
+    w3b[o] = W3b3_s[o * H + jb];
     b3[o] = W3b3_s[4 * H + o];
   }
-  const float w1ua0 = __ldg(net + net_off_W1(H) + ja * 6 + 4), w1ua1 = __ldg(net + net_off_W1(H) + ja * 6 + 5);
-  const float w1ub0 = __ldg(net + net_off_W1(H) + jb * 6 + 4), w1ub1 = __ldg(net + net_off_W1(H) + jb * 6 + 5);
+  const float b1a = __ldg(net + net_off_b1(H) + ja), b1b = __ldg(net + net_off_b1(H) + jb);
   const float b2a = __ldg(net + net_off_b2(H) + ja), b2b = __ldg(net + net_off_b2(H) + jb);
-  float beta_a = 0.f, beta_b = 0.f;
-#pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    beta_a = fmaf(dt * w1xa[o], b3[o], beta_a);
-    beta_b = fmaf(dt * w1xb[o], b3[o], beta_b);
-  }
-  // the lane's rows of M and W2 as packed pairs (w[i], w[i + 1]): one fma.rn.f32x2 multiplies
-  // two terms of a dot product, in the same chains (i mod 4) and order as four scalar FMAs
-  unsigned long long ma[H / 2], mb[H / 2], w2a[H / 2], w2b[H / 2];
+  // the lane's W2 rows as packed pairs (w[i], w[i + 1]) for fma.rn.f32x2
+  unsigned long long w2a[H / 2], w2b[H / 2];
 #pragma unroll
   for (int i = 0; i < H; i += 2) {
-    float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
-#pragma unroll
-    for (int o = 0; o < 4; ++o) {
-      a0 = fmaf(w1xa[o], W3b3_s[o * H + i], a0);
-      b0 = fmaf(w1xb[o], W3b3_s[o * H + i], b0);
-      a1 = fmaf(w1xa[o], W3b3_s[o * H + i + 1], a1);
-      b1 = fmaf(w1xb[o], W3b3_s[o * H + i + 1], b1);
-    }
-    ma[i / 2] = f2pack(dt * a0, dt * a1);
-    mb[i / 2] = f2pack(dt * b0, dt * b1);
     w2a[i / 2] = f2pack(__ldg(net + net_off_W2(H) + ja * H + i), __ldg(net + net_off_W2(H) + ja * H + i + 1));
     w2b[i / 2] = f2pack(__ldg(net + net_off_W2(H) + jb * H + i), __ldg(net + net_off_W2(H) + jb * H + i + 1));
   }
-  // a1(0) = b1 + W1x x_d(0) + W1u g(0)
-  float2 g = gvr[0];
-  float a1a = __ldg(net + net_off_b1(H) + ja), a1b = __ldg(net + net_off_b1(H) + jb);
-#pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    const float xo = __ldg(p.x0 + 3 + o);
-    a1a = fmaf(w1xa[o], xo, a1a);
-    a1b = fmaf(w1xb[o], xo, a1b);
-  }
-  a1a = fmaf(w1ua0, g.x, fmaf(w1ua1, g.y, a1a));
-  a1b = fmaf(w1ub0, g.x, fmaf(w1ub1, g.y, a1b));
-  float ca_c = 0.f, cb_c = 0.f;  // Kahan compensations
+  float xd0 = __ldg(p.x0 + 3), xd1 = __ldg(p.x0 + 4), xd2 = __ldg(p.x0 + 5), xd3 = __ldg(p.x0 + 6);
+  const int bit3 = (j >> 3) & 1, bit2 = (j >> 2) & 1;
+  const int src = lane & 16;  // first lane of this half-warp
+  float2 g_next = gvr[0];
   for (int t = 0; t < T; ++t) {
-    const float2 gn = gvr[t + 1 < T ? t + 1 : t];
+    const float2 g = g_next;
+    g_next = gvr[t + 1 < T ? t + 1 : t];  // next step's control, off the chain
+    float a1a = b1a, a1b = b1b;
+    a1a = fmaf(w1a[0], xd0, a1a); a1b = fmaf(w1b[0], xd0, a1b);
+    a1a = fmaf(w1a[1], xd1, a1a); a1b = fmaf(w1b[1], xd1, a1b);
+    a1a = fmaf(w1a[2], xd2, a1a); a1b = fmaf(w1b[2], xd2, a1b);
+    a1a = fmaf(w1a[3], xd3, a1a); a1b = fmaf(w1b[3], xd3, a1b);
+    a1a = fmaf(w1a[4], g.x, a1a); a1b = fmaf(w1b[4], g.x, a1b);
+    a1a = fmaf(w1a[5], g.y, a1a); a1b = fmaf(w1b[5], g.y, a1b);
+    __syncwarp();  // every lane of the half has read the previous h1 row
     hB[ja] = activation<ACT>(a1a);
     hB[jb] = activation<ACT>(a1b);
     __syncwarp();
@@ -158,62 +133,27 @@ __device__ __forceinline__ void recurrence_half32(const IterParams &p, const flo
       pb01 = ffma2(w2b[kk / 2], hv.x, pb01);
       pb23 = ffma2(w2b[kk / 2 + 1], hv.y, pb23);
     }
-    float *row = ring + (t & 31) * kRingStride;
     const float2 qa01 = f2unpack(pa01), qa23 = f2unpack(pa23), qb01 = f2unpack(pb01), qb23 = f2unpack(pb23);
-    row[ja] = activation<ACT>((qa01.x + qa01.y) + (qa23.x + qa23.y));
-    row[jb] = activation<ACT>((qb01.x + qb01.y) + (qb23.x + qb23.y));
-    __syncwarp();
-    if (t + 1 < T) {
-      const ulonglong2 *row2 = reinterpret_cast<const ulonglong2 *>(row);
-      const float dgx = gn.x - g.x, dgy = gn.y - g.y;
-      unsigned long long ea01 = f2pack(fmaf(w1ua0, dgx, beta_a), w1ua1 * dgy), ea23 = 0ull;
-      unsigned long long eb01 = f2pack(fmaf(w1ub0, dgx, beta_b), w1ub1 * dgy), eb23 = 0ull;
-#pragma unroll
-      for (int kk = 0; kk < H; kk += 4) {
-        const ulonglong2 hv = row2[kk >> 2];
-        ea01 = ffma2(ma[kk / 2], hv.x, ea01);
-        ea23 = ffma2(ma[kk / 2 + 1], hv.y, ea23);
-        eb01 = ffma2(mb[kk / 2], hv.x, eb01);
-        eb23 = ffma2(mb[kk / 2 + 1], hv.y, eb23);
-      }
-      const float2 fa01 = f2unpack(ea01), fa23 = f2unpack(ea23), fb01 = f2unpack(eb01), fb23 = f2unpack(eb23);
-      const float ea0 = fa01.x, ea1 = fa01.y, ea2 = fa23.x, ea3 = fa23.y;
-      const float eb0 = fb01.x, eb1 = fb01.y, eb2 = fb23.x, eb3 = fb23.y;
-      const float ya = ((ea0 + ea1) + (ea2 + ea3)) - ca_c;
-      const float sa = a1a + ya;
-      ca_c = (sa - a1a) - ya;
-      a1a = sa;
-      const float yb = ((eb0 + eb1) + (eb2 + eb3)) - cb_c;
-      const float sb = a1b + yb;
-      cb_c = (sb - a1b) - yb;
-      a1b = sb;
-      g = gn;
-    }
-    if ((t & 31) == 31 || t + 1 == T) {
-      const int t0 = t & ~31;
-#pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int r = j + 16 * rr;
-        if (t0 + r <= t) {
-          const float4 *r4 = reinterpret_cast<const float4 *>(ring + r * kRingStride);
-          float d0 = b3[0], d1 = b3[1], d2 = b3[2], d3 = b3[3];
-#pragma unroll
-          for (int kk = 0; kk < H; kk += 4) {
-            const float4 hv = r4[kk >> 2];
-            const float4 q0 = *reinterpret_cast<const float4 *>(W3b3_s + 0 * H + kk);
-            const float4 q1 = *reinterpret_cast<const float4 *>(W3b3_s + 1 * H + kk);
-            const float4 q2 = *reinterpret_cast<const float4 *>(W3b3_s + 2 * H + kk);
-            const float4 q3 = *reinterpret_cast<const float4 *>(W3b3_s + 3 * H + kk);
-            d0 = fmaf(q0.x, hv.x, fmaf(q0.y, hv.y, fmaf(q0.z, hv.z, fmaf(q0.w, hv.w, d0))));
-            d1 = fmaf(q1.x, hv.x, fmaf(q1.y, hv.y, fmaf(q1.z, hv.z, fmaf(q1.w, hv.w, d1))));
-            d2 = fmaf(q2.x, hv.x, fmaf(q2.y, hv.y, fmaf(q2.z, hv.z, fmaf(q2.w, hv.w, d2))));
-            d3 = fmaf(q3.x, hv.x, fmaf(q3.y, hv.y, fmaf(q3.z, hv.z, fmaf(q3.w, hv.w, d3))));
-          }
-          traj[t0 + r + 1] = make_float4(d0, d1, d2, d3);
-        }
-      }
-      __syncwarp();  // the ring is reused by the next block
-    }
+    const float h2a = activation<ACT>((qa01.x + qa01.y) + (qa23.x + qa23.y));
+    const float h2b = activation<ACT>((qb01.x + qb01.y) + (qb23.x + qb23.y));
+    // layer 3: this lane's two neurons' terms, reduced over the half-warp (reduce-scatter:
+    // lane j ends with output 2 bit3 + bit2), then gathered from lanes 0, 4, 8, 12
+    const float p0 = fmaf(w3a[0], h2a, w3b[0] * h2b), p1 = fmaf(w3a[1], h2a, w3b[1] * h2b);
+    const float p2 = fmaf(w3a[2], h2a, w3b[2] * h2b), p3 = fmaf(w3a[3], h2a, w3b[3] * h2b);
+    const float q0 = (bit3 ? p2 : p0) + __shfl_xor_sync(FULL_MASK, bit3 ? p0 : p2, 8);
+    const float q1 = (bit3 ? p3 : p1) + __shfl_xor_sync(FULL_MASK, bit3 ? p1 : p3, 8);
+    float v = (bit2 ? q1 : q0) + __shfl_xor_sync(FULL_MASK, bit2 ? q0 : q1, 4);
+    v += __shfl_xor_sync(FULL_MASK, v, 2);
+    v += __shfl_xor_sync(FULL_MASK, v, 1);
+    const float d0 = __shfl_sync(FULL_MASK, v, src + 0) + b3[0];
+    const float d1 = __shfl_sync(FULL_MASK, v, src + 4) + b3[1];
+    const float d2 = __shfl_sync(FULL_MASK, v, src + 8) + b3[2];
+    const float d3 = __shfl_sync(FULL_MASK, v, src + 12) + b3[3];
+    xd0 = fmaf(d0, dt, xd0);
+    xd1 = fmaf(d1, dt, xd1);
+    xd2 = fmaf(d2, dt, xd2);
+    xd3 = fmaf(d3, dt, xd3);
+    if (j == 0) traj[t + 1] = make_float4(xd0, xd1, xd2, xd3);
   }
 }
 
@@ -400,43 +340,21 @@ __global__ void __launch_bounds__(NW * 32, 1) iterate_fp32_kernel(const __grid_c
   // ---- phase 3: kinematics and running costs, this warp's samples side by side ----
   {
     float th_c[SPW], px_c[SPW], py_c[SPW];
-    float4 xd_c[SPW];
 #pragma unroll
     for (int q = 0; q < SPW; ++q) {
       th_c[q] = x0th;
       px_c[q] = x0px;
       py_c[q] = x0py;
-      xd_c[q] = traj_s[(warp * SPW + q) * (T + 1)];
     }
-    // 3a: x_d (H = 32: from the stored d), heading and position by prefix sums over t
+    // 3a: heading and position by prefix sums over t of the stored x_d
     for (int base = 0; base < T; base += 32) {
       const int tau = base + lane;
       const bool valid = tau < T;
 #pragma unroll
       for (int q = 0; q < SPW; ++q) {
         const int s = warp * SPW + q;
-        float4 *traj = traj_s + s * (T + 1);
-        float4 xo;
-        if constexpr (H == 32) {
-          // traj[tau + 1] holds d(tau): x_d(tau + 1) = x_d(0) + dt sum_{s <= tau} d(s)
-          float4 dd = traj[valid ? tau + 1 : T];
-          if (!valid) dd = make_float4(0.f, 0.f, 0.f, 0.f);
-          const float i0 = warp_incl_scan(dt * dd.x, lane), i1 = warp_incl_scan(dt * dd.y, lane);
-          const float i2 = warp_incl_scan(dt * dd.z, lane), i3 = warp_incl_scan(dt * dd.w, lane);
-          // every lane takes part in each shuffle; lane 0 then drops the value
-          float e0 = __shfl_up_sync(FULL_MASK, i0, 1), e1 = __shfl_up_sync(FULL_MASK, i1, 1);
-          float e2 = __shfl_up_sync(FULL_MASK, i2, 1), e3 = __shfl_up_sync(FULL_MASK, i3, 1);
-          if (lane == 0) e0 = e1 = e2 = e3 = 0.f;
-          xo = make_float4(xd_c[q].x + e0, xd_c[q].y + e1, xd_c[q].z + e2, xd_c[q].w + e3);
-          __syncwarp();  // every lane has read its d before any x_d overwrites it
-          if (valid) traj[tau + 1] = make_float4(xd_c[q].x + i0, xd_c[q].y + i1, xd_c[q].z + i2, xd_c[q].w + i3);
-          xd_c[q].x += __shfl_sync(FULL_MASK, i0, 31);
-          xd_c[q].y += __shfl_sync(FULL_MASK, i1, 31);
-          xd_c[q].z += __shfl_sync(FULL_MASK, i2, 31);
-          xd_c[q].w += __shfl_sync(FULL_MASK, i3, 31);
-        } else {
-          xo = traj[valid ? tau : T - 1];
-        }
+        const float4 *traj = traj_s + s * (T + 1);
+        float4 xo = traj[valid ? tau : T - 1];  // x_d(tau)
         if (!valid) xo = make_float4(0.f, 0.f, 0.f, 0.f);
         const float dth = dt * xo.w;
         const float incl_th = warp_incl_scan(dth, lane);
