@@ -4,6 +4,7 @@
   interpolation weights) and clamps to the edge outside the map;
 * the track term is capped, speed and slip terms have their closed forms
   (slip angle against math.atan), impulses switch exactly at the thresholds;
+* the rollout's threshold margin is the smallest over its steps;
 * over a whole rollout, the time-decayed impulse sums to a geometric series
   over t = 1..T and a planar map along a straight line gives an arithmetic
   series, which pins "cost after the step".
@@ -142,3 +143,19 @@ def test_cost_applied_after_each_step():
     S, _, _, _ = oracle.rollout_sample(P, x0, np.zeros((T, 2)), 0, 0)
     ref = T * (a + bx * x0[0] + cy * x0[1]) + bx * dt * vx * T * (T + 1) / 2
     assert S == pytest.approx(ref, abs=1e-4)
+
+
+def test_rollout_margin_is_smallest_over_the_steps():
+    # the rollout's threshold margin is the smallest over t = 1..T of min(|h - track_thresh|,
+    # ||zeta| - slip_thresh|): on the planar map along a straight line h(p_t) is linear in t, so the
+    # margin comes from the step whose h is closest to the threshold (zeta = 0 keeps the slip
+    # margin at 0.75, above every track margin here)
+    tmap, (a, bx, cy) = planar_map(n=256, res=0.25, ox=-10.0, oy=-10.0)
+    T, dt, vx = 25, 0.02, 3.0
+    x0 = np.array([1.0, 2.0, 0.0, 0.0, vx, 0.0, 0.0])
+    h = a + bx * (x0[0] + np.arange(1, T + 1) * dt * vx) + cy * x0[1]
+    for thr in (h[0] - 0.01, h[11] + 1e-4, h[-1] + 0.02):
+        P = prob(tmap, K=1, T=T, sigma=(0.0, 0.0), dt=dt, cost_w=(1.0, 0.0, 0.0, 0.0), map_cap=100.0,
+                 track_thresh=float(thr))
+        _, _, _, m = oracle.rollout_sample(P, x0, np.zeros((T, 2)), 0, 0)
+        assert m == pytest.approx(np.abs(h - thr).min(), abs=2e-6)

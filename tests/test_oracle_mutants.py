@@ -128,6 +128,15 @@ MUTANTS = [
     # the sort of the cross-entropy ranks and the Savitzky-Golay solve
     ("cem_sort_descending", "while (i > 0 && f[i - 1] > S[k])", "while (i > 0 && f[i - 1] < S[k])", CEM),
     ("savgol_back_substitution", "b[c] = s / A[c * n + c];", "b[c] = s;", LOOP),
+    ("rollout_clamp_dropped", "gv[i] = clampd(v[i], P->u_min[i], P->u_max[i]);", "gv[i] = v[i];", WU),
+    ("weights_eta_counts_nonfinite", "eta += isfinite(S[k]) ? exp(-(S[k] - rho) / lambda) : 0.0;",
+     "eta += isfinite(S[k]) ? exp(-(S[k] - rho) / lambda) : 1.0;", WU),
+    ("weights_rho_first_finite", "if (isfinite(S[k]) && S[k] < rho) rho = S[k];",
+     "if (isfinite(S[k]) && rho == INFINITY) rho = S[k];", WU),
+    ("update_noise_next_step", "      oracle_noise(P, iter, k, t, eps);\n      int importance",
+     "      oracle_noise(P, iter, k, t + 1 < P->T ? t + 1 : t, eps);\n      int importance", WU),
+    ("rollout_margin_not_tracked", "if (m < mmin) mmin = m;", "", COST),
+    ("rollout_margin_last_step", "if (m < mmin) mmin = m;", "mmin = m;", COST),
 ]
 
 

@@ -5,6 +5,9 @@
   limits stated in Sec. III-E, non-finite handling;
 * update: zero noise leaves U unchanged, the two lambda limits give the mean
   noise and the best sample's noise, the exploration split of Alg. 1;
+* rollouts: controls outside [u_min, u_max] reach the dynamics clamped (a
+  saturated nominal sequence makes every importance sample's trajectory the
+  one under constant u_max);
 * a linear-Gaussian / quadratic-cost toy whose optimal distribution q* of
   Sec. III-B is Gaussian with a closed-form mean (the self-normalised estimate
   at large K must match it within its CLT error);
@@ -58,8 +61,10 @@ def test_weights_lambda_limits():
 
 
 def test_weights_nonfinite_and_args():
-    rc, w, rho, _ = oracle.weights(np.array([np.inf, np.nan, 4.0, 5.0]), 1.0)
+    rc, w, rho, eta = oracle.weights(np.array([np.inf, np.nan, 4.0, 5.0]), 1.0)
     assert rc == 0 and rho == 4.0 and w[0] == 0 and w[1] == 0 and w[2] > w[3] > 0
+    # eta~ sums the finite samples only, so the weights still sum to one
+    assert eta == pytest.approx(1.0 + math.exp(-1.0), rel=1e-15) and w.sum() == pytest.approx(1.0, abs=1e-15)
     rc, _, _, _ = oracle.weights(np.array([np.inf, np.nan]), 1.0)
     assert rc == oracle.ERR_NONFINITE
     assert oracle.weights(np.array([1.0]), 0.0)[0] == oracle.ERR_ARG
@@ -124,6 +129,29 @@ def test_exploration_split_in_the_rollouts():
             _, tU, _, _ = oracle.rollout_sample(P, x0, U, 1, k)
             _, t0, _, _ = oracle.rollout_sample(P, x0, Z, 1, k)
             assert np.array_equal(tU, t0) == (k >= n_imp), (alpha, k)
+
+
+def test_saturated_controls_reach_the_dynamics_clamped():
+    # Alg. 1 feeds the dynamics g(v), v clamped to [u_min, u_max]: with a nominal sequence far
+    # outside the box every importance sample drives with the bound itself, so all of their
+    # trajectories equal the one under constant u_max whatever their noise, while the
+    # exploration samples (v = eps, inside the box) differ from it
+    T = 12
+    x0 = problems.x0_for(problems.ellipse_map(), speed=3.0)
+    U = np.full((T, 2), 50.0)
+    P = small_problem(K=6, T=T, alpha_explore=0.5)  # u_max = (1, 1)
+    x = np.asarray(x0, dtype=np.float64)
+    ref = [x]
+    for _ in range(T):
+        x = oracle.dynamics_step(P, x, np.array([1.0, 1.0]))
+        ref.append(x)
+    ref = np.array(ref)
+    for k in range(6):
+        _, traj, _, _ = oracle.rollout_sample(P, x0, U, 3, k)
+        if k < 3:
+            np.testing.assert_array_equal(traj, ref)
+        else:
+            assert not np.allclose(traj, ref)
 
 
 def linear_system(P: oracle.Problem, layers, xd0, T):
