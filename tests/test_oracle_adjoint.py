@@ -145,6 +145,13 @@ def test_state_cost_grad_on_planar_map():
         # the map holds float32 samples of the plane: slope error of order 1e-7 / res
         np.testing.assert_allclose(g[:2], [1.7 * bx, 1.7 * cy], rtol=0, atol=2e-6)
         assert np.all(g[2:] == 0.0)
+    # within half a texel of the left edge the clamped lookup is flat in x (both columns are
+    # column 0), so dh/dp_x is 0 there while dh/dp_y keeps the plane's slope
+    py = tmap.origin_y + 10.3 * tmap.res
+    for frac in (0.1, 0.25, 0.45):
+        g, _ = oracle.state_cost_grad(P, np.array([tmap.origin_x + frac * tmap.res, py, 0, 0, 1.0, 0, 0]), 1)
+        assert g[0] == 0.0
+        np.testing.assert_allclose(g[1], 1.7 * cy, rtol=0, atol=2e-6)
 
 
 def test_state_cost_grad_speed_and_slip_closed_form():

@@ -64,6 +64,11 @@ def test_clamp_to_edge():
     # below-left corner -> texel (0, 0)
     assert oracle.costmap(P, tmap.origin_x - 50, tmap.origin_y - 50) == pytest.approx(float(m32[0, 0]), abs=1e-12)
     assert math.isnan(oracle.costmap(P, float("nan"), 0.0))
+    # within half a texel of the left edge (before the first texel centre) the lookup is
+    # clamped too: at a row centre it is the edge texel itself, not an extrapolation
+    for frac in (0.1, 0.25, 0.45):
+        v = oracle.costmap(P, tmap.origin_x + frac * tmap.res, tmap.origin_y + 10.5 * tmap.res)
+        assert v == pytest.approx(float(m32[10, 0]), abs=1e-12)
 
 
 def const_map(v, n=16, res=1.0):

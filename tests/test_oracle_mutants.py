@@ -137,6 +137,35 @@ MUTANTS = [
      "      oracle_noise(P, iter, k, t + 1 < P->T ? t + 1 : t, eps);\n      int importance", WU),
     ("rollout_margin_not_tracked", "if (m < mmin) mmin = m;", "", COST),
     ("rollout_margin_last_step", "if (m < mmin) mmin = m;", "mmin = m;", COST),
+    ("mlp_h1_no_tanh", "    h1[j] = act(P, a);", "    h1[j] = a;", DYN, 2, 0),
+    ("mlp_h2_no_tanh", "    h2[j] = act(P, a);", "    h2[j] = a;", DYN, 2, 0),
+    ("mlp_w3_reads_h1", "a += P->W3[(size_t)o * H + i] * h2[i];", "a += P->W3[(size_t)o * H + i] * h1[i];", DYN),
+    ("position_uses_new_heading", "xn[1] = x[1] + (sin(th) * vx + cos(th) * vy) * P->dt;",
+     "xn[1] = x[1] + (sin(th + thd * P->dt) * vx + cos(th + thd * P->dt) * vy) * P->dt;", DYN),
+    ("state_derivative_without_dt", "xn[3 + i] = x[3 + i] + f[i] * P->dt;", "xn[3 + i] = x[3 + i] + f[i];", DYN),
+    ("plant_without_clamp",
+     "double gv[2] = {clampd(u[0], P->u_min[0], P->u_max[0]), clampd(u[1], P->u_min[1], P->u_max[1])};",
+     "double gv[2] = {u[0], u[1]};", DYN + LOOP),
+    ("clamp_bounds_swapped", "return v < lo ? lo : (v > hi ? hi : v);", "return v < lo ? hi : (v > hi ? lo : v);",
+     DYN + WU),
+    ("costmap_clamp_high_edge", "(i > (double)(n - 1) ? n - 1 : (long)i)", "(i > (double)(n - 1) ? n - 2 : (long)i)",
+     COST),
+    ("costmap_floor_truncates", "double jf = floor(fx), if_ = floor(fy);",
+     "double jf = (double)(long)fx, if_ = (double)(long)fy;", COST, 2, 0),
+    ("box_muller_z1_cos", "z[1] = r * sin(two_pi * u1);", "z[1] = r * cos(two_pi * u1);", NOISE),
+    ("noise_seed_halves_swapped", "uint32_t key[2] = {(uint32_t)P->seed, (uint32_t)(P->seed >> 32)};",
+     "uint32_t key[2] = {(uint32_t)(P->seed >> 32), (uint32_t)P->seed};", NOISE),
+    ("noise_iter_hi_mask", "(uint32_t)((iter >> 32) & 0xFFFFu)", "(uint32_t)((iter >> 32) & 0xFFu)", NOISE),
+    ("noise_iter_lo_dropped", "{(uint32_t)k, (uint32_t)t, (uint32_t)iter,", "{(uint32_t)k, (uint32_t)t, 0u,", NOISE),
+    ("basis_alpha_r_sign", "atan(vy / vx - 0.35 * r / vx)", "atan(vy / vx + 0.35 * r / vx)", BASIS),
+    ("basis_slow_threshold", "const int fast = vx > 0.1;", "const int fast = vx > 0.0;", BASIS),
+    ("basis_phi24_square", "phi[24] = uF * uF * uF;", "phi[24] = uF * uF;", BASIS),
+    ("basis_phi3_abs_dropped", "phi[3] = sd * tf * fabs(tf) / (1200.0 * 1200.0);",
+     "phi[3] = sd * tf * tf / (1200.0 * 1200.0);", BASIS),
+    ("adj_h1_no_tanh", "    h1[j] = act(P, a);", "    h1[j] = a;", ADJ, 2, 1),
+    ("adj_h2_no_tanh", "    h2[j] = act(P, a);", "    h2[j] = a;", ADJ, 2, 1),
+    ("adj_costmap_floor_truncates", "double jf = floor(fx), if_ = floor(fy);",
+     "double jf = (double)(long)fx, if_ = (double)(long)fy;", ADJ, 2, 1),
 ]
 
 

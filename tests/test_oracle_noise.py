@@ -87,13 +87,14 @@ def test_noise_scale_and_counter_layout():
     assert abs(eps[..., 0].std() - 0.3) < 5 * 0.3 / math.sqrt(2 * n)
     assert abs(eps[..., 1].std() - 0.35) < 5 * 0.35 / math.sqrt(2 * n)
     # counter = (k, t, iter_lo, iter_hi & 0xFFFF | instance << 16), key = (seed_lo, seed_hi)
-    it = (5 << 32) | 9
     P2 = P.replace(instance=3)
-    for k, t in [(0, 0), (17, 5), (511, 39)]:
-        w = oracle.philox(np.array([[k, t, 9, 5 | (3 << 16)]], np.uint32),
-                          [problems.PHILOX_SEED & 0xFFFFFFFF, problems.PHILOX_SEED >> 32])[0]
-        z = oracle.box_muller(int(w[0]), int(w[1]))
-        assert np.array_equal(oracle.noise_at(P2, it, k, t), np.array([0.3 * z[0], 0.35 * z[1]]))
+    for hi in (5, 0xBEEF):  # all 16 kept bits of the iteration's high word reach the counter
+        it = (hi << 32) | 9
+        for k, t in [(0, 0), (17, 5), (511, 39)]:
+            w = oracle.philox(np.array([[k, t, 9, hi | (3 << 16)]], np.uint32),
+                              [problems.PHILOX_SEED & 0xFFFFFFFF, problems.PHILOX_SEED >> 32])[0]
+            z = oracle.box_muller(int(w[0]), int(w[1]))
+            assert np.array_equal(oracle.noise_at(P2, it, k, t), np.array([0.3 * z[0], 0.35 * z[1]]))
     # different iterations, instances and seeds give unrelated streams
     assert not np.allclose(oracle.noise(P, 4)[0, 0], eps[0, 0])
     assert not np.allclose(oracle.noise(P2, 3)[0, 0], eps[0, 0])
