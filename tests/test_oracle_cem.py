@@ -3,8 +3,9 @@
 * the elite set equals the zeta = round(K (1 - delta)) lowest costs found by numpy's
   argsort (a separate sort), the weights are 1/zeta on it and sum to one;
 * ties at the threshold enter the elite set together (the set of costs <= Z),
-  normalised by its size; non-finite costs are never elite; all non-finite is an
-  error;
+  normalised by its size; non-finite costs (-inf included) are never elite and
+  zeta clamps to the number of finite costs; all non-finite is an error;
+* costs handed to the iteration (the stage-wise form) replace the rollouts' own;
 * delta -> 1 keeps only the arg-min, delta = 0 keeps every finite sample (the plain
   mean); the CEM update is the un-weighted mean of the elite controls.
 """
@@ -37,8 +38,12 @@ def test_ties_nonfinite_and_limits():
     np.testing.assert_allclose(w, [0, 0.25, 0.25, 0.25, 0.25, 0, 0, 0], atol=1e-15)
     rc, w, _, m = oracle.cem_weights(S, 1.0)  # zeta clamps to 1: the arg-min
     assert m == 1 and w[1] == 1.0
-    rc, w, _, m = oracle.cem_weights(S, 0.0)  # every finite cost
-    assert m == 6 and np.all(w[[5, 6]] == 0) and w.sum() == pytest.approx(1.0)
+    rc, w, Z, m = oracle.cem_weights(S, 0.0)  # zeta = 8 clamps to the 6 finite costs: every one
+    assert m == 6 and Z == 9.0 and np.all(w[[5, 6]] == 0) and w.sum() == pytest.approx(1.0)
+    # -inf is not a finite cost either: it is never elite and does not count in |E|
+    rc, w, Z, m = oracle.cem_weights(np.array([-np.inf, 2.0, 1.0]), 0.5)  # zeta = round(1.5) = 2
+    assert rc == 0 and Z == 2.0 and m == 2
+    np.testing.assert_array_equal(w, [0.0, 0.5, 0.5])
     rc, w, _, _ = oracle.cem_weights([np.nan, np.inf], 0.5)
     assert rc == oracle.ERR_NONFINITE and np.all(w == 0)
 
@@ -55,3 +60,20 @@ def test_cem_update_is_the_elite_mean():
     eps = oracle.noise(P, 4)
     ref = np.mean(np.asarray(U, np.float64)[None] + eps[elite], axis=0)
     np.testing.assert_allclose(Uo, ref, rtol=0, atol=1e-13)
+
+
+def test_cem_iteration_takes_given_costs():
+    # the stage-wise form: costs handed in replace the rollouts' own in the weights, so the
+    # elite set is the given costs' lowest zeta (here the reverse of the rollouts' order)
+    tmap = problems.ellipse_map()
+    P = problems.oracle_problem(problems.params_small(K=40, T=10), tmap, problems.network(32))
+    x0 = problems.x0_for(tmap, speed=3.0)
+    U = inputs.nominal_controls(10, seed=3, scale=0.3)
+    _, _, _, S = oracle.iterate_cem(P, x0, U, 4, delta=0.8)
+    S_use = -S
+    rc, Uo, w, S2 = oracle.iterate_cem(P, x0, U, 4, delta=0.8, S_use=S_use)
+    assert rc == 0 and np.array_equal(S2, S)
+    np.testing.assert_array_equal(w, oracle.cem_weights(S_use, 0.8)[1])
+    elite = np.argsort(S_use, kind="stable")[:8]
+    eps = oracle.noise(P, 4)
+    np.testing.assert_allclose(Uo, np.mean(np.asarray(U, np.float64)[None] + eps[elite], axis=0), rtol=0, atol=1e-13)

@@ -166,6 +166,23 @@ MUTANTS = [
     ("adj_h2_no_tanh", "    h2[j] = act(P, a);", "    h2[j] = a;", ADJ, 2, 1),
     ("adj_costmap_floor_truncates", "double jf = floor(fx), if_ = floor(fy);",
      "double jf = (double)(long)fx, if_ = (double)(long)fy;", ADJ, 2, 1),
+    ("savgol_value_is_slope", "y[(size_t)j * stride] = b[0];", "y[(size_t)j * stride] = b[1];", LOOP),
+    ("savgol_stride_ignored", "b[r] += pw[r] * x[(size_t)i * stride];", "b[r] += pw[r] * x[(size_t)i];", LOOP),
+    ("savgol_window_short", "for (int32_t o = -half; o <= half; ++o) {", "for (int32_t o = -half; o < half; ++o) {",
+     LOOP),
+    ("delta_smoothing_without_difference", "      for (int32_t t = 0; t < 2 * T; ++t) D[t] = U_prime[t] - U[t];",
+     "      for (int32_t t = 0; t < 2 * T; ++t) D[t] = U_prime[t];", LOOP),
+    ("applied_throttle_from_next_step", "    u_applied[1] = Us[1];", "    u_applied[1] = Us[3];", LOOP),
+    ("warm_start_shift_by_two", "      U_next[2 * (t - 1)] = Us[2 * t];\n",
+     "      U_next[2 * (t - 1)] = Us[2 * t < 2 * T - 2 ? 2 * t + 2 : 2 * t];\n", LOOP),
+    ("plant_driven_by_next_control", "    if (plant) oracle_plant_step(P, x0, u_applied, x_next);",
+     "    if (plant) oracle_plant_step(P, x0, Us + 2, x_next);", LOOP),
+    ("cem_zeta_not_clamped_low", "  if (zeta < 1) zeta = 1;\n", "", CEM),
+    ("cem_zeta_clamped_to_K", "  if (zeta > n) zeta = n;\n", "  if (zeta > K) zeta = K;\n", CEM),
+    ("cem_minus_inf_counted", "m += (isfinite(S[k]) && S[k] <= Z) ? 1 : 0;", "m += (S[k] <= Z) ? 1 : 0;", CEM),
+    ("cem_weight_not_normalised", "? 1.0 / (double)m : 0.0;", "? 1.0 : 0.0;", CEM),
+    ("cem_given_costs_ignored", "rc = oracle_cem_weights(P->K, S_use ? S_use : S, delta, w, NULL, NULL);",
+     "rc = oracle_cem_weights(P->K, S, delta, w, NULL, NULL);", CEM),
 ]
 
 
