@@ -8,10 +8,14 @@ reverse sweep is pinned against things it does not share code with:
   network weights; with exploration samples, the control-cost term, active
   clamps and the impulse terms present;
 * torch autograd (float64) for the network's vector-Jacobian product;
-* a planar costmap, whose bilinear slope is the plane's gradient in closed form;
+* a planar costmap, whose bilinear slope is the plane's gradient in closed form,
+  zero above the cap and, across x, within half a texel of the edge;
+* non-finite costs keep weight 0 and stay out of J and of every gradient;
 * lambda -> infinity, where the weights are uniform: dJ/dcost_w is the mean of
   the per-sample cost components and dU'/dU is the identity.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -145,6 +149,13 @@ def test_state_cost_grad_on_planar_map():
         # the map holds float32 samples of the plane: slope error of order 1e-7 / res
         np.testing.assert_allclose(g[:2], [1.7 * bx, 1.7 * cy], rtol=0, atol=2e-6)
         assert np.all(g[2:] == 0.0)
+    # above the cap the track term is constant, so the map passes no slope
+    Pc = oracle.Problem(layers=list(layers), costmap=tmap.data.astype(np.float32), res=tmap.res,
+                        origin_x=tmap.origin_x, origin_y=tmap.origin_y,
+                        **problems.params_small(cost_w=(1.7, 0.0, 0.0, 0.0), map_cap=0.2))
+    for px, py in [(0.3, 6.0), (4.1, 9.9)]:
+        g, comp = oracle.state_cost_grad(Pc, np.array([px, py, 0, 0, 1.0, 0, 0]), 1)
+        assert comp[0] == 0.2 and np.all(g == 0.0)
     # within half a texel of the left edge the clamped lookup is flat in x (both columns are
     # column 0), so dh/dp_x is 0 there while dh/dp_y keeps the plane's slope
     py = tmap.origin_y + 10.3 * tmap.res
@@ -193,3 +204,11 @@ def test_stagewise_costs_override():
     np.testing.assert_allclose(r2["w"], r0["w"], rtol=1e-12)
     np.testing.assert_allclose(r2["g_net"], r0["g_net"], rtol=1e-9, atol=1e-12)
     assert r2["J"] == pytest.approx(r0["J"] + 123.0, rel=1e-13)
+    # a non-finite cost has weight 0 and stays out of J = sum_k w_k S_k (no 0 * inf)
+    S_bad = r0["S"].copy()
+    S_bad[[1, 4]] = [np.inf, np.nan]
+    r3 = oracle.iterate_vjp(P, x0, U, 1, 0.5, gU, S_use=S_bad)
+    ok = np.isfinite(S_bad)
+    assert np.all(r3["w"][~ok] == 0.0) and math.isfinite(r3["J"])
+    assert r3["J"] == pytest.approx(float(np.dot(r3["w"][ok], S_bad[ok])), rel=1e-14)
+    assert np.all(np.isfinite(r3["g_net"])) and np.all(np.isfinite(r3["g_U"]))

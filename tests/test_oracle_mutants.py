@@ -183,6 +183,42 @@ MUTANTS = [
     ("cem_weight_not_normalised", "? 1.0 / (double)m : 0.0;", "? 1.0 : 0.0;", CEM),
     ("cem_given_costs_ignored", "rc = oracle_cem_weights(P->K, S_use ? S_use : S, delta, w, NULL, NULL);",
      "rc = oracle_cem_weights(P->K, S, delta, w, NULL, NULL);", CEM),
+    ("adj_gb3_dropped", "    gb3[o] += dbar[o];\n",
+     "", ADJ),
+    ("adj_gW3_uses_h1", "for (int i = 0; i < H; ++i) gW3[o * H + i] += dbar[o] * h2[i];",
+     "for (int i = 0; i < H; ++i) gW3[o * H + i] += dbar[o] * h1[i];", ADJ),
+    ("adj_h2_derivative_uses_h1", "a2bar[i] = s * act_deriv(P, h2[i]);",
+     "a2bar[i] = s * act_deriv(P, h1[i]);", ADJ),
+    ("adj_gb2_dropped", "    gb2[j] += a2bar[j];\n",
+     "", ADJ),
+    ("adj_gW1_input_index", "for (int m = 0; m < 6; ++m) gW1[j * 6 + m] += a1bar[j] * z[m];",
+     "for (int m = 0; m < 6; ++m) gW1[j * 6 + m] += a1bar[j] * z[5 - m];", ADJ),
+    ("adj_zbar_transposed", "for (int j = 0; j < H; ++j) s += P->W1[j * 6 + m] * a1bar[j];",
+     "for (int j = 0; j < H; ++j) s += P->W1[(j * 6 + m) % (6 * H)] * a1bar[(j + 1) % H];", ADJ),
+    ("adj_map_slope_no_res", "gx[0] += P->cost_w[0] * dh_dfx / P->res;",
+     "gx[0] += P->cost_w[0] * dh_dfx;", ADJ),
+    ("adj_map_slope_through_cap", "  if (!(h > P->map_cap)) {\n    double fx",
+     "  if (1) {\n    double fx", ADJ),
+    ("adj_slip_dvx_sign", "double dz_dvx = vy * sgn / r2,",
+     "double dz_dvx = -vy * sgn / r2,", ADJ),
+    ("adj_vx_through_heading", "xbar[4] += dt * (xbar_n[0] * c + xbar_n[1] * s);",
+     "xbar[4] += dt * (xbar_n[0] * c - xbar_n[1] * s);", ADJ),
+    ("adj_vy_through_heading", "xbar[5] += dt * (-xbar_n[0] * s + xbar_n[1] * c);",
+     "xbar[5] += dt * (xbar_n[0] * s + xbar_n[1] * c);", ADJ),
+    ("adj_dbar_without_dt", "double dbar[4] = {dt * xbar_n[3], dt * xbar_n[4], dt * xbar_n[5], dt * xbar_n[6]};",
+     "double dbar[4] = {xbar_n[3], xbar_n[4], xbar_n[5], xbar_n[6]};", ADJ),
+    ("adj_state_skips_network", "  for (int i = 0; i < 4; ++i) xbar[3 + i] += zbar[i];\n",
+     "", ADJ),
+    ("adj_controls_swapped", "  gvbar[0] = zbar[4];\n  gvbar[1] = zbar[5];",
+     "  gvbar[0] = zbar[5];\n  gvbar[1] = zbar[4];", ADJ),
+    ("adj_cost_at_previous_state", "    oracle_state_cost_grad(P, xt, t, gx, comp);",
+     "    oracle_state_cost_grad(P, xp, t, gx, comp);", ADJ),
+    ("adj_control_cost_du_uses_u", "        ubar += Sbar * P->gamma * v[i] * is2;",
+     "        ubar += Sbar * P->gamma * u[i] * is2;", ADJ),
+    ("adj_J_includes_zero_weights", "    if (w[k] != 0.0) J += w[k] * Sw[k];",
+     "    J += w[k] * Sw[k];", ADJ),
+    ("adj_c0_dropped", "    for (int32_t t = 0; t < 2 * T; ++t) c0 += gUo[t] * U_out[t];",
+     "    for (int32_t t = 0; t < 2 * T; ++t) c0 += 0.0;", ADJ),
 ]
 
 
