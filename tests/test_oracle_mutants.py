@@ -219,6 +219,28 @@ MUTANTS = [
      "    J += w[k] * Sw[k];", ADJ),
     ("adj_c0_dropped", "    for (int32_t t = 0; t < 2 * T; ++t) c0 += gUo[t] * U_out[t];",
      "    for (int32_t t = 0; t < 2 * T; ++t) c0 += 0.0;", ADJ),
+    ("philox_k0_weyl_constant", "k0 += 0x9E3779B9u;",
+     "k0 += 0x9E3779B8u;", NOISE),
+    ("philox_multiplier0", "uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;",
+     "uint64_t p0 = (uint64_t)0xD2511F55u * (uint64_t)c0;", NOISE),
+    ("philox_lo_words_swapped", "    uint32_t n1 = lo1;\n",
+     "    uint32_t n1 = lo0;\n", NOISE),
+    ("philox_key_bump_first_round", "    if (round > 0) {\n",
+     "    if (round >= 0) {\n", NOISE),
+    ("uniform_bits_shift", "static double u01(uint32_t a) { return ((double)(a >> 8) + 1.0) * (1.0 / 16777216.0); }",
+     "static double u01(uint32_t a) { return ((double)(a >> 9) + 1.0) * (1.0 / 8388608.0); }", NOISE),
+    ("box_muller_two_pi_as_pi", "  z[0] = r * cos(two_pi * u1);",
+     "  z[0] = r * cos(0.5 * two_pi * u1);", NOISE),
+    ("noise_words_2_3", "  oracle_box_muller(w[0], w[1], z);",
+     "  oracle_box_muller(w[2], w[3], z);", NOISE),
+    ("dyn_heading_uses_yaw_of_xd", "  double th = x[2], vx = x[4], vy = x[5], thd = x[6];\n  double z[6]",
+     "  double th = x[2], vx = x[4], vy = x[5], thd = x[3];\n  double z[6]", DYN),
+    ("basis_theta_row_stride", "a += P->theta[i * 4 + o] * phi[i];",
+     "a += P->theta[i * 4 + (o + 1) % 4] * phi[i];", BASIS),
+    ("basis_phi19_scale", "phi[19] = th * vx / 3.0;",
+     "phi[19] = th * vx / 30.0;", BASIS),
+    ("basis_phi9_slow_branch", "phi[9] = fast ? (vy / vx) / 40.0 : 0.0;",
+     "phi[9] = (vy / (vx == 0.0 ? 1.0 : vx)) / 40.0;", BASIS),
 ]
 
 
